@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for the FFT-based Morlet CWT (arXiv 2506.07793).
+
+TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py may import this package.  The CUDA library never
+calls it and shares no code with it.
+
+The arithmetic lives in plain C (cwt_oracle.c, loaded through ctypes); this
+module only marshals numpy arrays and derives power and phase from the complex
+coefficients (Section "Precision": real part, imaginary part, phase and power
+of the CWT result).  See cwt_oracle.c for the definition being computed:
+the cyclic convolution of the zero-padded signal with the N-periodised,
+unit-energy Morlet wavelet of Eq. 3, which is what Eq. 2 evaluates.
+
+Parity pins live in tests/test_oracle_pins.py.  Every function here is pinned
+except `paper_style_error`, which restates the error metric of Table 1 and is
+marked "parity unpinned" (it is a report, not a result).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_periodised_wavelet.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.oracle_periodised_wavelet.restype = ctypes.c_int
+        lib.oracle_wavelet.argtypes = lib.oracle_periodised_wavelet.argtypes
+        lib.oracle_wavelet.restype = ctypes.c_int
+        lib.oracle_cwt_rows.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip,
+                                        ctypes.c_int, dp, dp, ctypes.c_int]
+        lib.oracle_cwt_rows.restype = ctypes.c_int
+        lib.oracle_dft.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.oracle_dft.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+WAVELETS = {"morlet": 0, "gabor": 1}
+
+
+def periodised_wavelet(freq, n_cycles, fs, N, wavelet="morlet"):
+    """p[m] = sum_r psi((m + rN)/fs), m in [0, N) -- before normalisation."""
+    lib = _load()
+    re = np.zeros(N)
+    im = np.zeros(N)
+    rc = lib.oracle_periodised_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(fs),
+                                       int(N), _dp(re), _dp(im))
+    if rc != 0:
+        raise ValueError("oracle_periodised_wavelet: bad argument")
+    return re + 1j * im
+
+
+def wavelet(freq, n_cycles, fs, N, wavelet="morlet"):
+    """Unit-energy N-periodised sampled wavelet of one scale (complex128)."""
+    lib = _load()
+    re = np.zeros(N)
+    im = np.zeros(N)
+    rc = lib.oracle_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(fs), int(N),
+                            _dp(re), _dp(im))
+    if rc != 0:
+        raise ValueError("oracle_wavelet: bad argument")
+    return re + 1j * im
+
+
+def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", threads=None):
+    """Complex CWT coefficients of the (channel, scale) pairs in `rows`.
+
+    x: [C][n] real signal.  Returns complex128 [len(rows)][ceil(n/d)].
+    """
+    lib = _load()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if x.ndim == 1:
+        x = x[None, :]
+    C, n = x.shape
+    freqs = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+    n_cycles = np.ascontiguousarray(np.broadcast_to(np.asarray(n_cycles, dtype=np.float64),
+                                                    freqs.shape))
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1, 2)
+    rc_ = np.ascontiguousarray(rows[:, 0].astype(np.int32))
+    rs_ = np.ascontiguousarray(rows[:, 1].astype(np.int32))
+    d = int(decimation)
+    n_out = (n + d - 1) // d
+    out_re = np.zeros((len(rows), n_out))
+    out_im = np.zeros((len(rows), n_out))
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = lib.oracle_cwt_rows(_dp(x), C, n, int(N), float(fs), _dp(freqs), _dp(n_cycles),
+                             len(freqs), WAVELETS[wavelet], d, _ip(rc_), _ip(rs_), len(rows),
+                             _dp(out_re), _dp(out_im), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_cwt_rows failed ({rc})")
+    return out_re + 1j * out_im
+
+
+def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None):
+    """Complex CWT of every row: complex128 [C][S][ceil(n/d)]."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[None, :]
+    C = x.shape[0]
+    S = len(np.atleast_1d(freqs))
+    rows = [(c, s) for c in range(C) for s in range(S)]
+    out = cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation, wavelet, threads)
+    return out.reshape(C, S, -1)
+
+
+def power(c):
+    """|c|^2 (Section "Precision": power of the CWT result)."""
+    return c.real * c.real + c.imag * c.imag
+
+
+def phase(c):
+    """atan2(Im c, Re c) in (-pi, pi] (Section "Precision": phase part)."""
+    return np.arctan2(c.imag, c.real)
+
+
+def dft(z, sign=-1):
+    """Brute-force O(N^2) DFT (no 1/N), for tiny-input pins only."""
+    lib = _load()
+    z = np.asarray(z, dtype=np.complex128)
+    re = np.ascontiguousarray(z.real)
+    im = np.ascontiguousarray(z.imag)
+    ore = np.zeros(len(z))
+    oim = np.zeros(len(z))
+    if lib.oracle_dft(_dp(re), _dp(im), len(z), int(sign), _dp(ore), _dp(oim)) != 0:
+        raise ValueError("oracle_dft: bad argument")
+    return ore + 1j * oim
+
+
+def paper_style_error(test, ref, interior=(0.2, 0.8), threshold_sd=1e-5):
+    """Table 1's metric: |test - ref| / SD(ref) over the interior of each row.
+
+    Parity unpinned: this is a secondary report, not a result of the method.
+    Returns (max, mean, count above threshold) over the interior window for
+    the real and imaginary parts.
+    """
+    n = ref.shape[-1]
+    lo, hi = int(round(interior[0] * n)), int(round(interior[1] * n))
+    out = {}
+    for name, f in (("real", np.real), ("imag", np.imag)):
+        r = f(ref)[..., lo:hi]
+        t = f(test)[..., lo:hi]
+        sd = np.std(r)
+        diff = np.abs(t - r) / sd
+        out[name] = (float(diff.max()), float(diff.mean()), int((diff > threshold_sd).sum()))
+    return out

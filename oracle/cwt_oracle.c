@@ -1,0 +1,266 @@
+/*
+ * cwt_oracle.c -- plain, slow, FP64 CPU oracle for the FFT-based continuous
+ * wavelet transform (CWT) of multichannel EEG (arXiv 2506.07793).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this library.  It shares no code,
+ * header, table or constant with the CUDA library: it works in the time
+ * domain, with no FFT, so that it can check the GPU's frequency-domain path.
+ *
+ * What it computes (the result the paper's method reaches, written out):
+ *
+ *  1. The complex Morlet wavelet in the sigma-parametrisation of Eq. 3
+ *     (Section "Fourier transformed formula").  With carrier F (Hz) and
+ *     sigma = n_cycles, the time scale is a = sigma / (2 pi F) seconds and
+ *     kappa = exp(-sigma^2 / 2).  The time-domain wavelet whose Fourier
+ *     transform is Eq. 3 (up to constant factors that the unit-energy
+ *     normalisation below removes) is
+ *         psi(tau) = exp(-tau^2 / (2 a^2)) * (exp(i 2 pi F tau) - kappa).
+ *     kappa makes the wavelet zero-mean (the Morlet correction term; with
+ *     kappa = 0 it is the Gabor wavelet of Eq. 4).
+ *
+ *  2. The FFT path computes a CYCLIC convolution over the padded length N
+ *     (Eq. 1 and Eq. 2: the inverse FFT of a product of spectra).  Sampling
+ *     the analytic spectrum on N bins is the same as convolving cyclically
+ *     with the N-periodised sampled wavelet
+ *         p[m] = sum_{r in Z} psi((m + r N) / fs),   m = 0..N-1,
+ *     (indices m > N/2 hold negative time).  The sum over r runs over every
+ *     replica whose Gaussian envelope is not exactly zero in double.
+ *
+ *  3. Each scale is normalised to unit discrete energy,
+ *         pn[m] = p[m] / sqrt(sum_m |p[m]|^2).
+ *
+ *  4. The signal x[0..n) is zero-padded to N and convolved cyclically:
+ *         c[t] = sum_{m=0}^{n-1} x[m] * pn[(t - m) mod N],
+ *     for the kept output positions t = 0, d, 2d, ... < n (decimation d).
+ *     Power and phase are |c|^2 and atan2(Im c, Re c); the Python wrapper
+ *     derives them from c.
+ *
+ * Everything is O(n * n_out) per (channel, scale) row, in double, with a
+ * plain sequential sum.  Rows are independent, so they are spread over
+ * POSIX threads; threading changes no arithmetic.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* Envelope exp(-u) is exactly 0.0 in double for u > 745.2, so replicas with
+ * |tau| > a * sqrt(2 * 746) contribute nothing; 39 a is a safe bound. */
+#define ORACLE_ENVELOPE_RADIUS 39.0
+
+/* Step 1: the Morlet wavelet at time tau (seconds). */
+static void morlet_psi(double tau, double F, double sigma, double *re, double *im)
+{
+    double a = sigma / (2.0 * ORACLE_PI * F);
+    double env = exp(-(tau * tau) / (2.0 * a * a));
+    double kappa = exp(-0.5 * sigma * sigma);
+    double ph = 2.0 * ORACLE_PI * F * tau;
+    *re = env * (cos(ph) - kappa);
+    *im = env * sin(ph);
+}
+
+/* Gabor variant (kappa = 0, Eq. 4), kept for the pins that compare the two. */
+static void gabor_psi(double tau, double F, double sigma, double *re, double *im)
+{
+    double a = sigma / (2.0 * ORACLE_PI * F);
+    double env = exp(-(tau * tau) / (2.0 * a * a));
+    double ph = 2.0 * ORACLE_PI * F * tau;
+    *re = env * cos(ph);
+    *im = env * sin(ph);
+}
+
+/* Step 2: p[m] = sum_r psi((m + r N) / fs).  kind 0 = Morlet, 1 = Gabor.
+ * Returns 0, or -1 on a bad argument. */
+int oracle_periodised_wavelet(int kind, double F, double sigma, double fs, int N,
+                              double *p_re, double *p_im)
+{
+    if (N <= 0 || !(F > 0.0) || !(sigma > 0.0) || !(fs > 0.0) || (kind != 0 && kind != 1))
+        return -1;
+    double a = sigma / (2.0 * ORACLE_PI * F);
+    double reach = ORACLE_ENVELOPE_RADIUS * a * fs; /* in samples */
+    for (int m = 0; m < N; ++m) {
+        double lo = ceil((-reach - (double)m) / (double)N);
+        double hi = floor((reach - (double)m) / (double)N);
+        double sre = 0.0, sim = 0.0;
+        for (double r = lo; r <= hi; r += 1.0) {
+            double tau = ((double)m + r * (double)N) / fs;
+            double vre, vim;
+            if (kind == 0)
+                morlet_psi(tau, F, sigma, &vre, &vim);
+            else
+                gabor_psi(tau, F, sigma, &vre, &vim);
+            sre += vre;
+            sim += vim;
+        }
+        p_re[m] = sre;
+        p_im[m] = sim;
+    }
+    return 0;
+}
+
+/* Steps 2 + 3: the unit-energy periodised wavelet of one scale. */
+int oracle_wavelet(int kind, double F, double sigma, double fs, int N, double *w_re, double *w_im)
+{
+    int rc = oracle_periodised_wavelet(kind, F, sigma, fs, N, w_re, w_im);
+    if (rc != 0)
+        return rc;
+    double e = 0.0;
+    for (int m = 0; m < N; ++m)
+        e += w_re[m] * w_re[m] + w_im[m] * w_im[m];
+    if (!(e > 0.0))
+        return -1;
+    double inv = 1.0 / sqrt(e);
+    for (int m = 0; m < N; ++m) {
+        w_re[m] *= inv;
+        w_im[m] *= inv;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 4: direct cyclic convolution over selected (channel, scale) rows.   */
+
+typedef struct {
+    const double *x; /* [C][n] */
+    int n, N, d, n_out;
+    const double *wre, *wim; /* [S][N] unit-energy wavelets */
+    const int *row_c, *row_s; /* rows to compute */
+    int n_rows;
+    double *out_re, *out_im; /* [n_rows][n_out] */
+    int next;                /* next row to take (guarded by lock) */
+    pthread_mutex_t lock;
+} conv_job;
+
+static void conv_row(const conv_job *J, int i)
+{
+    const double *x = J->x + (size_t)J->row_c[i] * (size_t)J->n;
+    const double *wr = J->wre + (size_t)J->row_s[i] * (size_t)J->N;
+    const double *wi = J->wim + (size_t)J->row_s[i] * (size_t)J->N;
+    double *ore = J->out_re + (size_t)i * (size_t)J->n_out;
+    double *oim = J->out_im + (size_t)i * (size_t)J->n_out;
+    for (int o = 0; o < J->n_out; ++o) {
+        int t = o * J->d;
+        double sre = 0.0, sim = 0.0;
+        for (int m = 0; m < J->n; ++m) {
+            int idx = t - m;
+            if (idx < 0)
+                idx += J->N;
+            sre += x[m] * wr[idx];
+            sim += x[m] * wi[idx];
+        }
+        ore[o] = sre;
+        oim[o] = sim;
+    }
+}
+
+static void *conv_worker(void *arg)
+{
+    conv_job *J = (conv_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int i = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (i >= J->n_rows)
+            break;
+        conv_row(J, i);
+    }
+    return NULL;
+}
+
+/*
+ * oracle_cwt_rows: CWT coefficients of the listed rows.
+ *   x        [C][n] signal (double)
+ *   N        cyclic length (>= n)
+ *   fs       sampling rate (Hz)
+ *   freqs, n_cycles [S]: carrier F_s and sigma_s of each scale
+ *   kind     0 = Morlet, 1 = Gabor
+ *   d        decimation (>= 1); n_out = ceil(n / d)
+ *   row_c, row_s [n_rows]: channel and scale index of each requested row
+ *   out_re, out_im [n_rows][n_out]
+ *   n_threads worker threads (>= 1)
+ * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
+ */
+int oracle_cwt_rows(const double *x, int C, int n, int N, double fs, const double *freqs,
+                    const double *n_cycles, int S, int kind, int d, const int *row_c,
+                    const int *row_s, int n_rows, double *out_re, double *out_im, int n_threads)
+{
+    if (C <= 0 || n <= 0 || N < n || S <= 0 || d < 1 || n_rows < 0 || !(fs > 0.0))
+        return -1;
+    for (int i = 0; i < n_rows; ++i)
+        if (row_c[i] < 0 || row_c[i] >= C || row_s[i] < 0 || row_s[i] >= S)
+            return -1;
+    if (n_threads < 1)
+        n_threads = 1;
+    double *wre = (double *)malloc(sizeof(double) * (size_t)S * (size_t)N);
+    double *wim = (double *)malloc(sizeof(double) * (size_t)S * (size_t)N);
+    if (!wre || !wim) {
+        free(wre);
+        free(wim);
+        return -2;
+    }
+    int rc = 0;
+    for (int s = 0; s < S && rc == 0; ++s)
+        rc = oracle_wavelet(kind, freqs[s], n_cycles[s], fs, N, wre + (size_t)s * N,
+                            wim + (size_t)s * N);
+    if (rc == 0) {
+        conv_job J;
+        J.x = x;
+        J.n = n;
+        J.N = N;
+        J.d = d;
+        J.n_out = (n + d - 1) / d;
+        J.wre = wre;
+        J.wim = wim;
+        J.row_c = row_c;
+        J.row_s = row_s;
+        J.n_rows = n_rows;
+        J.out_re = out_re;
+        J.out_im = out_im;
+        J.next = 0;
+        pthread_mutex_init(&J.lock, NULL);
+        if (n_threads == 1) {
+            conv_worker(&J);
+        } else {
+            pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+            int started = 0;
+            if (th)
+                for (; started < n_threads; ++started)
+                    if (pthread_create(&th[started], NULL, conv_worker, &J) != 0)
+                        break;
+            conv_worker(&J); /* the caller's thread works too */
+            for (int i = 0; i < started; ++i)
+                pthread_join(th[i], NULL);
+            free(th);
+        }
+        pthread_mutex_destroy(&J.lock);
+    }
+    free(wre);
+    free(wim);
+    return rc;
+}
+
+/* Brute-force O(N^2) DFT in double, sign -1 (forward) or +1 (inverse, no
+ * 1/N).  Used only by the pins to cross-check indexing on tiny inputs. */
+int oracle_dft(const double *in_re, const double *in_im, int N, int sign, double *out_re,
+               double *out_im)
+{
+    if (N <= 0 || (sign != 1 && sign != -1))
+        return -1;
+    for (int k = 0; k < N; ++k) {
+        double sre = 0.0, sim = 0.0;
+        for (int m = 0; m < N; ++m) {
+            /* angle reduced mod N in integers to keep it exact */
+            long long km = ((long long)k * (long long)m) % (long long)N;
+            double ang = (double)sign * 2.0 * ORACLE_PI * (double)km / (double)N;
+            double c = cos(ang), s = sin(ang);
+            sre += in_re[m] * c - in_im[m] * s;
+            sim += in_re[m] * s + in_im[m] * c;
+        }
+        out_re[k] = sre;
+        out_im[k] = sim;
+    }
+    return 0;
+}
