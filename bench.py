@@ -1,0 +1,309 @@
+"""Benchmark: CWT coefficients per second on the fused FP32 workload.
+
+Workload (one step): 64 channels x 10,000 samples (10 s at 1000 Hz) of seeded
+synthetic EEG, float32, Morlet with n_cycles rising linearly 3 -> 10 over 100
+log-spaced frequencies 1-100 Hz, outputs complex64 coefficients and float32
+power: one cwt_execute (forward FFT of every channel + the fused scale-block
+kernel) over inputs already resident in HBM.  The wavelet bank is generated
+once at plan creation and reported separately (bank_ms).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream; between steps a 256 MB buffer (> the 129 MB L2) is
+overwritten outside the events.  N > 1 (torchrun) runs one independent
+workload per rank (weak scaling, no collective on the data path); the time is
+the max over ranks.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CWT coeffs/sec (ch x scales x samples)"
+UNIT = "coeffs/s"
+WORKLOAD = "fused"
+L2_FLUSH_BYTES = 256 << 20
+PROFILE_FILE = os.path.join(ROOT, "profiles", "scale_block_fp32_fused_64x100x10000.txt")
+KERNEL_SOURCES = ["fft_core.cuh", "scale_block.cu"]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2506_07793_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the scale-block kernel from the committed ncu
+    summary, or None when the kernel source changed since it was captured."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, x_rows, n_channels):
+    """The FP64 oracle, as it stands, on the host cores: all scales of the first
+    n_channels channels of the same workload."""
+    import oracle
+    from paper_2506_07793_gb300 import cwt_fft_length
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    N = cwt_fft_length(w.samples)
+    rows = [(c, s) for c in range(n_channels) for s in range(w.scales)]
+    t0 = time.perf_counter()
+    oracle.cwt_rows(x_rows[:n_channels].astype(np.float64), N, w.fs, w.freqs, w.n_cycles, rows,
+                    threads=cores)
+    dt = time.perf_counter() - t0
+    coeffs = len(rows) * w.n_out
+    return {"value": coeffs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_channels} of {w.channels} channels x all {w.scales} scales x "
+                      f"{w.n_out} samples ({coeffs} coefficients), {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, each step a bounded
+    sample (1 channel x all scales) of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from eeg_synth import workload
+    import oracle
+    w = workload(WORKLOAD)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    N = 1
+    while N < max(w.samples, 32):
+        N *= 2
+    x = w.signal(channels=1).astype(np.float64)
+    rows = [(0, s) for s in range(w.scales)]
+    for _ in range(args.warmup):
+        oracle.cwt_rows(x, N, w.fs, w.freqs, w.n_cycles, rows[:4], threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cwt_rows(x, N, w.fs, w.freqs, w.n_cycles, rows, threads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = len(rows) * w.n_out / dt
+    sample = f"1 of {w.channels} channels x all {w.scales} scales x {w.n_out} samples per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.notes, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-channels", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2506_07793_gb300 as cw
+    from eeg_synth import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = workload(WORKLOAD)
+    # each rank transforms its own independent recording (weak scaling)
+    x_host = w.signal(first_channel=rank * w.channels)
+    x = torch.from_numpy(x_host).cuda()
+    kinds = cw.CWT_OUT_COMPLEX | cw.CWT_OUT_POWER
+    plan = cw.cwt_plan_create(w.channels, w.samples, w.fs, w.freqs, w.n_cycles,
+                              cw.CWT_WAVELET_MORLET, kinds, cw.cwt_options_init())
+    info = cw.cwt_plan_info(plan)
+    shape = (w.channels, w.scales, w.n_out)
+    out_c = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    out_p = torch.empty(shape, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        cw.cwt_execute(plan, x, out_c, out_p, None, stream)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    cw.cwt_plan_set_profiling(plan, True)
+    cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_SCALE_BLOCK, reset=True)
+    cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_FORWARD_FFT, reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        cw.cwt_execute(plan, x, out_c, out_p, None, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    n_sb, ms_sb = cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_SCALE_BLOCK, reset=True)
+    n_fw, ms_fw = cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_FORWARD_FFT, reset=True)
+    cw.cwt_plan_set_profiling(plan, False)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    coeffs_rank = w.coefficients
+    ms_step = total_ms / args.steps
+    value = coeffs_rank * world / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel (fused scale block)
+    peaks, peak_kind = measured_peaks()
+    N = info.fft_length
+    alg_bytes = (w.channels * w.scales * w.n_out * (8 + 4)      # complex64 + float32 power out
+                 + w.channels * N * 8                              # forward spectra, read once
+                 + w.scales * N * 4)                               # wavelet bank, read once
+    sb_s = ms_sb / max(n_sb, 1) * 1e-3
+    achieved = alg_bytes / sb_s / 1e9
+    traffic = profiled_traffic()
+    roofline = {"kernel": "scale_block_kernel<16384,float>", "bound": "hbm",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
+                "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                "kernel_ms": sb_s * 1e3, "forward_fft_ms": ms_fw / max(n_fw, 1)}
+
+    # end to end through the host-buffer entry point (pinned memory)
+    h_in = torch.from_numpy(x_host).pin_memory()
+    h_c = torch.empty(shape, dtype=torch.complex64).pin_memory()
+    h_p = torch.empty(shape, dtype=torch.float32).pin_memory()
+    cw.cwt_execute_host(plan, h_in, h_c, h_p, None, stream)  # allocates staging
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        cw.cwt_execute_host(plan, h_in, h_c, h_p, None, stream)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": coeffs_rank * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(x_host.nbytes),
+           "d2h_bytes_per_step": int(h_c.numel() * 8 + h_p.numel() * 4),
+           "ms_per_step": e2e_s * 1e3}
+    cw.cwt_plan_destroy(plan)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.notes, "channels": w.channels, "samples": w.samples,
+                       "scales": w.scales, "fft_length": N, "coefficients_per_step": coeffs_rank,
+                       "l2": "256 MB buffer overwritten between timed steps (outside the events)",
+                       "bank_ms": info.bank_ms, "wall_s_timed_region": wall,
+                       "parallelism": f"weak x{world}, no collective"},
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * cwt.h -- C ABI of the GB300-native FFT-based continuous wavelet transform
+ * (CWT) of multichannel EEG, after arXiv 2506.07793 (Nakanishi, "Novel
+ * software for continuous wavelet analysis enable EEG real-time analysis on
+ * portable computers").
+ *
+ * The method (Section "Fourier transformed formula", Eq. 2): for every
+ * channel take one forward FFT of the zero-padded signal, multiply it by the
+ * analytic Fourier-domain wavelet of each scale (Morlet, Eq. 3; Gabor, Eq. 4),
+ * take one inverse FFT per (channel, scale) and reduce the result to complex
+ * coefficients, power or phase (Section "Precision").  Padding follows Section
+ * "Fast Fourier transform".  The wavelets are generated on the GPU once per
+ * plan and reused (Section "Optimizing performance").
+ *
+ * Result definition.  For signal x[0..n) of channel c, padded length N and the
+ * scale with carrier F_s (Hz) and sigma_s = n_cycles_s, the library returns
+ *     coef[c][s][o] = sum_{m<n} x[m] * w_s[(d*o - m) mod N],  o < n_out,
+ * where w_s is the N-periodised sampled Morlet wavelet normalised to unit
+ * energy, d the decimation and n_out = ceil(n/d).  power = |coef|^2 and
+ * phase = atan2(Im, Re) in (-pi, pi].  The GPU evaluates this with FFTs;
+ * the values are those of the direct cyclic convolution, up to FP32 rounding.
+ *
+ * Conventions for every function below:
+ *  - Every call returns a cwt_status and never throws or aborts across the ABI.
+ *    Output arguments are written only when CWT_OK is returned.
+ *  - "Device pointer" means memory of the plan's GPU (cudaMalloc, the torch
+ *    caching allocator, or managed memory); "host pointer" means CPU memory
+ *    (pinned memory makes the copies asynchronous-capable and faster).
+ *  - Device buffers passed to cwt_execute must be 16-byte aligned; the caller
+ *    owns them.  The plan owns its wavelet bank, tables and workspace.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is asynchronous on it; errors raised by kernels surface at the next
+ *    call that synchronises (cwt_execute_host, cwt_plan_bank, profiling reads)
+ *    or at the caller's own synchronisation.
+ *  - A plan is not thread-safe, and its executions must not overlap on the
+ *    GPU (they share the plan's spectrum workspace): issue them on one stream
+ *    or synchronise in between.  Different plans are independent.
+ *  - Layouts are row-major: signal [C][n]; every output [C][S][n_out].
+ *    Complex outputs are interleaved (re, im) pairs of the I/O type.
+ */
+#ifndef CWT_GB300_CWT_H
+#define CWT_GB300_CWT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cwt_plan_s *cwt_plan; /* opaque; created and freed by the library */
+
+typedef enum {
+    CWT_OK = 0,
+    CWT_EINVAL = 1,        /* bad argument (value, pointer kind, alignment) */
+    CWT_ENOMEM = 2,        /* device or host allocation failed */
+    CWT_EUNSUPPORTED = 3,  /* valid request that this build does not implement */
+    CWT_ECUDA = 4,         /* a CUDA runtime call failed (see cwt_plan_last_error) */
+    CWT_EAGAIN = 5,        /* not enough data yet / nothing ready */
+    CWT_EBUSY = 6,         /* admission refused: no slot or memory budget */
+    CWT_ETIMEDOUT = 7,     /* a bounded device wait gave up */
+    CWT_EDEVICE = 8        /* the device reported an error status */
+} cwt_status;
+
+typedef enum {
+    CWT_WAVELET_MORLET = 0, /* Eq. 3 */
+    CWT_WAVELET_GABOR = 1,  /* Eq. 4 (Morlet without the admissibility term) */
+    CWT_WAVELET_GMW = 2     /* Eq. 5: not implemented (CWT_EUNSUPPORTED) */
+} cwt_wavelet;
+
+/* Output kinds, a bitmask (Section "Precision": real/imaginary, phase, power). */
+enum { CWT_OUT_COMPLEX = 1u, CWT_OUT_POWER = 2u, CWT_OUT_PHASE = 4u };
+
+typedef enum { CWT_PREC_FP32 = 0, CWT_PREC_TC_FP16 = 1, CWT_PREC_TC_BF16 = 2 } cwt_precision;
+typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
+
+/* Padding policy (Section "Fast Fourier transform").  POW2 pads to the next
+ * power of two (the choice the paper attributes to MNE-python).  SMOOTH, the
+ * paper's own policy (smallest 2,3,5,7-smooth length), is not implemented. */
+typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
+
+/* Kernel identifiers for the profiling counters. */
+typedef enum {
+    CWT_KERNEL_BANK = 0,        /* wavelet-bank + band generation (plan creation) */
+    CWT_KERNEL_FORWARD_FFT = 1, /* per-channel forward FFT */
+    CWT_KERNEL_SCALE_BLOCK = 2, /* fused multiply + inverse FFT + reduce + store */
+    CWT_KERNEL_COUNT = 3
+} cwt_kernel_id;
+
+typedef struct {
+    int precision;  /* cwt_precision; only CWT_PREC_FP32 is implemented */
+    int decimation; /* keep every d-th output sample, d >= 1 (default 1) */
+    int pad_policy; /* cwt_pad_policy (default CWT_PAD_POW2) */
+    int fft_length; /* 0: from pad_policy; else an explicit N >= samples that is a
+                       power of two the build supports (see cwt_fft_length) */
+    int io_dtype;   /* cwt_dtype of the signal and of every output (default F32);
+                       F64 is converted to FP32 on load and back on store */
+    int reserved[11];
+} cwt_options;
+
+typedef struct {
+    int channels, samples, scales;
+    int fft_length;     /* N */
+    int n_out;          /* ceil(samples / decimation) */
+    int decimation;
+    int fold;           /* spectral fold factor f (power of two dividing d) */
+    int inverse_length; /* N / fold: size of each inverse FFT */
+    int device;         /* CUDA ordinal the plan lives on */
+    int io_dtype;
+    unsigned output_kinds;
+    size_t workspace_bytes; /* device bytes owned by the plan */
+    double bank_ms;         /* GPU time of the bank generation at creation */
+} cwt_plan_info_t;
+
+/* Human-readable name of a status.  Never NULL. */
+const char *cwt_status_str(cwt_status s);
+
+/* Fill *opt with defaults (FP32, d=1, POW2, N from policy, F32 I/O). */
+cwt_status cwt_options_init(cwt_options *opt);
+
+/* Padded FFT length N for `samples` under `pad_policy` (Section "Fast Fourier
+ * transform"): the next power of two >= max(samples, 32).  Writes *n_fft.
+ * CWT_EINVAL if samples < 1; CWT_EUNSUPPORTED if the policy is not built or
+ * N exceeds the largest supported length (2^14).  Host-only; no CUDA call. */
+cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
+
+/*
+ * cwt_plan_create -- validate, pick N, allocate the plan's device memory on
+ * the current CUDA device and generate the wavelet bank there in FP64
+ * (Eq. 3/Eq. 4 summed over aliases, normalised to unit energy, rounded to
+ * FP32) together with each scale's non-negligible band (Section "Optimizing
+ * performance": wavelets are generated in GPU memory first).
+ *   channels, samples  C >= 1, n >= 1
+ *   fs                 sampling rate in Hz, > 0
+ *   freqs_hz[n_freqs]  host array, each 0 < F < fs/2
+ *   n_cycles[n_freqs]  host array, each > 0 (sigma of Eq. 3)
+ *   wavelet            cwt_wavelet
+ *   output_kinds       non-empty subset of CWT_OUT_*
+ *   opt                NULL for defaults
+ * On CWT_OK *out holds a new plan (free with cwt_plan_destroy).  Argument
+ * errors are reported before any CUDA call.  Blocks until the bank is built.
+ */
+cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
+                           const double *freqs_hz, int n_freqs, const double *n_cycles,
+                           int wavelet, unsigned output_kinds, const cwt_options *opt);
+
+/* Free the plan and its device memory (synchronises the device work of the
+ * plan first).  NULL is accepted. */
+cwt_status cwt_plan_destroy(cwt_plan plan);
+
+/* Describe the plan (host-only, no synchronisation). */
+cwt_status cwt_plan_info(cwt_plan plan, cwt_plan_info_t *info);
+
+/* Device bytes owned by the plan (0 for NULL). */
+size_t cwt_plan_workspace_bytes(cwt_plan plan);
+
+/* Text of the last CUDA error the plan saw ("" if none).  Never NULL. */
+const char *cwt_plan_last_error(cwt_plan plan);
+
+/*
+ * cwt_execute -- the hot path (Eq. 2): forward FFT of every channel, then one
+ * fused kernel per scale block that multiplies by the wavelet spectrum,
+ * inverse-FFTs on chip, reduces and stores only the requested outputs.
+ *   d_signal  device [C][n] of io_dtype
+ *   d_complex device [C][S][n_out] complex (2 x io_dtype), or NULL
+ *   d_power   device [C][S][n_out] io_dtype, or NULL
+ *   d_phase   device [C][S][n_out] io_dtype, or NULL
+ * Exactly the kinds given at plan creation must be non-NULL.  Pointers must
+ * be device memory of the plan's GPU and 16-byte aligned (else CWT_EINVAL).
+ * Asynchronous on `stream`.
+ */
+cwt_status cwt_execute(cwt_plan plan, const void *d_signal, void *d_complex, void *d_power,
+                       void *d_phase, void *stream);
+
+/*
+ * cwt_execute_host -- the same transform with HOST buffers: copies the signal
+ * to the plan's device staging buffer, runs cwt_execute on `stream`, copies
+ * the requested outputs back and waits for them.  Staging buffers are
+ * allocated on the first call and kept by the plan.  Same layouts as
+ * cwt_execute.  Returns when the outputs are in host memory.
+ */
+cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex, void *h_power,
+                            void *h_phase, void *stream);
+
+/*
+ * cwt_plan_bank -- copy the plan's wavelet bank to host memory (synchronous).
+ *   h_bank        [S][N] float32: the real spectrum W_s[k] / N actually used
+ *                 (the 1/N of the inverse FFT is folded in), or NULL
+ *   h_band_start  [S] first bin of each scale's band (0..N-1), or NULL
+ *   h_band_len    [S] number of bins in the band (the band wraps mod N), or NULL
+ * Bins outside the band hold values below 1e-10 of the scale's peak and are
+ * skipped by the kernels.
+ */
+cwt_status cwt_plan_bank(cwt_plan plan, float *h_bank, int *h_band_start, int *h_band_len);
+
+/*
+ * cwt_fft -- batched, unnormalised complex FFT with the library's Stockham
+ * kernels (a building block, exposed for testing and reuse).
+ *   d_in, d_out  device [batch][n] complex64, 16-byte aligned; may alias
+ *   n            power of two, 32 <= n <= 16384
+ *   direction    -1: sum x[m] e^{-2 pi i k m / n};  +1: e^{+2 pi i ...}
+ * Asynchronous on `stream`.
+ */
+cwt_status cwt_fft(const void *d_in, void *d_out, int n, int batch, int direction, void *stream);
+
+/*
+ * Profiling (Section "Comparison between devices and software" times each
+ * method; here each kernel is timed with CUDA events on its own stream).
+ * cwt_plan_set_profiling(plan, 1) makes every later launch of the plan record
+ * an event pair on its stream; cwt_plan_profile_read waits for the recorded
+ * events of `kernel` (a cwt_kernel_id), returns their count and summed
+ * milliseconds, and with reset != 0 forgets them.
+ */
+cwt_status cwt_plan_set_profiling(cwt_plan plan, int enable);
+cwt_status cwt_plan_profile_read(cwt_plan plan, int kernel, int *launches, double *total_ms,
+                                 int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CWT_GB300_CWT_H */

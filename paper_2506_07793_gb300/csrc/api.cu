@@ -1,0 +1,402 @@
+// api.cu -- the library's C ABI (include/cwt.h): argument validation, plan
+// lifecycle, execution entry points and profiling counters.
+//
+// Plan creation follows Section "Optimizing performance" of arXiv 2506.07793:
+// the Fourier-transformed wavelets are generated in GPU memory once, then data
+// are transformed there, and results leave the GPU only when asked for.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+using cwtk::ilog2c;
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+cwt_status fail_cuda(cwt_plan_s *p, cudaError_t e) {
+    if (p) p->last_error = cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return CWT_ENOMEM;
+    return CWT_ECUDA;
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Device pointer of the given device, 16-byte aligned.
+bool device_ptr_ok(const void *ptr, int dev) {
+    if (!ptr || (reinterpret_cast<uintptr_t>(ptr) & 15u)) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the non-sticky error
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+cudaError_t prof_begin(cwt_plan_s *p, int kernel, cudaStream_t st, cwtk::ProfEvent *ev) {
+    if (!p->profiling) return cudaSuccess;
+    if (p->prof_pool.empty()) {
+        cwtk::ProfEvent e{};
+        cudaError_t r = cudaEventCreate(&e.start);
+        if (r == cudaSuccess) r = cudaEventCreate(&e.stop);
+        if (r != cudaSuccess) return r;
+        p->prof_pool.push_back(e);
+    }
+    *ev = p->prof_pool.back();
+    p->prof_pool.pop_back();
+    ev->kernel = kernel;
+    return cudaEventRecord(ev->start, st);
+}
+
+cudaError_t prof_end(cwt_plan_s *p, cudaStream_t st, cwtk::ProfEvent *ev) {
+    if (!p->profiling) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(ev->stop, st);
+    p->prof.push_back(*ev);
+    return r;
+}
+
+size_t out_elem_bytes(const cwt_plan_s *p) { return p->io == CWT_DTYPE_F64 ? 8 : 4; }
+
+cwt_status run_execute(cwt_plan_s *p, const void *sig, void *oc, void *op, void *oph,
+                       cudaStream_t st) {
+    cwtk::ProfEvent ev{};
+    cudaError_t e = prof_begin(p, CWT_KERNEL_FORWARD_FFT, st, &ev);
+    if (e == cudaSuccess) e = cwtk::launch_forward(p, sig, st);
+    if (e == cudaSuccess) e = prof_end(p, st, &ev);
+    if (e == cudaSuccess) e = prof_begin(p, CWT_KERNEL_SCALE_BLOCK, st, &ev);
+    if (e == cudaSuccess) e = cwtk::launch_scale_block(p, oc, op, oph, st);
+    if (e == cudaSuccess) e = prof_end(p, st, &ev);
+    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+}
+
+void free_plan_memory(cwt_plan_s *p) {
+    cudaFree(p->bank);
+    cudaFree(p->band);
+    cudaFree(p->spec);
+    cudaFree(p->stage_in);
+    cudaFree(p->stage_c);
+    cudaFree(p->stage_p);
+    cudaFree(p->stage_ph);
+    for (auto &e : p->prof) {
+        cudaEventDestroy(e.start);
+        cudaEventDestroy(e.stop);
+    }
+    for (auto &e : p->prof_pool) {
+        cudaEventDestroy(e.start);
+        cudaEventDestroy(e.stop);
+    }
+    p->prof.clear();
+    p->prof_pool.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cwt_status_str(cwt_status s) {
+    switch (s) {
+        case CWT_OK: return "CWT_OK";
+        case CWT_EINVAL: return "CWT_EINVAL: invalid argument";
+        case CWT_ENOMEM: return "CWT_ENOMEM: out of memory";
+        case CWT_EUNSUPPORTED: return "CWT_EUNSUPPORTED: not supported by this build";
+        case CWT_ECUDA: return "CWT_ECUDA: CUDA runtime error";
+        case CWT_EAGAIN: return "CWT_EAGAIN: not ready";
+        case CWT_EBUSY: return "CWT_EBUSY: admission refused";
+        case CWT_ETIMEDOUT: return "CWT_ETIMEDOUT: device wait timed out";
+        case CWT_EDEVICE: return "CWT_EDEVICE: device reported an error";
+    }
+    return "CWT_UNKNOWN_STATUS";
+}
+
+cwt_status cwt_options_init(cwt_options *opt) {
+    if (!opt) return CWT_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = CWT_PREC_FP32;
+    opt->decimation = 1;
+    opt->pad_policy = CWT_PAD_POW2;
+    opt->fft_length = 0;
+    opt->io_dtype = CWT_DTYPE_F32;
+    return CWT_OK;
+}
+
+cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft) {
+    if (!n_fft || samples < 1) return CWT_EINVAL;
+    if (pad_policy != CWT_PAD_POW2) return pad_policy == CWT_PAD_SMOOTH ? CWT_EUNSUPPORTED : CWT_EINVAL;
+    if (samples > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+    int N = cwtk::kMinFft;
+    while (N < samples) N <<= 1;
+    *n_fft = N;
+    return CWT_OK;
+}
+
+cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
+                           const double *freqs_hz, int n_freqs, const double *n_cycles,
+                           int wavelet, unsigned output_kinds, const cwt_options *opt) {
+    // ---- host-side validation (no CUDA call before this block ends) ----
+    if (!out || channels < 1 || samples < 1 || !(fs > 0.0) || !std::isfinite(fs) || !freqs_hz ||
+        !n_cycles || n_freqs < 1)
+        return CWT_EINVAL;
+    for (int i = 0; i < n_freqs; ++i) {
+        if (!(freqs_hz[i] > 0.0) || !(freqs_hz[i] < 0.5 * fs) || !std::isfinite(freqs_hz[i]))
+            return CWT_EINVAL;
+        if (!(n_cycles[i] > 0.0) || !std::isfinite(n_cycles[i])) return CWT_EINVAL;
+    }
+    if (wavelet != CWT_WAVELET_MORLET && wavelet != CWT_WAVELET_GABOR)
+        return wavelet == CWT_WAVELET_GMW ? CWT_EUNSUPPORTED : CWT_EINVAL;
+    const unsigned all = CWT_OUT_COMPLEX | CWT_OUT_POWER | CWT_OUT_PHASE;
+    if (output_kinds == 0 || (output_kinds & ~all)) return CWT_EINVAL;
+    cwt_options o;
+    cwt_options_init(&o);
+    if (opt) o = *opt;
+    if (o.decimation < 1) return CWT_EINVAL;
+    if (o.io_dtype != CWT_DTYPE_F32 && o.io_dtype != CWT_DTYPE_F64) return CWT_EINVAL;
+    if (o.precision != CWT_PREC_FP32) {
+        if (o.precision == CWT_PREC_TC_FP16 || o.precision == CWT_PREC_TC_BF16) return CWT_EUNSUPPORTED;
+        return CWT_EINVAL;
+    }
+    int N = 0;
+    if (o.fft_length != 0) {
+        if (o.fft_length < samples || !is_pow2(o.fft_length) || o.fft_length < cwtk::kMinFft)
+            return CWT_EINVAL;
+        if (o.fft_length > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+        N = o.fft_length;
+    } else {
+        cwt_status st = cwt_fft_length(samples, o.pad_policy, &N);
+        if (st != CWT_OK) return st;
+    }
+    if ((long long)channels * n_freqs > (1ll << 30)) return CWT_EUNSUPPORTED;
+
+    cwt_plan_s *p = new (std::nothrow) cwt_plan_s();
+    if (!p) return CWT_ENOMEM;
+    p->C = channels;
+    p->n = samples;
+    p->S = n_freqs;
+    p->N = N;
+    p->d = o.decimation;
+    int f = 1;
+    while ((p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
+    p->fold = f;
+    p->M = N / f;
+    p->sub = p->d / f;
+    p->n_out = (samples + p->d - 1) / p->d;
+    p->fs = fs;
+    p->wavelet = wavelet;
+    p->outputs = output_kinds;
+    p->io = o.io_dtype;
+    p->freqs.assign(freqs_hz, freqs_hz + n_freqs);
+    p->cycles.assign(n_cycles, n_cycles + n_freqs);
+
+    // ---- device side ----
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cwtk::device_twiddles(&p->tw);
+    const size_t bank_b = sizeof(float) * (size_t)n_freqs * N;
+    const size_t band_b = sizeof(int) * 2 * (size_t)n_freqs;
+    const size_t spec_b = sizeof(float2) * (size_t)channels * N;
+    if (e == cudaSuccess) e = cudaMalloc(&p->bank, bank_b);
+    if (e == cudaSuccess) e = cudaMalloc(&p->band, band_b);
+    if (e == cudaSuccess) e = cudaMalloc(&p->spec, spec_b);
+    p->bytes = bank_b + band_b + spec_b;
+    cudaStream_t st = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        cwt_status s = fail_cuda(p, e);
+        free_plan_memory(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return CWT_OK;
+}
+
+cwt_status cwt_plan_destroy(cwt_plan p) {
+    if (!p) return CWT_OK;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        free_plan_memory(p);
+    }
+    delete p;
+    return CWT_OK;
+}
+
+cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
+    if (!p || !info) return CWT_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->channels = p->C;
+    info->samples = p->n;
+    info->scales = p->S;
+    info->fft_length = p->N;
+    info->n_out = p->n_out;
+    info->decimation = p->d;
+    info->fold = p->fold;
+    info->inverse_length = p->M;
+    info->device = p->device;
+    info->io_dtype = p->io;
+    info->output_kinds = p->outputs;
+    info->workspace_bytes = p->bytes + p->stage_bytes;
+    info->bank_ms = p->bank_ms;
+    return CWT_OK;
+}
+
+size_t cwt_plan_workspace_bytes(cwt_plan p) { return p ? p->bytes + p->stage_bytes : 0; }
+
+const char *cwt_plan_last_error(cwt_plan p) { return p ? p->last_error.c_str() : ""; }
+
+cwt_status cwt_execute(cwt_plan p, const void *d_signal, void *d_complex, void *d_power,
+                       void *d_phase, void *stream) {
+    if (!p) return CWT_EINVAL;
+    const bool wc = p->outputs & CWT_OUT_COMPLEX, wp = p->outputs & CWT_OUT_POWER,
+               wph = p->outputs & CWT_OUT_PHASE;
+    if (wc != (d_complex != nullptr) || wp != (d_power != nullptr) || wph != (d_phase != nullptr))
+        return CWT_EINVAL;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWT_ECUDA;
+    if (!device_ptr_ok(d_signal, p->device)) return CWT_EINVAL;
+    if (wc && !device_ptr_ok(d_complex, p->device)) return CWT_EINVAL;
+    if (wp && !device_ptr_ok(d_power, p->device)) return CWT_EINVAL;
+    if (wph && !device_ptr_ok(d_phase, p->device)) return CWT_EINVAL;
+    return run_execute(p, d_signal, d_complex, d_power, d_phase, (cudaStream_t)stream);
+}
+
+cwt_status cwt_execute_host(cwt_plan p, const void *h_signal, void *h_complex, void *h_power,
+                            void *h_phase, void *stream) {
+    if (!p || !h_signal) return CWT_EINVAL;
+    const bool wc = p->outputs & CWT_OUT_COMPLEX, wp = p->outputs & CWT_OUT_POWER,
+               wph = p->outputs & CWT_OUT_PHASE;
+    if (wc != (h_complex != nullptr) || wp != (h_power != nullptr) || wph != (h_phase != nullptr))
+        return CWT_EINVAL;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWT_ECUDA;
+    const size_t eb = out_elem_bytes(p);
+    const size_t in_b = eb * (size_t)p->C * p->n;
+    const size_t out_b = eb * (size_t)p->C * p->S * p->n_out;
+    cudaError_t e = cudaSuccess;
+    if (!p->stage_in) {
+        e = cudaMalloc(&p->stage_in, in_b);
+        if (e == cudaSuccess && wc) e = cudaMalloc(&p->stage_c, 2 * out_b);
+        if (e == cudaSuccess && wp) e = cudaMalloc(&p->stage_p, out_b);
+        if (e == cudaSuccess && wph) e = cudaMalloc(&p->stage_ph, out_b);
+        if (e != cudaSuccess) {
+            cudaFree(p->stage_in);
+            cudaFree(p->stage_c);
+            cudaFree(p->stage_p);
+            cudaFree(p->stage_ph);
+            p->stage_in = p->stage_c = p->stage_p = p->stage_ph = nullptr;
+            return fail_cuda(p, e);
+        }
+        p->stage_bytes = in_b + (wc ? 2 * out_b : 0) + (wp ? out_b : 0) + (wph ? out_b : 0);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(p->stage_in, h_signal, in_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail_cuda(p, e);
+    cwt_status s = run_execute(p, p->stage_in, wc ? p->stage_c : nullptr, wp ? p->stage_p : nullptr,
+                               wph ? p->stage_ph : nullptr, st);
+    if (s != CWT_OK) return s;
+    if (wc) e = cudaMemcpyAsync(h_complex, p->stage_c, 2 * out_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && wp) e = cudaMemcpyAsync(h_power, p->stage_p, out_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && wph)
+        e = cudaMemcpyAsync(h_phase, p->stage_ph, out_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+}
+
+cwt_status cwt_plan_bank(cwt_plan p, float *h_bank, int *h_band_start, int *h_band_len) {
+    if (!p) return CWT_EINVAL;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWT_ECUDA;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && h_bank)
+        e = cudaMemcpy(h_bank, p->bank, sizeof(float) * (size_t)p->S * p->N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && (h_band_start || h_band_len)) {
+        int *tmp = new (std::nothrow) int[2 * (size_t)p->S];
+        if (!tmp) return CWT_ENOMEM;
+        e = cudaMemcpy(tmp, p->band, sizeof(int) * 2 * (size_t)p->S, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (int s = 0; s < p->S; ++s) {
+                if (h_band_start) h_band_start[s] = tmp[2 * s];
+                if (h_band_len) h_band_len[s] = tmp[2 * s + 1];
+            }
+        delete[] tmp;
+    }
+    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+}
+
+cwt_status cwt_fft(const void *d_in, void *d_out, int n, int batch, int direction, void *stream) {
+    if (!d_in || !d_out || batch < 0 || !is_pow2(n) || (direction != 1 && direction != -1))
+        return CWT_EINVAL;
+    if (n < cwtk::kMinFft || n > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+    if (batch == 0) return CWT_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CWT_ECUDA;
+    if (!device_ptr_ok(d_in, dev) || !device_ptr_ok(d_out, dev)) return CWT_EINVAL;
+    const float2 *tw = nullptr;
+    cudaError_t e = cwtk::device_twiddles(&tw);
+    if (e == cudaSuccess)
+        e = cwtk::launch_fft((const float2 *)d_in, (float2 *)d_out, ilog2c(n), batch, direction, tw,
+                             (cudaStream_t)stream);
+    if (e == cudaErrorMemoryAllocation) return CWT_ENOMEM;
+    return e == cudaSuccess ? CWT_OK : CWT_ECUDA;
+}
+
+cwt_status cwt_plan_set_profiling(cwt_plan p, int enable) {
+    if (!p) return CWT_EINVAL;
+    p->profiling = enable != 0;
+    return CWT_OK;
+}
+
+cwt_status cwt_plan_profile_read(cwt_plan p, int kernel, int *launches, double *total_ms, int reset) {
+    if (!p || kernel < 0 || kernel >= CWT_KERNEL_COUNT) return CWT_EINVAL;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWT_ECUDA;
+    int cnt = 0;
+    double ms = 0.0;
+    if (kernel == CWT_KERNEL_BANK) {
+        cnt = 1;
+        ms = p->bank_ms;
+    } else {
+        for (auto &ev : p->prof) {
+            if (ev.kernel != kernel) continue;
+            cudaError_t e = cudaEventSynchronize(ev.stop);
+            float f = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&f, ev.start, ev.stop);
+            if (e != cudaSuccess) return fail_cuda(p, e);
+            ms += f;
+            ++cnt;
+        }
+        if (reset) {
+            std::vector<cwtk::ProfEvent> keep;
+            for (auto &ev : p->prof) {
+                if (ev.kernel == kernel)
+                    p->prof_pool.push_back(ev);
+                else
+                    keep.push_back(ev);
+            }
+            p->prof.swap(keep);
+        }
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    return CWT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+// fft_core.cuh -- Stockham FFT building blocks for sm_103a.
+//
+// The CWT of arXiv 2506.07793 evaluates the cyclic convolution with one
+// forward FFT per channel and one inverse FFT per (channel, scale) (Section
+// "Fourier transformed formula", Eq. 2); the paper leans on Cooley-Tukey
+// factorisations (Section "Fast Fourier transform").  This header holds the
+// radix-R Stockham passes used by every kernel of the library:
+//
+//  * A row of length N is handled by T = N / R threads; each thread keeps R
+//    complex values in registers.
+//  * Pass p (Ns = R^p, radix Rp): thread j owns butterflies jj = j + g*T.  It
+//    multiplies input r by w^r with w = exp(+-2 pi i (jj mod Ns) / (Ns Rp)),
+//    runs an Rp-point DFT in registers and writes output r to position
+//    (jj - jj mod Ns) * Rp + (jj mod Ns) + r * Ns.  This is the self-sorting
+//    (Stockham) decimation-in-time order: the last pass writes natural order.
+//  * Between passes the row is exchanged through shared memory as separate
+//    re/im float arrays with one pad word per 32 (bank-conflict-free for the
+//    power-of-two strides used here).
+//  * The first pass reads its inputs through a caller functor (global memory,
+//    fused pre-processing) and the last pass hands each output to a caller
+//    functor (fused epilogue), so neither end touches shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cwtk {
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
+// Twiddle table: tw[m] = exp(+2 pi i m / kTwN), m < kTwN, generated in FP64 and
+// rounded to FP32 (one table per device, shared by every plan).
+constexpr int kTwLog2 = 17;
+constexpr int kTwN = 1 << kTwLog2;
+
+// Shared-memory padding: one extra word every 32 words.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int spad_size(int n) { return n + (n >> 5); }
+
+// cos(2 pi j / 32), j = 0..8 (first quadrant), as exact-to-float literals.
+__host__ __device__ constexpr float cos_q32(int j) {
+    return j == 0 ? 1.0f
+         : j == 1 ? 0.980785280403230449126f
+         : j == 2 ? 0.923879532511286756128f
+         : j == 3 ? 0.831469612302545237079f
+         : j == 4 ? 0.707106781186547524401f
+         : j == 5 ? 0.555570233019602224743f
+         : j == 6 ? 0.382683432365089771728f
+         : j == 7 ? 0.195090322016128267848f
+                  : 0.0f;
+}
+// cos(2 pi m / 32) and sin(2 pi m / 32) for any integer m.
+__host__ __device__ constexpr float cos32(int m) {
+    return ((m & 31) >> 3) == 0 ? cos_q32(m & 7)
+         : ((m & 31) >> 3) == 1 ? -cos_q32(8 - (m & 7))
+         : ((m & 31) >> 3) == 2 ? -cos_q32(m & 7)
+                                : cos_q32(8 - (m & 7));
+}
+__host__ __device__ constexpr float sin32(int m) { return cos32(m + 24); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// a * exp(SIGN * 2 pi i * m / 32) with m known at compile time after unrolling;
+// the trivial roots reduce to swaps and negations, the eighth roots to one
+// multiply per component.
+template <int SIGN>
+__device__ __forceinline__ float2 rot32(float2 a, int m) {
+    m &= 31;
+    if (m == 0) return a;
+    if (m == 16) return make_float2(-a.x, -a.y);
+    if (m == 8) return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    if (m == 24) return SIGN > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    const float c = cos32(m), s = SIGN > 0 ? sin32(m) : -sin32(m);
+    if ((m & 7) == 4) {  // |c| = |s| = sqrt(2)/2: signs fold away at compile time
+        const float h = 0.707106781186547524401f;
+        const float sc = c > 0.f ? 1.f : -1.f, ss = s > 0.f ? 1.f : -1.f;
+        return make_float2(h * (sc * a.x - ss * a.y), h * (ss * a.x + sc * a.y));
+    }
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+}
+
+__host__ __device__ constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// In-register DFT of R = 2..32 points, natural order in and out:
+// X[k] = sum_m v[m] exp(SIGN 2 pi i k m / R).  Radix-2 decimation in frequency
+// with compile-time twiddles, then a compile-time bit-reversal (register
+// renaming only).
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(float2 *v) {
+    static_assert(R >= 1 && R <= 32 && (R & (R - 1)) == 0, "radix must be a power of two <= 32");
+    constexpr int L2 = ilog2c(R);
+#pragma unroll
+    for (int stage = 0; stage < L2; ++stage) {
+        const int half = R >> (stage + 1);
+#pragma unroll
+        for (int base = 0; base < R; base += 2 * half) {
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const float2 a = v[base + k], b = v[base + k + half];
+                v[base + k] = cadd(a, b);
+                v[base + k + half] = rot32<SIGN>(csub(a, b), k * (32 / (2 * half)));
+            }
+        }
+    }
+    float2 t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, L2)];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// v[r] *= w^r for r = 1..Rp-1.  The low powers w^1..w^7 come from a
+// square-and-multiply chain; higher powers are w^(8h) * w^(r mod 8), so each
+// factor is at most ~6 roundings from exact and only ~10 twiddles are live.
+template <int Rp>
+__device__ __forceinline__ void twiddle_chain(float2 *v, float2 w1) {
+    constexpr int LO = Rp < 8 ? Rp : 8;
+    float2 wl[LO];
+    wl[0] = make_float2(1.f, 0.f);
+    if (LO > 1) wl[1] = w1;
+#pragma unroll
+    for (int r = 2; r < LO; ++r) wl[r] = (r & 1) ? cmul(wl[r - 1], w1) : cmul(wl[r >> 1], wl[r >> 1]);
+#pragma unroll
+    for (int r = 1; r < LO; ++r) v[r] = cmul(v[r], wl[r]);
+    if constexpr (Rp > 8) {
+        const float2 w8 = cmul(wl[4], wl[4]);
+        float2 wh = w8;
+#pragma unroll
+        for (int h = 1; h < Rp / 8; ++h) {
+            v[8 * h] = cmul(v[8 * h], wh);
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[8 * h + r] = cmul(cmul(v[8 * h + r], wh), wl[r]);
+            if (h + 1 < Rp / 8) wh = cmul(wh, w8);
+        }
+    }
+}
+
+// Pass schedule for a row of N points, R points per thread.
+template <int N, int R>
+struct FftShape {
+    static constexpr int T = N / R;  // threads per row
+    static constexpr int L2N = ilog2c(N);
+    static constexpr int L2R = ilog2c(R);
+    static constexpr int NP = (L2N + L2R - 1) / L2R;  // number of passes
+    static constexpr int LAST_L2 = L2N - (NP - 1) * L2R;
+    static constexpr int SMEM_FLOATS = 2 * spad_size(N);  // re + im, padded
+    __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? R : (1 << LAST_L2); }
+    __host__ __device__ static constexpr int ns(int p) { return 1 << (p * L2R); }
+    static_assert((1 << L2N) == N && (1 << L2R) == R && R <= N, "power-of-two sizes only");
+};
+
+// Load the inputs of pass 0 through `load(index)` (index in [0, N)).
+template <int N, int R, typename Load>
+__device__ __forceinline__ void fft_load_first(float2 (&v)[R], int j, Load &load) {
+    using S = FftShape<N, R>;
+    constexpr int R0 = S::radix(0), G0 = R / R0;
+#pragma unroll
+    for (int g = 0; g < G0; ++g)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[g * R0 + r] = load(j + g * S::T + r * (N / R0));
+}
+
+// Pass P of the Stockham FFT, then (recursively) the remaining passes.  The
+// outputs of the last pass go to `store(t, value)` with t in [0, N) natural
+// order.  `tw` is the device twiddle table (kTwN entries).
+template <int N, int R, int SIGN, int P>
+struct StockhamPass {
+    template <typename Store>
+    __device__ __forceinline__ static void run(float2 (&v)[R], float *__restrict__ sre,
+                                               float *__restrict__ sim,
+                                               const float2 *__restrict__ tw, int j, Store &store) {
+        using S = FftShape<N, R>;
+        constexpr int Rp = S::radix(P), G = R / Rp, Ns = S::ns(P), T = S::T;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (Ns > 1) {
+                const int k = (j + g * T) & (Ns - 1);
+                float2 w1 = __ldg(&tw[k * (kTwN / (Ns * Rp))]);
+                if (SIGN < 0) w1.y = -w1.y;
+                twiddle_chain<Rp>(&v[g * Rp], w1);
+            }
+            dft<Rp, SIGN>(&v[g * Rp]);
+        }
+        if constexpr (P == S::NP - 1) {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) store(j + g * T + r * Ns, v[g * Rp + r]);
+        } else {
+            __syncthreads();  // every thread has finished reading the previous exchange
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int jj = j + g * T;
+                const int k = jj & (Ns - 1);
+                const int base = (jj - k) * Rp + k;
+#pragma unroll
+                for (int r = 0; r < Rp; ++r) {
+                    const int idx = spad(base + r * Ns);
+                    sre[idx] = v[g * Rp + r].x;
+                    sim[idx] = v[g * Rp + r].y;
+                }
+            }
+            __syncthreads();
+            constexpr int Rq = S::radix(P + 1), Gq = R / Rq;
+#pragma unroll
+            for (int g = 0; g < Gq; ++g)
+#pragma unroll
+                for (int r = 0; r < Rq; ++r) {
+                    const int idx = spad(j + g * T + r * (N / Rq));
+                    v[g * Rq + r] = make_float2(sre[idx], sim[idx]);
+                }
+            StockhamPass<N, R, SIGN, P + 1>::run(v, sre, sim, tw, j, store);
+        }
+    }
+};
+
+// Whole-row FFT: load -> passes -> store.  All threads of the CTA must call
+// it together (it contains __syncthreads).
+template <int N, int R, int SIGN, typename Load, typename Store>
+__device__ __forceinline__ void fft_row(float *__restrict__ sre, float *__restrict__ sim,
+                                        const float2 *__restrict__ tw, int j, Load &load,
+                                        Store &store) {
+    float2 v[R];
+    fft_load_first<N, R>(v, j, load);
+    StockhamPass<N, R, SIGN, 0>::run(v, sre, sim, tw, j, store);
+}
+
+// Launch shape for a row kernel of size N: R points per thread, several rows
+// per CTA for short rows so that a CTA has at least 256 threads.
+template <int N>
+struct RowConfig {
+    static constexpr int R = N >= 16384 ? 32 : (N >= 16 ? 16 : N);
+    static constexpr int T = N / R;
+    static constexpr int ROWS = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = T * ROWS;
+    static constexpr int SMEM_BYTES = ROWS * FftShape<N, R>::SMEM_FLOATS * 4;
+};
+
+}  // namespace cwtk

@@ -1,0 +1,83 @@
+// internal.h -- plan state and kernel launchers shared by the library's
+// translation units (not part of the public ABI; see include/cwt.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cwt.h"
+
+namespace cwtk {
+
+constexpr int kMinFft = 32;        // smallest padded length (keeps radix passes >= 2)
+constexpr int kMaxFftLog2 = 14;    // largest single-pass length 16384 (shared-memory row)
+constexpr int kMaxFft = 1 << kMaxFftLog2;
+constexpr double kBandRelThreshold = 1e-10;  // bins below this fraction of a scale's peak are skipped
+
+// Per-device FP32 twiddle table exp(2 pi i m / 2^17), built in FP64 on first use.
+cudaError_t device_twiddles(const float2 **out);
+
+struct ProfEvent {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace cwtk
+
+struct cwt_plan_s {
+    int device = 0;
+    int C = 0, n = 0, S = 0;
+    int N = 0;        // padded forward length
+    int d = 1;        // decimation
+    int fold = 1;     // spectral fold factor (power of two dividing d)
+    int M = 0;        // inverse length N / fold
+    int sub = 1;      // d / fold: remaining subsampling of the inverse output
+    int n_out = 0;
+    double fs = 0;
+    int wavelet = 0;
+    unsigned outputs = 0;
+    int io = CWT_DTYPE_F32;
+    std::vector<double> freqs, cycles;
+
+    float *bank = nullptr;    // [S][N] W_s[k] / N (real)
+    int *band = nullptr;      // [S][2]: start, length
+    float2 *spec = nullptr;   // [C][N] forward spectra (workspace)
+    const float2 *tw = nullptr;
+    size_t bytes = 0;
+    double bank_ms = 0;
+
+    // host-buffer execution staging (allocated on first use)
+    void *stage_in = nullptr, *stage_c = nullptr, *stage_p = nullptr, *stage_ph = nullptr;
+    size_t stage_bytes = 0;
+
+    bool profiling = false;
+    std::vector<cwtk::ProfEvent> prof, prof_pool;
+    std::string last_error;
+};
+
+namespace cwtk {
+
+// Opt a kernel into `bytes` of dynamic shared memory once per device
+// (one bit of *done per device ordinal < 32; setting it twice is harmless).
+template <typename K>
+cudaError_t ensure_smem_attr(K *kernel, int bytes, unsigned *done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 32 && (*done & (1u << dev))) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev < 32) *done |= 1u << dev;
+    return e;
+}
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st);
+cudaError_t launch_forward(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+cudaError_t launch_scale_block(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
+                               cudaStream_t st);
+cudaError_t launch_fft(const float2 *in, float2 *out, int log2n, int batch, int sign,
+                       const float2 *tw, cudaStream_t st);
+
+}  // namespace cwtk

@@ -1,0 +1,121 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function that
+include/*.h declares, and its host-side logic (argument validation, padding
+policy, status strings) behaves as documented.  No CUDA compute is issued: each
+call here returns before the library's first CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_07793_gb300 as p
+    return p
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        names += re.findall(r"\b(cwt_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for s in range(9):
+        assert lib.cwt_status_str(s).startswith("CWT_")
+    assert "UNKNOWN" in lib.cwt_status_str(99)
+
+
+def test_options_defaults(lib):
+    o = lib.cwt_options_init()
+    assert (o.precision, o.decimation, o.pad_policy, o.fft_length, o.io_dtype) == (0, 1, 0, 0, 0)
+
+
+@pytest.mark.parametrize("n,N", [(1, 32), (31, 32), (32, 32), (33, 64), (500, 512), (10000, 16384),
+                                 (16384, 16384)])
+def test_pow2_padding(lib, n, N):
+    assert lib.cwt_fft_length(n) == N
+
+
+def test_padding_limits(lib):
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_fft_length(0)
+    assert e.value.status == lib.CWT_EINVAL
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_fft_length(16385)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_fft_length(100, lib.CWT_PAD_SMOOTH)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+
+
+BAD = [
+    dict(channels=0), dict(samples=0), dict(fs=0.0), dict(fs=float("nan")),
+    dict(freqs=[10.0, 0.0]), dict(freqs=[10.0, 250.0]), dict(freqs=[-1.0]),
+    dict(n_cycles=[7.0, 0.0]), dict(n_cycles=[7.0, float("inf")]),
+    dict(wavelet=7), dict(kinds=0), dict(kinds=8), dict(decimation=0), dict(io=5),
+    dict(precision=9), dict(fft_length=100), dict(fft_length=64, samples=100),
+]
+
+
+@pytest.mark.parametrize("bad", BAD)
+def test_invalid_arguments_rejected_before_cuda(lib, bad):
+    a = dict(channels=2, samples=100, fs=500.0, freqs=[10.0, 20.0], n_cycles=[7.0, 7.0],
+             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0)
+    a.update(bad)
+    o = lib.cwt_options_init()
+    o.decimation, o.io_dtype, o.precision, o.fft_length = a["decimation"], a["io"], a["precision"], a["fft_length"]
+    f = np.asarray(a["freqs"], dtype=np.float64)
+    c = np.asarray(a["n_cycles"], dtype=np.float64)
+    if len(c) != len(f):
+        c = np.resize(c, len(f))
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(a["channels"], a["samples"], a["fs"], f, c, a["wavelet"], a["kinds"], o)
+    assert e.value.status == lib.CWT_EINVAL
+
+
+@pytest.mark.parametrize("what", ["gmw", "tc_fp16", "tc_bf16", "too_long"])
+def test_unsupported_requests(lib, what):
+    o = lib.cwt_options_init()
+    wavelet, samples = 0, 100
+    if what == "gmw":
+        wavelet = lib.CWT_WAVELET_GMW
+    elif what == "tc_fp16":
+        o.precision = lib.CWT_PREC_TC_FP16
+    elif what == "tc_bf16":
+        o.precision = lib.CWT_PREC_TC_BF16
+    else:
+        samples = 20000
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(1, samples, 500.0, [10.0], [7.0], wavelet, lib.CWT_OUT_POWER, o)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+
+
+def test_null_plan_calls(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    so.cwt_plan_workspace_bytes.restype = ctypes.c_size_t
+    assert so.cwt_plan_workspace_bytes(None) == 0
+    assert so.cwt_plan_destroy(None) == 0
+    assert so.cwt_execute(None, None, None, None, None, None) == lib.CWT_EINVAL
+    assert so.cwt_plan_info(None, None) == lib.CWT_EINVAL
+    so.cwt_plan_last_error.restype = ctypes.c_char_p
+    assert so.cwt_plan_last_error(None) == b""

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every case draws seeded synthetic inputs from eeg_synth, runs the library on
+cuda:0 and compares element by element with oracle/ on the same inputs:
+  * the plain workload (8 ch x 500 @500 Hz, f64 I/O, power): every row;
+  * the fused workload at full size (64 ch x 10000 @1000 Hz, complex + power),
+    in the launch configuration the benchmark times: a spread of sampled rows;
+  * edge cases: n = 1, n at and just past a power of two, the largest
+    single-pass length, one channel / one scale, frequencies near Nyquist,
+    small and large n_cycles, Gabor, decimation, phase, f64 I/O.
+Bar: FP32 paths within 1e-5 per row (tests/metrics.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from eeg_synth import eeg, workload
+from tests.metrics import FP32_TOL, complex_err, phase_err, power_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_07793_gb300 as p
+    return p
+
+
+def run_gpu(lib, x, fs, freqs, cycles, outputs, dtype="f32", decimation=1, wavelet="morlet",
+            fft_length=0):
+    import torch
+    C, n = x.shape
+    t = lib.CWT(C, n, fs, freqs, cycles, outputs=outputs, dtype=dtype, decimation=decimation,
+                wavelet=wavelet, fft_length=fft_length)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = t(xt)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    N = t.info.fft_length
+    t.close()
+    return res, N
+
+
+def check(res, ref, tol=FP32_TOL):
+    worst = {}
+    if "complex" in res:
+        worst["complex"] = complex_err(res["complex"], ref).max()
+    if "power" in res:
+        worst["power"] = power_err(res["power"], ref).max()
+    if "phase" in res:
+        worst["phase"] = phase_err(res["phase"], ref).max()
+    for k, v in worst.items():
+        assert v <= tol, f"{k} row error {v:.3e} > {tol:.0e}"
+    return worst
+
+
+def test_fft_matches_library_fft_and_parseval(lib):
+    import torch
+    rng = np.random.default_rng(1)
+    for log2n in range(5, 15):
+        n = 1 << log2n
+        z = (rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))).astype(np.complex64)
+        d_in = torch.from_numpy(z).cuda()
+        for direction in (-1, 1):
+            d_out = torch.empty_like(d_in)
+            lib.cwt_fft(d_in, d_out, n, 3, direction)
+            torch.cuda.synchronize()
+            got = d_out.cpu().numpy().astype(np.complex128)
+            zz = z.astype(np.complex128)
+            ref = np.fft.fft(zz, axis=1) if direction < 0 else np.fft.ifft(zz, axis=1) * n
+            rel = np.abs(got - ref).max() / np.abs(ref).max()
+            assert rel < 2e-6 * log2n, (n, direction, rel)
+            # Parseval: sum |x|^2 = (1/n) sum |X|^2
+            assert np.allclose((np.abs(got) ** 2).sum(1) / n, (np.abs(zz) ** 2).sum(1), rtol=1e-5)
+    # in place
+    z = (rng.standard_normal((2, 1024)) + 1j * rng.standard_normal((2, 1024))).astype(np.complex64)
+    d = torch.from_numpy(z).cuda()
+    lib.cwt_fft(d, d, 1024, 2, -1)
+    torch.cuda.synchronize()
+    assert np.abs(d.cpu().numpy() - np.fft.fft(z.astype(np.complex128), axis=1)).max() < 1e-3
+
+
+@pytest.mark.parametrize("F,sigma,fs,n", [(10.0, 7.0, 500.0, 500), (1.0, 3.0, 1000.0, 10000),
+                                          (240.0, 3.0, 500.0, 300), (40.0, 10.0, 250.0, 2048),
+                                          (0.5, 7.0, 2048.0, 4096)])
+def test_bank_matches_oracle_wavelet_spectrum(lib, F, sigma, fs, n):
+    """The FP64-generated, FP32-stored bank equals the DFT of the oracle's
+    unit-energy periodised wavelet (times 1/N), and its band holds every bin
+    above 1e-10 of the peak."""
+    plan = lib.cwt_plan_create(1, n, fs, [F], [sigma], 0, lib.CWT_OUT_POWER)
+    try:
+        bank, start, length = lib.cwt_plan_bank(plan)
+        N = lib.cwt_plan_info(plan).fft_length
+    finally:
+        lib.cwt_plan_destroy(plan)
+    W = np.fft.fft(oracle.wavelet(F, sigma, fs, N)).real / N
+    assert np.abs(bank[0] - W).max() <= 1e-6 * np.abs(W).max()
+    k = np.arange(N)
+    inside = ((k - start[0]) % N) < length[0]
+    assert np.all(np.abs(W[~inside]) <= 2e-10 * np.abs(W).max())
+
+
+def test_plain_workload_every_row(lib):
+    w = workload("plain")
+    x = w.signal()
+    res, N = run_gpu(lib, x, w.fs, w.freqs, w.n_cycles, w.outputs, dtype=w.dtype)
+    assert res["power"].dtype == np.float64 and res["power"].shape == (8, 40, 500)
+    ref = oracle.cwt(x, N, w.fs, w.freqs, w.n_cycles)
+    check(res, ref)
+
+
+def test_fused_workload_full_size_sampled_rows(lib):
+    """64 x 10000, complex64 + power, exactly as the benchmark launches it;
+    the oracle recomputes a spread of rows (lowest/highest scale, smallest and
+    largest n_cycles, first/last channel)."""
+    w = workload("fused")
+    x = w.signal()
+    res, N = run_gpu(lib, x, w.fs, w.freqs, w.n_cycles, w.outputs)
+    assert res["complex"].shape == (64, 100, 10000) and res["complex"].dtype == np.complex64
+    rows = [(c, s) for c in (0, 31, 63) for s in (0, 1, 37, 64, 98, 99)]
+    ref = oracle.cwt_rows(x, N, w.fs, w.freqs, w.n_cycles, rows)
+    got = {k: np.stack([v[c, s] for c, s in rows]) for k, v in res.items()}
+    check(got, ref)
+    # power is |complex|^2 of the same kernel output
+    assert np.allclose(res["power"][0], np.abs(res["complex"][0]) ** 2, rtol=1e-5, atol=0)
+
+
+EDGE = [
+    # (C, n, fs, freqs, cycles, kwargs)
+    (1, 1, 100.0, [10.0], [7.0], {}),
+    (2, 31, 100.0, [5.0, 30.0], [3.0, 7.0], {}),
+    (2, 32, 100.0, [5.0, 30.0], [3.0, 7.0], {}),
+    (3, 33, 100.0, [5.0, 30.0, 49.0], [3.0, 7.0, 10.0], {}),
+    (5, 3001, 1000.0, np.geomspace(1, 400, 7), np.linspace(2, 12, 7), {}),
+    (2, 16384, 1000.0, [0.7, 499.0], [7.0, 3.0], {}),
+    (1, 700, 500.0, [2.0], [1.0], {}),
+    (2, 1000, 250.0, [124.0, 100.0], [2.0, 7.0], {}),
+    (3, 900, 300.0, [9.0, 41.0], [7.0, 5.0], dict(wavelet="gabor")),
+    (2, 777, 500.0, [6.0, 60.0], [7.0, 7.0], dict(fft_length=4096)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(EDGE)))
+def test_edge_cases_all_outputs(lib, case):
+    C, n, fs, freqs, cycles, kw = EDGE[case]
+    x = eeg(100 + case, C, n, fs, np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), **kw)
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, wavelet=kw.get("wavelet", "morlet"))
+    check(res, ref)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 6, 8, 16])
+def test_decimation(lib, d):
+    C, n, fs = 3, 2500, 1000.0
+    freqs, cycles = np.geomspace(2, 80, 9), np.clip(np.geomspace(2, 80, 9) / 2, 3, 12)
+    x = eeg(200 + d, C, n, fs, np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), decimation=d)
+    assert res["power"].shape == (C, 9, -(-n // d))
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=d)
+    check(res, ref)
+
+
+def test_f64_io_complex_and_phase(lib):
+    x = eeg(300, 2, 1200, 512.0, np.float64)
+    res, N = run_gpu(lib, x, 512.0, [3.0, 12.0, 100.0], [7.0, 7.0, 7.0],
+                     ("complex", "power", "phase"), dtype="f64")
+    assert res["complex"].dtype == np.complex128
+    check(res, oracle.cwt(x, N, 512.0, [3.0, 12.0, 100.0], [7.0, 7.0, 7.0]))
+
+
+def test_host_buffers_match_device_path_and_repeat_bitwise(lib):
+    import torch
+    w = workload("plain")
+    x = np.ascontiguousarray(w.signal()[:, :])
+    plan = lib.cwt_plan_create(8, 500, w.fs, w.freqs, w.n_cycles, 0, lib.CWT_OUT_COMPLEX | lib.CWT_OUT_POWER,
+                               _opts(lib, io=lib.CWT_DTYPE_F64))
+    try:
+        hc = np.empty((8, 40, 500), np.complex128)
+        hp = np.empty((8, 40, 500), np.float64)
+        lib.cwt_execute_host(plan, x, hc, hp, None)
+        xt = torch.from_numpy(x).cuda()
+        dc = torch.empty((8, 40, 500), dtype=torch.complex128, device="cuda")
+        dp = torch.empty((8, 40, 500), dtype=torch.float64, device="cuda")
+        lib.cwt_execute(plan, xt, dc, dp, None)
+        lib.cwt_execute(plan, xt, dc, dp, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(dc.cpu().numpy(), hc) and np.array_equal(dp.cpu().numpy(), hp)
+    finally:
+        lib.cwt_plan_destroy(plan)
+
+
+def test_bad_pointers_rejected_on_host(lib):
+    import torch
+    plan = lib.cwt_plan_create(1, 100, 500.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER)
+    try:
+        x = torch.zeros(100, device="cuda")
+        out = torch.zeros(100, device="cuda")
+        host = np.zeros(100, np.float32)
+        for sig, o in ((host, out), (x, host), (x[1:], out), (x, None)):
+            with pytest.raises(lib.CWTError) as e:
+                lib.cwt_execute(plan, sig, None, o, None)
+            assert e.value.status == lib.CWT_EINVAL
+        with pytest.raises(lib.CWTError):  # complex not requested at creation
+            lib.cwt_execute(plan, x, torch.zeros(200, device="cuda"), out, None)
+    finally:
+        lib.cwt_plan_destroy(plan)
+
+
+def test_profiling_counts_launches(lib):
+    import torch
+    plan = lib.cwt_plan_create(4, 1000, 500.0, [10.0, 20.0], [7.0, 7.0], 0, lib.CWT_OUT_POWER)
+    try:
+        lib.cwt_plan_set_profiling(plan, True)
+        x = torch.zeros((4, 1000), device="cuda")
+        out = torch.empty((4, 2, 1000), device="cuda")
+        for _ in range(3):
+            lib.cwt_execute(plan, x, None, out, None)
+        n_f, ms_f = lib.cwt_plan_profile_read(plan, lib.CWT_KERNEL_FORWARD_FFT)
+        n_s, ms_s = lib.cwt_plan_profile_read(plan, lib.CWT_KERNEL_SCALE_BLOCK)
+        assert (n_f, n_s) == (3, 3) and ms_f > 0 and ms_s > 0
+        assert lib.cwt_plan_profile_read(plan, lib.CWT_KERNEL_SCALE_BLOCK) == (0, 0.0)
+        nb, bank_ms = lib.cwt_plan_profile_read(plan, lib.CWT_KERNEL_BANK)
+        assert nb == 1 and bank_ms > 0
+    finally:
+        lib.cwt_plan_destroy(plan)
+
+
+def test_paper_style_error_report(lib):
+    """Table 1's metric (|diff| / SD over the 20-80 % interior, threshold
+    1e-5 SD) for 1 s at 1000 Hz, sigma 7, 30-90 Hz by 1 Hz, against the oracle."""
+    fs, n = 1000.0, 1000
+    freqs = np.arange(30.0, 91.0)
+    x = eeg(400, 1, n, fs, np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, np.full(len(freqs), 7.0), ("complex",))
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, np.full(len(freqs), 7.0))
+    rep = oracle.paper_style_error(res["complex"].astype(np.complex128), ref)
+    assert rep["real"][2] == 0 and rep["imag"][2] == 0, rep
+
+
+def _opts(lib, **kw):
+    o = lib.cwt_options_init()
+    if "io" in kw:
+        o.io_dtype = kw["io"]
+    return o
