@@ -8,14 +8,16 @@
 //
 //  * A row of length N is handled by T = N / R threads; each thread keeps R
 //    complex values in registers.
-//  * Pass p (Ns = R^p, radix Rp): thread j owns butterflies jj = j + g*T.  It
-//    multiplies input r by w^r with w = exp(+-2 pi i (jj mod Ns) / (Ns Rp)),
-//    runs an Rp-point DFT in registers and writes output r to position
+//  * Pass p (radix Rp, Ns = product of the earlier radices): thread j owns
+//    butterflies jj = j + g*T.  It multiplies input r by w^r with
+//    w = exp(+-2 pi i (jj mod Ns) / (Ns Rp)), runs an Rp-point DFT in
+//    registers and writes output r to position
 //    (jj - jj mod Ns) * Rp + (jj mod Ns) + r * Ns.  This is the self-sorting
 //    (Stockham) decimation-in-time order: the last pass writes natural order.
-//  * Between passes the row is exchanged through shared memory as separate
-//    re/im float arrays with one pad word per 32 (bank-conflict-free for the
-//    power-of-two strides used here).
+//  * Between passes the row is exchanged through shared memory as float2 with
+//    one pad slot per 16 (bank-conflict-free for the strides used here).
+//  * Only pass 0 may have a smaller radix; passes 1.. run one rolled loop body
+//    so the kernel's code stays small enough for the instruction cache.
 //  * The first pass reads its inputs through a caller functor (global memory,
 //    fused pre-processing) and the last pass hands each output to a caller
 //    functor (fused epilogue), so neither end touches shared memory.
@@ -32,10 +34,6 @@ __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c
 // rounded to FP32 (one table per device, shared by every plan).
 constexpr int kTwLog2 = 17;
 constexpr int kTwN = 1 << kTwLog2;
-
-// Shared-memory padding: one extra word every 32 words.
-__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
-__host__ __device__ constexpr int spad_size(int n) { return n + (n >> 5); }
 
 // cos(2 pi j / 32), j = 0..8 (first quadrant), as exact-to-float literals.
 __host__ __device__ constexpr float cos_q32(int j) {
@@ -143,105 +141,104 @@ __device__ __forceinline__ void twiddle_chain(float2 *v, float2 w1) {
     }
 }
 
-// Pass schedule for a row of N points, R points per thread.
+// Pass schedule for a row of N = 2^L points with R = 2^r points per thread.
+// The leftover factor comes FIRST: pass 0 has radix 2^(L mod r) (or R), each
+// thread running G0 = R / radix0 butterflies of it; every later pass has radix
+// R, so passes 1.. share one rolled loop body (small code footprint).
 template <int N, int R>
 struct FftShape {
     static constexpr int T = N / R;  // threads per row
     static constexpr int L2N = ilog2c(N);
     static constexpr int L2R = ilog2c(R);
-    static constexpr int NP = (L2N + L2R - 1) / L2R;  // number of passes
-    static constexpr int LAST_L2 = L2N - (NP - 1) * L2R;
-    static constexpr int SMEM_FLOATS = 2 * spad_size(N);  // re + im, padded
-    __host__ __device__ static constexpr int radix(int p) { return p < NP - 1 ? R : (1 << LAST_L2); }
-    __host__ __device__ static constexpr int ns(int p) { return 1 << (p * L2R); }
+    static constexpr int REM = L2N % L2R;
+    static constexpr int R0 = REM ? (1 << REM) : R;  // radix of pass 0
+    static constexpr int G0 = R / R0;                 // pass-0 butterflies per thread
+    static constexpr int NP = 1 + (L2N - ilog2c(R0)) / L2R;  // total passes
+    static constexpr int SMEM_F2 = N + (N >> 4);      // padded float2 slots
     static_assert((1 << L2N) == N && (1 << L2R) == R && R <= N, "power-of-two sizes only");
 };
 
-// Load the inputs of pass 0 through `load(index)` (index in [0, N)).
-template <int N, int R, typename Load>
-__device__ __forceinline__ void fft_load_first(float2 (&v)[R], int j, Load &load) {
-    using S = FftShape<N, R>;
-    constexpr int R0 = S::radix(0), G0 = R / R0;
-#pragma unroll
-    for (int g = 0; g < G0; ++g)
-#pragma unroll
-        for (int r = 0; r < R0; ++r) v[g * R0 + r] = load(j + g * S::T + r * (N / R0));
-}
+// float2 shared-memory slot of element i: one pad slot every 16, so that
+// half-warps touching power-of-two strides up to 16 land on distinct banks.
+__device__ __forceinline__ int spad2(int i) { return i + (i >> 4); }
 
-// Pass P of the Stockham FFT, then (recursively) the remaining passes.  The
-// outputs of the last pass go to `store(t, value)` with t in [0, N) natural
-// order.  `tw` is the device twiddle table (kTwN entries).
-template <int N, int R, int SIGN, int P>
-struct StockhamPass {
-    template <typename Store>
-    __device__ __forceinline__ static void run(float2 (&v)[R], float *__restrict__ sre,
-                                               float *__restrict__ sim,
-                                               const float2 *__restrict__ tw, int j, Store &store) {
-        using S = FftShape<N, R>;
-        constexpr int Rp = S::radix(P), G = R / Rp, Ns = S::ns(P), T = S::T;
+// Whole-row FFT, X[t] = sum_k x[k] exp(SIGN 2 pi i k t / N), natural order in
+// and out.  `load(k)` supplies x[k] (pass 0 reads only through it);
+// `store(t, X[t])` receives every output exactly once from the last pass.
+// `sm` is this row's padded float2 staging buffer (FftShape::SMEM_F2 slots).
+// All threads of the CTA call it together (it contains __syncthreads).
+template <int N, int R, int SIGN, typename Load, typename Store>
+__device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *__restrict__ tw,
+                                        int j, Load &load, Store &store) {
+    using S = FftShape<N, R>;
+    constexpr int T = S::T, R0 = S::R0, G0 = S::G0;
+    // ---- pass 0: radix R0, Ns = 1, no twiddles; inputs from `load`
+    {
+        float2 v[R];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if (Ns > 1) {
-                const int k = (j + g * T) & (Ns - 1);
-                float2 w1 = __ldg(&tw[k * (kTwN / (Ns * Rp))]);
-                if (SIGN < 0) w1.y = -w1.y;
-                twiddle_chain<Rp>(&v[g * Rp], w1);
-            }
-            dft<Rp, SIGN>(&v[g * Rp]);
-        }
-        if constexpr (P == S::NP - 1) {
+        for (int g = 0; g < G0; ++g)
 #pragma unroll
-            for (int g = 0; g < G; ++g)
+            for (int r = 0; r < R0; ++r) v[g * R0 + r] = load(j + g * T + r * (N / R0));
 #pragma unroll
-                for (int r = 0; r < Rp; ++r) store(j + g * T + r * Ns, v[g * Rp + r]);
+        for (int g = 0; g < G0; ++g) dft<R0, SIGN>(&v[g * R0]);
+        if constexpr (S::NP == 1) {
+#pragma unroll
+            for (int g = 0; g < G0; ++g)
+#pragma unroll
+                for (int r = 0; r < R0; ++r) store(j + g * T + r, v[g * R0 + r]);
+            return;
         } else {
-            __syncthreads();  // every thread has finished reading the previous exchange
+            __syncthreads();  // the buffer may still be read by a previous row
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int jj = j + g * T;
-                const int k = jj & (Ns - 1);
-                const int base = (jj - k) * Rp + k;
+            for (int g = 0; g < G0; ++g)
 #pragma unroll
-                for (int r = 0; r < Rp; ++r) {
-                    const int idx = spad(base + r * Ns);
-                    sre[idx] = v[g * Rp + r].x;
-                    sim[idx] = v[g * Rp + r].y;
-                }
-            }
-            __syncthreads();
-            constexpr int Rq = S::radix(P + 1), Gq = R / Rq;
-#pragma unroll
-            for (int g = 0; g < Gq; ++g)
-#pragma unroll
-                for (int r = 0; r < Rq; ++r) {
-                    const int idx = spad(j + g * T + r * (N / Rq));
-                    v[g * Rq + r] = make_float2(sre[idx], sim[idx]);
-                }
-            StockhamPass<N, R, SIGN, P + 1>::run(v, sre, sim, tw, j, store);
+                for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
         }
     }
-};
-
-// Whole-row FFT: load -> passes -> store.  All threads of the CTA must call
-// it together (it contains __syncthreads).
-template <int N, int R, int SIGN, typename Load, typename Store>
-__device__ __forceinline__ void fft_row(float *__restrict__ sre, float *__restrict__ sim,
-                                        const float2 *__restrict__ tw, int j, Load &load,
-                                        Store &store) {
-    float2 v[R];
-    fft_load_first<N, R>(v, j, load);
-    StockhamPass<N, R, SIGN, 0>::run(v, sre, sim, tw, j, store);
+    // ---- passes 1..NP-1: radix R, Ns = R0 * R^(p-1)
+    int Ns = R0;
+#pragma unroll 1
+    for (int p = 1; p < S::NP; ++p) {
+        __syncthreads();
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
+        const int k = j & (Ns - 1);
+        float2 w1 = __ldg(&tw[k * (kTwN / (Ns * R))]);
+        if (SIGN < 0) w1.y = -w1.y;
+        twiddle_chain<R>(v, w1);
+        dft<R, SIGN>(v);
+        if (p == S::NP - 1) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) store(j + r * Ns, v[r]);
+        } else {
+            __syncthreads();
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
+        }
+        Ns *= R;
+    }
 }
+
+// Points per thread: a build-time tuning knob (the largest length and the
+// rest), measured on GB300; see RowConfig.
+#ifndef CWT_RADIX_16384
+#define CWT_RADIX_16384 32
+#endif
+#ifndef CWT_RADIX_DEFAULT
+#define CWT_RADIX_DEFAULT 16
+#endif
 
 // Launch shape for a row kernel of size N: R points per thread, several rows
 // per CTA for short rows so that a CTA has at least 256 threads.
-template <int N>
+template <int N, int RR = (N >= 16384 ? CWT_RADIX_16384 : (N >= CWT_RADIX_DEFAULT ? CWT_RADIX_DEFAULT : N))>
 struct RowConfig {
-    static constexpr int R = N >= 16384 ? 32 : (N >= 16 ? 16 : N);
+    static constexpr int R = RR;
     static constexpr int T = N / R;
     static constexpr int ROWS = T >= 256 ? 1 : 256 / T;
     static constexpr int THREADS = T * ROWS;
-    static constexpr int SMEM_BYTES = ROWS * FftShape<N, R>::SMEM_FLOATS * 4;
+    static constexpr int SMEM_BYTES = ROWS * FftShape<N, R>::SMEM_F2 * 8;
 };
 
 }  // namespace cwtk

@@ -21,12 +21,11 @@ __global__ void __launch_bounds__(RowConfig<N>::THREADS)
 forward_kernel(const IO *__restrict__ x, int C, int n, float2 *__restrict__ spec,
                const float2 *__restrict__ tw) {
     using RC = RowConfig<N>;
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     const int rl = threadIdx.x / RC::T, j = threadIdx.x % RC::T;
     const int row = blockIdx.x * RC::ROWS + rl;
     const bool act = row < C;
-    float *sre = smem + rl * FftShape<N, RC::R>::SMEM_FLOATS;
-    float *sim = sre + spad_size(N);
+    float2 *sm = smem2 + rl * FftShape<N, RC::R>::SMEM_F2;
     const IO *xr = x + (size_t)(act ? row : 0) * (size_t)n;
     float2 *out = spec + (size_t)(act ? row : 0) * (size_t)N;
     auto load = [&](int i) -> float2 {
@@ -35,26 +34,25 @@ forward_kernel(const IO *__restrict__ x, int C, int n, float2 *__restrict__ spec
     auto store = [&](int t, float2 v) {
         if (act) out[t] = v;
     };
-    fft_row<N, RC::R, -1>(sre, sim, tw, j, load, store);
+    fft_row<N, RC::R, -1>(sm, tw, j, load, store);
 }
 
 template <int N, int SIGN>
 __global__ void __launch_bounds__(RowConfig<N>::THREADS)
 fft_kernel(const float2 *in, float2 *out, int batch, const float2 *__restrict__ tw) {
     using RC = RowConfig<N>;
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     const int rl = threadIdx.x / RC::T, j = threadIdx.x % RC::T;
     const int row = blockIdx.x * RC::ROWS + rl;
     const bool act = row < batch;
-    float *sre = smem + rl * FftShape<N, RC::R>::SMEM_FLOATS;
-    float *sim = sre + spad_size(N);
+    float2 *sm = smem2 + rl * FftShape<N, RC::R>::SMEM_F2;
     const float2 *ir = in + (size_t)(act ? row : 0) * N;
     float2 *orow = out + (size_t)(act ? row : 0) * N;
     auto load = [&](int i) -> float2 { return act ? ir[i] : make_float2(0.f, 0.f); };
     auto store = [&](int t, float2 v) {
         if (act) orow[t] = v;
     };
-    fft_row<N, RC::R, SIGN>(sre, sim, tw, j, load, store);
+    fft_row<N, RC::R, SIGN>(sm, tw, j, load, store);
 }
 
 template <int N, typename IO>

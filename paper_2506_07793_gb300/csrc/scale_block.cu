@@ -36,19 +36,25 @@ template <typename IO> struct IO2;
 template <> struct IO2<float> { using type = float2; };
 template <> struct IO2<double> { using type = double2; };
 
+// Phase is rare on the hot path; keeping atan2f out of line keeps the
+// unrolled epilogue small.
+template <typename IO>
+__device__ __noinline__ void store_phase(IO *dst, float2 v) {
+    *dst = (IO)atan2f(v.y, v.x);
+}
+
 template <int M, typename IO>
 __global__ void __launch_bounds__(RowConfig<M>::THREADS)
 scale_block_kernel(const SBArgs a) {
     using RC = RowConfig<M>;
     using V2 = typename IO2<IO>::type;
-    extern __shared__ float smem[];
+    extern __shared__ float2 smem2[];
     const int rl = threadIdx.x / RC::T, j = threadIdx.x % RC::T;
     const int row = blockIdx.x * RC::ROWS + rl;
     const bool act = row < a.rows;
     const int c = act ? row / a.S : 0;
     const int s = act ? row - c * a.S : 0;
-    float *sre = smem + rl * FftShape<M, RC::R>::SMEM_FLOATS;
-    float *sim = sre + spad_size(M);
+    float2 *sm = smem2 + rl * FftShape<M, RC::R>::SMEM_F2;
 
     const float2 *X = a.spec + (size_t)c * (size_t)a.N;
     const float *W = a.bank + (size_t)s * (size_t)a.N;
@@ -58,6 +64,14 @@ scale_block_kernel(const SBArgs a) {
 
     auto load = [&](int jj) -> float2 {
         float2 acc = make_float2(0.f, 0.f);
+        if (fold == 1) {
+            if (((jj - b0) & nmask) < B) {
+                const float2 x = X[jj];
+                const float w = W[jj];
+                acc = make_float2(x.x * w, x.y * w);
+            }
+            return acc;
+        }
         for (int q = 0; q < fold; ++q) {
             const int k = jj + q * M;
             if (((k - b0) & nmask) < B) {
@@ -90,9 +104,9 @@ scale_block_kernel(const SBArgs a) {
             oc[obase + o] = z;
         }
         if (op) op[obase + o] = (IO)fmaf(v.x, v.x, v.y * v.y);
-        if (oph) oph[obase + o] = (IO)atan2f(v.y, v.x);
+        if (oph) store_phase(oph + obase + o, v);
     };
-    fft_row<M, RC::R, +1>(sre, sim, a.tw, j, load, store);
+    fft_row<M, RC::R, +1>(sm, a.tw, j, load, store);
 }
 
 template <int M, typename IO>
