@@ -214,6 +214,43 @@ cwt_status cwt_plan_set_profiling(cwt_plan plan, int enable);
 cwt_status cwt_plan_profile_read(cwt_plan plan, int kernel, int *launches, double *total_ms,
                                  int reset);
 
+/*
+ * cwt_execute_noalloc -- the Morlet transform of cwt_plan_create +
+ * cwt_execute (power-of-two padding, no decimation, float32 signal and
+ * outputs) for callers that must not allocate GPU memory while they run: a
+ * real-time EEG / BCI processing loop, where a cudaMalloc or cudaFree can
+ * synchronise the device and blow the loop's deadline, or a plug-in whose host
+ * application owns the GPU memory budget.  The paper has no counterpart; it is
+ * an addition of this library.
+ *
+ * It allocates nothing.  The caller passes the signal and the outputs; the
+ * twiddle table, wavelet bank, band table and spectra live in one fixed
+ * device array of CWT_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until the process exits.  The bank is regenerated (FP64, as
+ * in cwt_plan_create) on every call, so no plan is needed.
+ *   d_signal   device [channels][samples] float32, 16-byte aligned
+ *   fs, freqs_hz[n_freqs], n_cycles[n_freqs]  as for cwt_plan_create (host arrays)
+ *   d_complex  device [channels][n_freqs][samples] complex64, or NULL
+ *   d_power, d_phase  device [channels][n_freqs][samples] float32, or NULL
+ *              (at least one output non-NULL; all 16-byte aligned)
+ * Size limit: with N = cwt_fft_length(samples), the request must satisfy
+ *   1 MiB + 256-byte-rounded(16*S + 8*S*ceil(N/256) + 8*S + 4*S*N) + 8*C*N
+ *       <= CWT_NOALLOC_SCRATCH_BYTES   (S = n_freqs, C = channels),
+ * e.g. 64 channels x 10000 samples x 100 scales fits; larger requests return
+ * CWT_EINVAL before any device work.
+ * The first call on a device (the current device) resolves the array's device
+ * address and writes its twiddle table, then waits for that on `stream`; make
+ * that first call before any stream capture.  Every call reuses the same array
+ * and overwrites everything it reads, so nothing needs clearing between
+ * calls; calls that overlap on the GPU (unordered streams, other host
+ * threads) race on it and must be serialised by the caller.  Asynchronous on
+ * `stream` after the first call.
+ */
+#define CWT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+cwt_status cwt_execute_noalloc(const float *d_signal, int channels, int samples, double fs,
+                               const double *freqs_hz, const double *n_cycles, int n_freqs,
+                               void *d_complex, float *d_power, float *d_phase, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

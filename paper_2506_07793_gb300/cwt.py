@@ -72,6 +72,8 @@ _sig("cwt_execute", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("cwt_execute_host", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("cwt_plan_bank", ctypes.c_int, [_vp, _fp, _ip, _ip])
 _sig("cwt_fft", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp])
+_sig("cwt_execute_noalloc", ctypes.c_int,
+     [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp])
 _sig("cwt_plan_set_profiling", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("cwt_plan_profile_read", ctypes.c_int,
      [_vp, ctypes.c_int, _ip, _dp, ctypes.c_int])
@@ -185,6 +187,19 @@ def cwt_plan_bank(plan):
 def cwt_fft(d_in, d_out, n, batch, direction, stream=None):
     _check(_lib.cwt_fft(_ptr(d_in), _ptr(d_out), int(n), int(batch), int(direction),
                         _stream(stream)), "cwt_fft")
+
+
+def cwt_execute_noalloc(signal, channels, samples, fs, freqs_hz, n_cycles, complex_out=None,
+                        power_out=None, phase_out=None, stream=None):
+    """The transform without any GPU allocation (for callers that may not
+    allocate while running, e.g. real-time loops); see include/cwt.h."""
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64).reshape(-1))
+    c = np.ascontiguousarray(np.broadcast_to(np.asarray(n_cycles, dtype=np.float64), f.shape))
+    st = _lib.cwt_execute_noalloc(_ptr(signal), int(channels), int(samples), float(fs),
+                                  f.ctypes.data_as(_dp), c.ctypes.data_as(_dp), len(f),
+                                  _ptr(complex_out), _ptr(power_out), _ptr(phase_out),
+                                  _stream(stream))
+    _check(st, "cwt_execute_noalloc")
 
 
 def cwt_plan_set_profiling(plan, enable):
