@@ -166,6 +166,136 @@ def run_reference(args):
     }), flush=True)
 
 
+def timed_steps(step, steps, flush, stream):
+    """Run `steps` steps, each between CUDA events on `stream`, overwriting
+    `flush` (> L2) between them outside the events; returns total ms."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+
+def run_batch(args):
+    """Batching workload: 2048 epochs (U{256..8192} samples) x 64 channels,
+    64 scales, power decimated x4, one cwt_execute_batch per step."""
+    import torch
+    import paper_2506_07793_gb300 as cw
+    from eeg_synth import batch_signal, workload
+    import oracle
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload("batch")
+    lengths = w.extra["epoch_lengths"]
+    C, S, d = w.channels, w.scales, w.decimation
+    opt = cw.cwt_options_init()
+    opt.decimation = d
+    plan = cw.cwt_plan_create(C, 8192, w.fs, w.freqs, w.n_cycles, cw.CWT_WAVELET_MORLET,
+                              cw.CWT_OUT_POWER, opt)
+    ep, n_in, n_o = cw.pack_epochs(lengths, C, S, d)
+    x_host, _, _ = batch_signal(w)
+    x = torch.from_numpy(x_host).cuda()
+    out = torch.empty(n_o, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    step = lambda: cw.cwt_execute_batch(plan, ep, x, None, out, None, stream)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cw.cwt_plan_set_profiling(plan, True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    total_ms = timed_steps(step, args.steps, flush, stream)
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    n_b, ms_b = cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_BATCH, reset=True)
+    cw.cwt_plan_set_profiling(plan, False)
+    stats = cw.cwt_plan_batch_stats(plan)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    coeffs = int(n_o)
+    value = coeffs * world / (ms_step * 1e-3)
+    peaks, peak_kind = measured_peaks()
+    alg_bytes = int(x_host.nbytes) + coeffs * 4 + int(stats.bank_bytes)
+    k_s = ms_b / max(n_b, 1) * 1e-3
+    achieved = alg_bytes / k_s / 1e9
+    roofline = {"kernel": "batch_kernel (persistent, CUDA graph)", "bound": "hbm",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind, "traffic": None,
+                "alg_bytes_per_launch": alg_bytes, "kernel_ms": k_s * 1e3}
+    # end to end: pinned host input -> device, batch, device -> pinned host output
+    h_in = torch.from_numpy(x_host).pin_memory()
+    h_out = torch.empty(n_o, dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": coeffs * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x_host.nbytes),
+           "d2h_bytes_per_step": int(coeffs * 4), "ms_per_step": e2e_s * 1e3}
+    cw.cwt_plan_destroy(plan)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.notes, "epochs": len(lengths), "channels": C, "scales": S,
+                       "decimation": d, "coefficients_per_step": coeffs,
+                       "l2": "inputs (2.2 GB) and outputs (35 GB) exceed L2; 256 MB buffer also "
+                             "overwritten between timed steps",
+                       "autotuned": {"inverse_radix": stats.inverse_radix, "order": stats.order,
+                                     "candidate_ms": list(stats.tune_ms)},
+                       "items": stats.items, "grid": stats.grid, "wall_s_timed_region": wall,
+                       "parallelism": f"weak x{world}, no collective"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk,
+        }
+        if world == 1:
+            cores = len(os.sched_getaffinity(0))
+            n_ep = 2
+            t0 = time.perf_counter()
+            done = 0
+            for e_ in range(n_ep):
+                n = int(lengths[e_])
+                xe = x_host[ep[e_].in_offset:ep[e_].in_offset + C * n].reshape(C, n)
+                oracle.cwt(xe.astype(np.float64), cw.cwt_fft_length(n), w.fs, w.freqs, w.n_cycles,
+                           decimation=d, threads=cores)
+                done += C * S * (-(-n // d))
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": done / dt, "unit": UNIT, "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"first {n_ep} of {len(lengths)} epochs x all {C} "
+                                              f"channels x all {S} scales ({done} coefficients), "
+                                              f"{dt:.2f} s wall"}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,11 +304,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-channels", type=int, default=2)
+    ap.add_argument("--workload", default=WORKLOAD, choices=["fused", "batch"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     import torch
     import paper_2506_07793_gb300 as cw

@@ -109,7 +109,11 @@ def workload(name):
                      4, 3, "2048 epochs, n_e ~ U{256..8192}, 64 ch @1000 Hz, 64 log freqs 2-80 Hz, "
                      "n_cycles clip(f/2,3,12), power decimated x4")
         rng = np.random.default_rng(np.random.SeedSequence([3, 1_000_000]))
-        w.extra["epoch_lengths"] = rng.integers(256, 8193, size=2048)
+        lengths = rng.integers(256, 8193, size=2048)
+        w.extra["epoch_lengths"] = lengths
+        # epochs are windows of one continuous recording (event-locked epochs)
+        w.extra["recording_samples"] = 1 << 19
+        w.extra["epoch_starts"] = rng.integers(0, (1 << 19) - lengths + 1)
         return w
     if name == "precision":
         f = np.geomspace(0.5, 200.0, 128)
@@ -122,3 +126,21 @@ def workload(name):
                         "32 streams, C in {8,32,64,128,256}, fs in {250,500,1000,2000,4000}, "
                         "W=2048, 50 ms hop, 64 log freqs 1-100 Hz")
     raise KeyError(name)
+
+
+def batch_signal(w, epochs=None):
+    """Packed float32 input of the batching workload: epoch e is the window
+    [start_e, start_e + n_e) of one continuous C-channel recording, laid out
+    [C][n_e] and packed back to back in epoch order.  Returns (packed array,
+    per-epoch element offsets, recording [C][L])."""
+    lengths = np.asarray(w.extra["epoch_lengths"])
+    starts = np.asarray(w.extra["epoch_starts"])
+    if epochs is not None:
+        lengths, starts = lengths[:epochs], starts[:epochs]
+    rec = eeg(w.seed, w.channels, int(w.extra["recording_samples"]), w.fs, np.float32)
+    offs = np.zeros(len(lengths), dtype=np.int64)
+    offs[1:] = np.cumsum(w.channels * lengths[:-1])
+    packed = np.empty(int(w.channels * lengths.sum()), dtype=np.float32)
+    for e, (n, s0) in enumerate(zip(lengths, starts)):
+        packed[offs[e]:offs[e] + w.channels * n] = rec[:, s0:s0 + n].reshape(-1)
+    return packed, offs, rec

@@ -83,8 +83,34 @@ typedef enum {
     CWT_KERNEL_BANK = 0,        /* wavelet-bank + band generation (plan creation) */
     CWT_KERNEL_FORWARD_FFT = 1, /* per-channel forward FFT */
     CWT_KERNEL_SCALE_BLOCK = 2, /* fused multiply + inverse FFT + reduce + store */
-    CWT_KERNEL_COUNT = 3
+    CWT_KERNEL_BATCH = 3,       /* persistent batch kernel (one graph launch) */
+    CWT_KERNEL_COUNT = 4
 } cwt_kernel_id;
+
+/* One epoch of a batch (cwt_execute_batch).  Offsets are in elements of the
+ * packed arrays: the epoch's signal is the [C][samples] block starting at
+ * in_offset, and its outputs are the [C][S][ceil(samples/d)] blocks starting
+ * at out_offset in each requested output array (complex arrays count complex
+ * elements). */
+typedef struct {
+    long long in_offset;
+    long long out_offset;
+    int samples;  /* 1 <= samples <= the plan's samples and <= 8192 */
+    int reserved;
+} cwt_epoch;
+
+/* What the batch path did last (cwt_plan_batch_stats). */
+typedef struct {
+    int items;              /* work items (epoch, channel group) of the last batch */
+    int grid;               /* persistent CTAs launched */
+    int inverse_radix;      /* autotuned points per thread of the inverse FFTs (16 or 32) */
+    int order;              /* autotuned item order: 0 largest FFT first, 1 input order */
+    int tuned;              /* 1 once the autotuner has chosen for this batch shape */
+    int reserved;
+    double tune_ms[4];      /* candidate times: (16,0), (32,0), (16,1), (32,1) */
+    long long graph_launches;
+    size_t bank_bytes;      /* device bytes of the per-length wavelet banks */
+} cwt_batch_stats;
 
 typedef struct {
     int precision;  /* cwt_precision; only CWT_PREC_FP32 is implemented */
@@ -180,6 +206,28 @@ cwt_status cwt_execute(cwt_plan plan, const void *d_signal, void *d_complex, voi
  */
 cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex, void *h_power,
                             void *h_phase, void *stream);
+
+/*
+ * cwt_execute_batch -- many epochs of uneven length in one persistent launch
+ * replayed from a CUDA graph.  Epoch e is the same transform as cwt_execute
+ * on its own samples (padded length N_e = next power of two >= max(n_e, 32),
+ * Section "Fast Fourier transform"), with the plan's channels, scales,
+ * decimation and output kinds.  The paper loops over recordings in Python
+ * (Section "Wavelength and flexibility"); here they share one launch.
+ *   epochs[n_epochs]  host array of cwt_epoch (offsets in elements)
+ *   d_in              device packed float32 input
+ *   d_complex / d_power / d_phase  device packed outputs (exactly the plan's kinds)
+ * Requires an F32 plan.  The first batch of a new shape generates the banks
+ * for its lengths (allocating and waiting) and runs the autotuner, which times
+ * four schedules on this batch and keeps the fastest; later batches of the
+ * same shape only replay the graph.  Asynchronous on `stream` otherwise.
+ * CWT_EUNSUPPORTED for F64 plans or epochs longer than 8192 samples.
+ */
+cwt_status cwt_execute_batch(cwt_plan plan, const cwt_epoch *epochs, int n_epochs, const void *d_in,
+                             void *d_complex, void *d_power, void *d_phase, void *stream);
+
+/* Statistics of the plan's batch path (zeros before the first batch). */
+cwt_status cwt_plan_batch_stats(cwt_plan plan, cwt_batch_stats *stats);
 
 /*
  * cwt_plan_bank -- copy the plan's wavelet bank to host memory (synchronous).

@@ -88,6 +88,8 @@ cwt_status run_execute(cwt_plan_s *p, const void *sig, void *oc, void *op, void 
 }
 
 void free_plan_memory(cwt_plan_s *p) {
+    cwtk::free_batch_state(p->batch);
+    p->batch = nullptr;
     cudaFree(p->bank);
     cudaFree(p->band);
     cudaFree(p->spec);
@@ -318,6 +320,45 @@ cwt_status cwt_execute_host(cwt_plan p, const void *h_signal, void *h_complex, v
         e = cudaMemcpyAsync(h_phase, p->stage_ph, out_b, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+}
+
+cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, const void *d_in,
+                             void *d_complex, void *d_power, void *d_phase, void *stream) {
+    if (!p || n_epochs < 0 || (n_epochs > 0 && !epochs)) return CWT_EINVAL;
+    const bool wc = p->outputs & CWT_OUT_COMPLEX, wp = p->outputs & CWT_OUT_POWER,
+               wph = p->outputs & CWT_OUT_PHASE;
+    if (wc != (d_complex != nullptr) || wp != (d_power != nullptr) || wph != (d_phase != nullptr))
+        return CWT_EINVAL;
+    if (p->io != CWT_DTYPE_F32) return CWT_EUNSUPPORTED;
+    for (int i = 0; i < n_epochs; ++i) {
+        const cwt_epoch &e = epochs[i];
+        if (e.samples < 1 || e.samples > p->n || e.in_offset < 0 || e.out_offset < 0) return CWT_EINVAL;
+        if (e.samples > 8192) return CWT_EUNSUPPORTED;
+    }
+    if (n_epochs == 0) return CWT_OK;
+    DeviceGuard g(p->device);
+    if (!g.ok) return CWT_ECUDA;
+    if (!device_ptr_ok(d_in, p->device)) return CWT_EINVAL;
+    if (wc && !device_ptr_ok(d_complex, p->device)) return CWT_EINVAL;
+    if (wp && !device_ptr_ok(d_power, p->device)) return CWT_EINVAL;
+    if (wph && !device_ptr_ok(d_phase, p->device)) return CWT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // prepare (banks, work items, autotuning on a new shape), then one timed launch
+    cudaError_t e = cwtk::batch_execute(p, epochs, n_epochs, (const float *)d_in, (float2 *)d_complex,
+                                        (float *)d_power, (float *)d_phase, st, true);
+    cwtk::ProfEvent ev{};
+    if (e == cudaSuccess) e = prof_begin(p, CWT_KERNEL_BATCH, st, &ev);
+    if (e == cudaSuccess)
+        e = cwtk::batch_execute(p, epochs, n_epochs, (const float *)d_in, (float2 *)d_complex,
+                                (float *)d_power, (float *)d_phase, st, false);
+    if (e == cudaSuccess) e = prof_end(p, st, &ev);
+    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+}
+
+cwt_status cwt_plan_batch_stats(cwt_plan p, cwt_batch_stats *stats) {
+    if (!p || !stats) return CWT_EINVAL;
+    cwtk::batch_stats(p, stats);
+    return CWT_OK;
 }
 
 cwt_status cwt_plan_bank(cwt_plan p, float *h_bank, int *h_band_start, int *h_band_len) {

@@ -1,0 +1,435 @@
+// batch.cu -- many epochs of uneven length in one persistent launch.
+//
+// The paper loops over recordings in Python (Sections "Comparison between
+// devices and software" and "Wavelength and flexibility"); here a batch of
+// epochs, each with its own length n_e and hence its own padded length
+// N_e = next power of two >= max(n_e, 32) (Section "Fast Fourier transform"),
+// is one persistent kernel replayed from a CUDA graph.
+//
+// Work item = (epoch, group of G channels) with G * N_e = one tile of kTile
+// points (G capped by the channel count).  Per item the CTA
+//   1. runs the forward FFT of the G channels (Eq. 2, one FFT per channel)
+//      and keeps the spectra in shared memory -- they never reach HBM;
+//   2. for every (channel, scale) row: band product with the FP64-generated
+//      bank of length N_e (Eq. 3), spectral fold by the power-of-two factor f
+//      of the decimation, inverse FFT of N_e / f points, crop / decimate /
+//      reduce and coalesced stores (Section "Precision").
+// CTAs pull items from an atomic counter, largest FFTs first by default.  An
+// autotuner times the candidate schedules (inverse radix 16 or 32, item
+// order) on the first batch of a given shape and keeps the fastest; every
+// candidate computes the same values.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace cwtk {
+
+namespace {
+
+constexpr int kBThreads = 512;
+constexpr int kTile = kBThreads * 16;  // 8192 points per item
+constexpr int kMaxBatchLog2 = 13;      // N_e <= kTile
+
+struct BatchItem {
+    long long in_off;   // element offset of channel c0 of the epoch in the packed input
+    long long out_off;  // element offset of row (c0, scale 0) in each packed output
+    int n;              // epoch length
+    int log2n;          // log2 N_e
+    int G;              // channels in this item
+    int pad;
+};
+
+struct BatchArgs {
+    const float *in;
+    float2 *oc;
+    float *op;
+    float *oph;
+    const BatchItem *items;
+    int n_items;
+    int *counter;
+    const float *bank[kMaxBatchLog2 + 1];  // per log2 N: [S][N]
+    const int *band[kMaxBatchLog2 + 1];    // per log2 N: [S][2]
+    const float2 *tw;
+    int S, d;
+};
+
+__device__ __noinline__ void batch_store_phase(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
+
+template <int N>
+__device__ __forceinline__ void batch_forward(const BatchArgs &a, const BatchItem &it,
+                                              float2 *spec, float2 *stage) {
+    constexpr int R = N / kBThreads > 16 ? N / kBThreads : 16;
+    constexpr int Tf = N / R;
+    const int g = threadIdx.x / Tf, j = threadIdx.x % Tf;
+    const bool act = g < it.G;
+    const float *x = a.in + it.in_off + (long long)(act ? g : 0) * it.n;
+    float2 *st = stage + g * FftShape<N, R>::SMEM_F2;
+    float2 *sp = spec + g * N;
+    const int n = it.n;
+    auto load = [&](int i) -> float2 { return make_float2((act && i < n) ? x[i] : 0.f, 0.f); };
+    auto store = [&](int t, float2 v) { sp[t] = v; };
+    fft_row<N, R, -1>(st, a.tw, j, load, store);
+}
+
+template <int M, int RI>
+__device__ __forceinline__ void batch_inverse(const BatchArgs &a, const BatchItem &it,
+                                              const float2 *spec, float2 *stage, int N, int fold) {
+    constexpr int R = (M / RI) > kBThreads ? M / kBThreads : (M < RI ? M : RI);
+    constexpr int Ti = M / R;
+    constexpr int P = kBThreads / Ti;  // rows in flight
+    const int rows = it.G * a.S;
+    const float *bank = a.bank[it.log2n];
+    const int *band = a.band[it.log2n];
+    const int nmask = N - 1;
+    const int sub = a.d / fold;
+    const int n_out = (it.n + a.d - 1) / a.d;
+    const int rl = threadIdx.x / Ti, j = threadIdx.x % Ti;
+    float2 *st = stage + rl * FftShape<M, R>::SMEM_F2;
+#pragma unroll 1
+    for (int r0 = 0; r0 < rows; r0 += P) {
+        const int row = r0 + rl;
+        const bool act = row < rows;
+        const int g = act ? row / a.S : 0;
+        const int s = act ? row - g * a.S : 0;
+        const float2 *sp = spec + g * N;
+        const float *W = bank + (size_t)s * N;
+        const int b0 = band[2 * s], B = act ? band[2 * s + 1] : 0;
+        auto load = [&](int jj) -> float2 {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int q = 0; q < fold; ++q) {
+                const int k = jj + q * M;
+                if (((k - b0) & nmask) < B) {
+                    const float2 xv = sp[k];
+                    const float w = __ldg(&W[k]);
+                    acc.x = fmaf(xv.x, w, acc.x);
+                    acc.y = fmaf(xv.y, w, acc.y);
+                }
+            }
+            return acc;
+        };
+        const long long obase = it.out_off + (long long)row * n_out;
+        auto store = [&](int t, float2 v) {
+            if (!act) return;
+            int o = t;
+            if (sub != 1) {
+                if (t % sub) return;
+                o = t / sub;
+            }
+            if (o >= n_out) return;
+            if (a.oc) a.oc[obase + o] = v;
+            if (a.op) a.op[obase + o] = fmaf(v.x, v.x, v.y * v.y);
+            if (a.oph) batch_store_phase(a.oph + obase + o, v);
+        };
+        fft_row<M, R, +1>(st, a.tw, j, load, store);
+    }
+}
+
+template <int RI>
+__device__ __forceinline__ void batch_inverse_dispatch(const BatchArgs &a, const BatchItem &it,
+                                                       const float2 *spec, float2 *stage) {
+    const int N = 1 << it.log2n;
+    int fold = 1;
+    while ((a.d % (2 * fold)) == 0 && N / (2 * fold) >= kMinFft) fold *= 2;
+    switch (it.log2n - ilog2c(fold)) {
+        case 5: batch_inverse<1 << 5, RI>(a, it, spec, stage, N, fold); break;
+        case 6: batch_inverse<1 << 6, RI>(a, it, spec, stage, N, fold); break;
+        case 7: batch_inverse<1 << 7, RI>(a, it, spec, stage, N, fold); break;
+        case 8: batch_inverse<1 << 8, RI>(a, it, spec, stage, N, fold); break;
+        case 9: batch_inverse<1 << 9, RI>(a, it, spec, stage, N, fold); break;
+        case 10: batch_inverse<1 << 10, RI>(a, it, spec, stage, N, fold); break;
+        case 11: batch_inverse<1 << 11, RI>(a, it, spec, stage, N, fold); break;
+        case 12: batch_inverse<1 << 12, RI>(a, it, spec, stage, N, fold); break;
+        case 13: batch_inverse<1 << 13, RI>(a, it, spec, stage, N, fold); break;
+        default: break;
+    }
+}
+
+// Shared memory: spectra (kTile float2) + staging for kBThreads * RI points
+// (every thread holds RI points of some row in flight), padded 17/16.
+template <int RI>
+constexpr int batch_smem() { return (kTile + (kBThreads * RI) * 17 / 16) * 8; }
+
+template <int RI>
+__global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchArgs a) {
+    extern __shared__ float2 bsm[];
+    float2 *spec = bsm;
+    float2 *stage = bsm + kTile;
+    __shared__ int s_item;
+#pragma unroll 1
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_items) break;
+        const BatchItem it = a.items[item];
+        switch (it.log2n) {
+            case 5: batch_forward<1 << 5>(a, it, spec, stage); break;
+            case 6: batch_forward<1 << 6>(a, it, spec, stage); break;
+            case 7: batch_forward<1 << 7>(a, it, spec, stage); break;
+            case 8: batch_forward<1 << 8>(a, it, spec, stage); break;
+            case 9: batch_forward<1 << 9>(a, it, spec, stage); break;
+            case 10: batch_forward<1 << 10>(a, it, spec, stage); break;
+            case 11: batch_forward<1 << 11>(a, it, spec, stage); break;
+            case 12: batch_forward<1 << 12>(a, it, spec, stage); break;
+            case 13: batch_forward<1 << 13>(a, it, spec, stage); break;
+            default: break;
+        }
+        __syncthreads();  // spectra complete before any row reads them
+        batch_inverse_dispatch<RI>(a, it, spec, stage);
+        __syncthreads();  // s_item and the spectra are free again
+    }
+}
+
+}  // namespace
+
+// ---- host side -------------------------------------------------------------
+
+struct BatchState {
+    float *bank[kMaxBatchLog2 + 1] = {};
+    int *band[kMaxBatchLog2 + 1] = {};
+    BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
+    int *d_counter = nullptr;
+    std::vector<BatchItem> h_items_natural, h_items_sorted;
+    std::vector<BatchItem> uploaded;
+    // CUDA graph: memset(counter) -> batch_kernel
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t knode = nullptr;
+    int graph_ri = 0;
+    BatchArgs graph_args{};
+    // autotuner
+    bool tuned = false;
+    int ri = 16, order = 0;
+    double tune_ms[4] = {0, 0, 0, 0};
+    long long launches = 0;
+    int grid = 0;
+    size_t bytes = 0;
+};
+
+void free_batch_state(BatchState *b) {
+    if (!b) return;
+    for (int i = 0; i <= kMaxBatchLog2; ++i) {
+        cudaFree(b->bank[i]);
+        cudaFree(b->band[i]);
+    }
+    cudaFree(b->d_items);
+    cudaFree(b->d_counter);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+namespace {
+
+template <int RI>
+cudaError_t batch_attr() {
+    static unsigned done = 0;
+    return ensure_smem_attr(batch_kernel<RI>, batch_smem<RI>(), &done);
+}
+
+cudaError_t batch_grid(int ri, int *grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = ri == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<16>, kBThreads,
+                                                                     batch_smem<16>())
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<32>, kBThreads,
+                                                                     batch_smem<32>());
+    if (e == cudaSuccess) *grid = sms * std::max(per, 1);
+    return e;
+}
+
+// (Re)build the graph for radix `ri` with arguments `args`, or update its
+// kernel node in place when only the arguments changed.
+cudaError_t batch_graph(BatchState *b, int ri, const BatchArgs &args, int grid) {
+    cudaKernelNodeParams kp{};
+    void *kargs[] = {(void *)&args};
+    kp.func = ri == 16 ? (void *)batch_kernel<16> : (void *)batch_kernel<32>;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(kBThreads);
+    kp.sharedMemBytes = ri == 16 ? batch_smem<16>() : batch_smem<32>();
+    kp.kernelParams = kargs;
+    if (b->exec && b->graph_ri == ri) {
+        if (std::memcmp(&b->graph_args, &args, sizeof(args)) == 0) return cudaSuccess;
+        cudaError_t e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp);
+        if (e == cudaSuccess) b->graph_args = args;
+        return e;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&b->graph, 0);
+    cudaGraphNode_t mnode;
+    cudaMemsetParams mp{};
+    mp.dst = b->d_counter;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    mp.value = 0;
+    if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&mnode, b->graph, nullptr, 0, &mp);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&b->knode, b->graph, &mnode, 1, &kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
+        b->graph_ri = ri;
+        b->graph_args = args;
+    }
+    return e;
+}
+
+}  // namespace
+
+cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, const float *in,
+                          float2 *oc, float *op, float *oph, cudaStream_t st, bool prepare_only) {
+    if (!p->batch) p->batch = new BatchState();
+    BatchState *b = p->batch;
+    cudaError_t e = cudaSuccess;
+    if (!b->d_counter) {
+        e = cudaMalloc(&b->d_counter, sizeof(int));
+        if (e != cudaSuccess) return e;
+    }
+    // banks for every padded length in the batch (generated once per length)
+    const int C = p->C, S = p->S;
+    std::vector<BatchItem> items;
+    for (int ei = 0; ei < n_epochs; ++ei) {
+        const cwt_epoch &ep = epochs[ei];
+        int N = kMinFft;
+        while (N < ep.samples) N <<= 1;
+        const int L = ilog2c(N);
+        if (!b->bank[L]) {
+            e = cudaMalloc(&b->bank[L], sizeof(float) * (size_t)S * N);
+            if (e == cudaSuccess) e = cudaMalloc(&b->band[L], sizeof(int) * 2 * (size_t)S);
+            if (e == cudaSuccess) e = launch_bank_n(p, N, b->bank[L], b->band[L], st, nullptr);
+            if (e != cudaSuccess) return e;
+            b->bytes += sizeof(float) * (size_t)S * N + sizeof(int) * 2 * (size_t)S;
+        }
+        const int G = std::max(1, std::min(C, kTile / N));
+        const int n_out = (ep.samples + p->d - 1) / p->d;
+        for (int c0 = 0; c0 < C; c0 += G) {
+            BatchItem it{};
+            it.in_off = ep.in_offset + (long long)c0 * ep.samples;
+            it.out_off = ep.out_offset + (long long)c0 * S * n_out;
+            it.n = ep.samples;
+            it.log2n = L;
+            it.G = std::min(G, C - c0);
+            items.push_back(it);
+        }
+    }
+    if (items.empty()) return cudaSuccess;
+    // two orders: input order, and largest FFT first (stable)
+    std::vector<BatchItem> sorted = items;
+    std::stable_sort(sorted.begin(), sorted.end(),
+                     [](const BatchItem &x, const BatchItem &y) { return x.log2n > y.log2n; });
+    const bool shape_changed =
+        items.size() != b->h_items_natural.size() ||
+        std::memcmp(items.data(), b->h_items_natural.data(), items.size() * sizeof(BatchItem)) != 0;
+    if (shape_changed) {
+        b->h_items_natural = items;
+        b->h_items_sorted = sorted;
+        b->tuned = false;
+        if (items.size() > b->items_cap) {
+            cudaFree(b->d_items);
+            b->d_items = nullptr;
+            e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
+            if (e != cudaSuccess) return e;
+            b->items_cap = items.size();
+        }
+    }
+    BatchArgs a;
+    std::memset(&a, 0, sizeof(a));  // padding too: the graph compares argument bytes
+    a.in = in;
+    a.oc = oc;
+    a.op = op;
+    a.oph = oph;
+    a.items = b->d_items;
+    a.n_items = (int)items.size();
+    a.counter = b->d_counter;
+    for (int i = 0; i <= kMaxBatchLog2; ++i) {
+        a.bank[i] = b->bank[i];
+        a.band[i] = b->band[i];
+    }
+    a.tw = p->tw;
+    a.S = S;
+    a.d = p->d;
+    e = batch_attr<16>();
+    if (e == cudaSuccess) e = batch_attr<32>();
+    if (e != cudaSuccess) return e;
+
+    auto upload = [&](int order) -> cudaError_t {
+        const std::vector<BatchItem> &v = order == 0 ? b->h_items_sorted : b->h_items_natural;
+        if (b->uploaded.size() == v.size() &&
+            std::memcmp(b->uploaded.data(), v.data(), v.size() * sizeof(BatchItem)) == 0)
+            return cudaSuccess;
+        cudaError_t r = cudaMemcpyAsync(b->d_items, v.data(), v.size() * sizeof(BatchItem),
+                                        cudaMemcpyHostToDevice, st);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(st);  // host vector may change later
+        if (r == cudaSuccess) b->uploaded = v;
+        return r;
+    };
+    auto run = [&](int ri, int order) -> cudaError_t {
+        cudaError_t r = upload(order);
+        int grid = 0;
+        if (r == cudaSuccess) r = batch_grid(ri, &grid);
+        if (r == cudaSuccess) r = batch_graph(b, ri, a, grid);
+        if (r == cudaSuccess) r = cudaGraphLaunch(b->exec, st);
+        if (r == cudaSuccess) {
+            b->grid = grid;
+            ++b->launches;
+        }
+        return r;
+    };
+
+    if (!b->tuned) {
+        // autotune: time each (radix, order) candidate once on this batch
+        const int cands[4][2] = {{16, 0}, {32, 0}, {16, 1}, {32, 1}};
+        cudaEvent_t t0, t1;
+        e = cudaEventCreate(&t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t1);
+        double best = 1e300;
+        for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+            e = run(cands[c][0], cands[c][1]);  // warm (graph build, upload)
+            if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+            if (e == cudaSuccess) e = run(cands[c][0], cands[c][1]);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            b->tune_ms[c] = ms;
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                b->ri = cands[c][0];
+                b->order = cands[c][1];
+            }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (e != cudaSuccess) return e;
+        b->tuned = true;
+    }
+    if (prepare_only) return cudaSuccess;
+    return run(b->ri, b->order);
+}
+
+void batch_stats(const cwt_plan_s *p, cwt_batch_stats *s) {
+    std::memset(s, 0, sizeof(*s));
+    const BatchState *b = p->batch;
+    if (!b) return;
+    s->items = (int)b->h_items_natural.size();
+    s->grid = b->grid;
+    s->inverse_radix = b->ri;
+    s->order = b->order;
+    s->tuned = b->tuned;
+    for (int i = 0; i < 4; ++i) s->tune_ms[i] = b->tune_ms[i];
+    s->graph_launches = b->launches;
+    s->bank_bytes = b->bytes;
+}
+
+}  // namespace cwtk

@@ -189,20 +189,37 @@ __device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *_
             return;
         } else {
             __syncthreads();  // the buffer may still be read by a previous row
+            // (jj*R0 + r) >> 4 == (jj*R0) >> 4 for r < R0 <= 16, and T*R0 is a
+            // multiple of 16, so each group is one base plus constant offsets.
 #pragma unroll
-            for (int g = 0; g < G0; ++g)
+            for (int g = 0; g < G0; ++g) {
+                if constexpr (R0 <= 16) {
+                    float2 *dst = sm + spad2((j + g * T) * R0);
 #pragma unroll
-                for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
+                    for (int r = 0; r < R0; ++r) dst[r] = v[g * R0 + r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
+                }
+            }
         }
     }
     // ---- passes 1..NP-1: radix R, Ns = R0 * R^(p-1)
+    // Reads j + r*T (T a multiple of 16) and, for Ns >= 16, writes base + r*Ns
+    // are one padded base plus constant strides T*17/16 and Ns*17/16.
+    const float2 *src = sm + spad2(j);
     int Ns = R0;
 #pragma unroll 1
     for (int p = 1; p < S::NP; ++p) {
         __syncthreads();
         float2 v[R];
+        if constexpr (T % 16 == 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
+            for (int r = 0; r < R; ++r) v[r] = src[r * (T + T / 16)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
+        }
         const int k = j & (Ns - 1);
         float2 w1 = __ldg(&tw[k * (kTwN / (Ns * R))]);
         if (SIGN < 0) w1.y = -w1.y;
@@ -214,8 +231,15 @@ __device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *_
         } else {
             __syncthreads();
             const int base = (j - k) * R + k;
+            if (Ns >= 16) {
+                float2 *dst = sm + spad2(base);
+                const int stride = Ns + (Ns >> 4);
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
+                for (int r = 0; r < R; ++r) dst[r * stride] = v[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
+            }
         }
         Ns *= R;
     }

@@ -19,6 +19,9 @@ constexpr double kBandRelThreshold = 1e-10;  // bins below this fraction of a sc
 // Per-device FP32 twiddle table exp(2 pi i m / 2^17), built in FP64 on first use.
 cudaError_t device_twiddles(const float2 **out);
 
+struct BatchState;
+void free_batch_state(BatchState *b);
+
 struct ProfEvent {
     int kernel;
     cudaEvent_t start, stop;
@@ -52,6 +55,8 @@ struct cwt_plan_s {
     void *stage_in = nullptr, *stage_c = nullptr, *stage_p = nullptr, *stage_ph = nullptr;
     size_t stage_bytes = 0;
 
+    cwtk::BatchState *batch = nullptr;  // batch path state (banks per length, graph, tuning)
+
     bool profiling = false;
     std::vector<cwtk::ProfEvent> prof, prof_pool;
     std::string last_error;
@@ -74,10 +79,20 @@ cudaError_t ensure_smem_attr(K *kernel, int bytes, unsigned *done) {
 
 // Launchers (return the launch error, if any).
 cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st);
+// Bank and bands of the plan's scales for padded length N into the given
+// buffers ([S][N] floats, [S][2] ints); synchronises `st`.
+cudaError_t launch_bank_n(const cwt_plan_s *p, int N, float *bank, int *band, cudaStream_t st,
+                          double *ms_out);
 cudaError_t launch_forward(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 cudaError_t launch_scale_block(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
                                cudaStream_t st);
 cudaError_t launch_fft(const float2 *in, float2 *out, int log2n, int batch, int sign,
                        const float2 *tw, cudaStream_t st);
+// prepare_only: build the work items, generate missing banks and autotune a
+// new batch shape (its candidate runs write valid outputs); otherwise launch
+// the chosen schedule's graph once.
+cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, const float *in,
+                          float2 *oc, float *op, float *oph, cudaStream_t st, bool prepare_only);
+void batch_stats(const cwt_plan_s *p, cwt_batch_stats *s);
 
 }  // namespace cwtk

@@ -179,7 +179,12 @@ cudaError_t device_twiddles(const float2 **out) {
 }
 
 cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st) {
-    const int N = p->N, S = p->S;
+    return launch_bank_n(p, p->N, p->bank, p->band, st, &p->bank_ms);
+}
+
+cudaError_t launch_bank_n(const cwt_plan_s *p, int N, float *bank, int *band, cudaStream_t st,
+                          double *ms_out) {
+    const int S = p->S;
     const int nblk = (N + kBankThreads - 1) / kBankThreads;
     double *raw = nullptr, *partial = nullptr, *dF = nullptr, *dsig = nullptr;
     cudaError_t e = cudaMalloc(&raw, sizeof(double) * (size_t)S * N);
@@ -201,14 +206,14 @@ cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st) {
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        bank_finish_kernel<<<S, kBankThreads, 0, st>>>(N, nblk, raw, partial, p->bank, p->band);
+        bank_finish_kernel<<<S, kBankThreads, 0, st>>>(N, nblk, raw, partial, bank, band);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(t1, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess) p->bank_ms = ms;
+        if (cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms_out) *ms_out = ms;
     }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);

@@ -28,7 +28,7 @@ CWT_OUT_COMPLEX, CWT_OUT_POWER, CWT_OUT_PHASE = 1, 2, 4
 CWT_PREC_FP32, CWT_PREC_TC_FP16, CWT_PREC_TC_BF16 = 0, 1, 2
 CWT_DTYPE_F32, CWT_DTYPE_F64 = 0, 1
 CWT_PAD_POW2, CWT_PAD_SMOOTH = 0, 1
-CWT_KERNEL_BANK, CWT_KERNEL_FORWARD_FFT, CWT_KERNEL_SCALE_BLOCK = 0, 1, 2
+CWT_KERNEL_BANK, CWT_KERNEL_FORWARD_FFT, CWT_KERNEL_SCALE_BLOCK, CWT_KERNEL_BATCH = 0, 1, 2, 3
 
 
 class cwt_options(ctypes.Structure):
@@ -43,6 +43,18 @@ class cwt_plan_info_t(ctypes.Structure):
                 ("fold", ctypes.c_int), ("inverse_length", ctypes.c_int), ("device", ctypes.c_int),
                 ("io_dtype", ctypes.c_int), ("output_kinds", ctypes.c_uint),
                 ("workspace_bytes", ctypes.c_size_t), ("bank_ms", ctypes.c_double)]
+
+
+class cwt_epoch(ctypes.Structure):
+    _fields_ = [("in_offset", ctypes.c_longlong), ("out_offset", ctypes.c_longlong),
+                ("samples", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class cwt_batch_stats(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int), ("grid", ctypes.c_int), ("inverse_radix", ctypes.c_int),
+                ("order", ctypes.c_int), ("tuned", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("tune_ms", ctypes.c_double * 4), ("graph_launches", ctypes.c_longlong),
+                ("bank_bytes", ctypes.c_size_t)]
 
 
 _vp = ctypes.c_void_p
@@ -74,6 +86,9 @@ _sig("cwt_plan_bank", ctypes.c_int, [_vp, _fp, _ip, _ip])
 _sig("cwt_fft", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp])
 _sig("cwt_execute_noalloc", ctypes.c_int,
      [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp])
+_sig("cwt_execute_batch", ctypes.c_int,
+     [_vp, ctypes.POINTER(cwt_epoch), ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
+_sig("cwt_plan_batch_stats", ctypes.c_int, [_vp, ctypes.POINTER(cwt_batch_stats)])
 _sig("cwt_plan_set_profiling", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("cwt_plan_profile_read", ctypes.c_int,
      [_vp, ctypes.c_int, _ip, _dp, ctypes.c_int])
@@ -200,6 +215,33 @@ def cwt_execute_noalloc(signal, channels, samples, fs, freqs_hz, n_cycles, compl
                                   _ptr(complex_out), _ptr(power_out), _ptr(phase_out),
                                   _stream(stream))
     _check(st, "cwt_execute_noalloc")
+
+
+def pack_epochs(lengths, channels, scales, decimation=1):
+    """Packed layout for cwt_execute_batch: epochs back to back, each epoch's
+    signal [C][n_e] and outputs [C][S][ceil(n_e/d)].  Returns (epochs array,
+    total input elements, total output elements per output array)."""
+    arr = (cwt_epoch * len(lengths))()
+    i_off = o_off = 0
+    for k, n in enumerate(lengths):
+        n = int(n)
+        arr[k].in_offset, arr[k].out_offset, arr[k].samples = i_off, o_off, n
+        i_off += channels * n
+        o_off += channels * scales * (-(-n // decimation))
+    return arr, i_off, o_off
+
+
+def cwt_execute_batch(plan, epochs, d_in, complex_out=None, power_out=None, phase_out=None,
+                      stream=None):
+    st = _lib.cwt_execute_batch(plan, epochs, len(epochs), _ptr(d_in), _ptr(complex_out),
+                                _ptr(power_out), _ptr(phase_out), _stream(stream))
+    _check(st, "cwt_execute_batch")
+
+
+def cwt_plan_batch_stats(plan):
+    s = cwt_batch_stats()
+    _check(_lib.cwt_plan_batch_stats(plan, ctypes.byref(s)), "cwt_plan_batch_stats")
+    return s
 
 
 def cwt_plan_set_profiling(plan, enable):
