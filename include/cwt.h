@@ -229,6 +229,79 @@ cwt_status cwt_execute_batch(cwt_plan plan, const cwt_epoch *epochs, int n_epoch
 /* Statistics of the plan's batch path (zeros before the first batch). */
 cwt_status cwt_plan_batch_stats(cwt_plan plan, cwt_batch_stats *stats);
 
+/* ---------------------------------------------------------------------------
+ * Streaming (live EEG).  The paper's aim is real-time analysis (Abstract;
+ * Discussion: 64-channel EEG transformed several times per second).  A server
+ * keeps many live streams; each hop of H = ceil(fs * hop_seconds) new samples
+ * yields the CWT power of the window x[e - W, e) (cyclic, Eq. 2 with N = W,
+ * zeros before the first sample) at the H window positions
+ * [W - D - H, W - D), D = floor((W - H) / 2), i.e. absolute sample times
+ * [e - D - H, e - D).  Every ready hop of every open stream goes into the
+ * next cwt_server_step launch (continuous batching).
+ * ------------------------------------------------------------------------- */
+typedef struct cwt_server_s *cwt_server;
+
+typedef struct {
+    int max_streams;          /* stream slots (default 32) */
+    int window;               /* W = N; only 2048 is built */
+    double hop_seconds;       /* hop length in seconds (default 0.05) */
+    size_t mem_budget_bytes;  /* device bytes for streams (0 = no limit) */
+    unsigned output_kinds;    /* only CWT_OUT_POWER is built */
+    int reserved[7];
+} cwt_server_options;
+
+typedef struct {
+    int open_streams;
+    int reserved;
+    long long admitted, refused;  /* cwt_stream_open outcomes since the last reset */
+    long long hops, launches;     /* hops completed, batched launches */
+    long long coefficients;       /* power values delivered (C * S * H per hop) */
+    size_t device_bytes;          /* device memory held by banks and streams */
+    double latency_p50_s, latency_p99_s, latency_max_s, latency_mean_s;
+    double span_s;                /* first hop ready -> last hop done */
+} cwt_server_stats_t;
+
+cwt_status cwt_server_options_init(cwt_server_options *opt);
+
+/* A server for the scales freqs_hz/n_cycles (host arrays, as cwt_plan_create)
+ * on the current device.  Streams are opened later with their own fs. */
+cwt_status cwt_server_create(cwt_server *out, const double *freqs_hz, const double *n_cycles,
+                             int n_freqs, int wavelet, const cwt_server_options *opt);
+/* Waits for in-flight work, frees everything. */
+cwt_status cwt_server_destroy(cwt_server srv);
+
+/* Admit a stream of `channels` channels sampled at fs Hz (every frequency must
+ * be < fs/2).  CWT_EBUSY when no slot is free or its device memory would
+ * exceed the budget (the refusal is counted).  Generates the bank for a new fs. */
+cwt_status cwt_stream_open(cwt_server srv, int channels, double fs, int *stream_id);
+
+/* Append k new samples per channel: samples is [channels][k] float32, host or
+ * device memory.  Hops completed by these samples become ready.  CWT_EBUSY if
+ * the stream already holds 8 unpulled hops (step the server and pull first). */
+cwt_status cwt_stream_push(cwt_server srv, int stream_id, const float *samples, int k);
+
+/* Launch one batch with every ready hop of every open stream, asynchronously
+ * on the server's own CUDA stream (two batches may be in flight; a third call
+ * waits for the oldest).  *hops_launched (may be NULL) receives the count. */
+cwt_status cwt_server_step(cwt_server srv, int *hops_launched);
+
+/* Wait until every launched batch has completed. */
+cwt_status cwt_server_sync(cwt_server srv);
+
+/* Copy up to max_hops completed hops, oldest first, into out: each hop is a
+ * [channels][S][H] float32 block (power).  *first_sample receives the absolute
+ * time (in samples) of the first returned output (may be NULL).  CWT_EAGAIN
+ * with *n_hops = 0 when none is complete yet. */
+cwt_status cwt_stream_pull(cwt_server srv, int stream_id, float *out, int max_hops, int *n_hops,
+                           long long *first_sample);
+
+/* Close a stream (waits for its launched hops, frees its slot and memory). */
+cwt_status cwt_stream_close(cwt_server srv, int stream_id);
+
+/* Latency percentiles (ready -> output in host memory), throughput counters. */
+cwt_status cwt_server_stats(cwt_server srv, cwt_server_stats_t *stats);
+cwt_status cwt_server_reset_stats(cwt_server srv);
+
 /*
  * cwt_plan_bank -- copy the plan's wavelet bank to host memory (synchronous).
  *   h_bank        [S][N] float32: the real spectrum W_s[k] / N actually used

@@ -100,8 +100,21 @@ __device__ __forceinline__ void batch_inverse(const BatchArgs &a, const BatchIte
         const float2 *sp = spec + g * N;
         const float *W = bank + (size_t)s * N;
         const int b0 = band[2 * s], B = act ? band[2 * s + 1] : 0;
+        // Folded input j = sum over in-band k = j (mod M).  When the band is no
+        // wider than M, at most one k qualifies: k = b0 + ((j - b0) mod M).
+        const bool narrow = B <= M;
         auto load = [&](int jj) -> float2 {
             float2 acc = make_float2(0.f, 0.f);
+            if (narrow) {
+                const int delta = (jj - b0) & (M - 1);
+                if (delta < B) {
+                    const int k = (b0 + delta) & nmask;
+                    const float2 xv = sp[k];
+                    const float w = __ldg(&W[k]);
+                    acc = make_float2(xv.x * w, xv.y * w);
+                }
+                return acc;
+            }
             for (int q = 0; q < fold; ++q) {
                 const int k = jj + q * M;
                 if (((k - b0) & nmask) < B) {

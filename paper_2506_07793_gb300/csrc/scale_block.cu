@@ -62,12 +62,18 @@ scale_block_kernel(const SBArgs a) {
     const int nmask = a.N - 1;
     const int fold = a.fold;
 
+    // Folded input j = sum over in-band k = j (mod M).  When the band is no
+    // wider than M (always for fold 1), at most one k qualifies:
+    // k = b0 + ((j - b0) mod M).
+    const bool narrow = B <= M;
     auto load = [&](int jj) -> float2 {
         float2 acc = make_float2(0.f, 0.f);
-        if (fold == 1) {
-            if (((jj - b0) & nmask) < B) {
-                const float2 x = X[jj];
-                const float w = W[jj];
+        if (narrow) {
+            const int delta = (jj - b0) & (M - 1);
+            if (delta < B) {
+                const int k = (b0 + delta) & nmask;
+                const float2 x = X[k];
+                const float w = W[k];
                 acc = make_float2(x.x * w, x.y * w);
             }
             return acc;

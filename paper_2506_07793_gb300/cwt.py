@@ -57,6 +57,22 @@ class cwt_batch_stats(ctypes.Structure):
                 ("bank_bytes", ctypes.c_size_t)]
 
 
+class cwt_server_options(ctypes.Structure):
+    _fields_ = [("max_streams", ctypes.c_int), ("window", ctypes.c_int),
+                ("hop_seconds", ctypes.c_double), ("mem_budget_bytes", ctypes.c_size_t),
+                ("output_kinds", ctypes.c_uint), ("reserved", ctypes.c_int * 7)]
+
+
+class cwt_server_stats_t(ctypes.Structure):
+    _fields_ = [("open_streams", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("admitted", ctypes.c_longlong), ("refused", ctypes.c_longlong),
+                ("hops", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("coefficients", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
+                ("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
+                ("latency_max_s", ctypes.c_double), ("latency_mean_s", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -89,6 +105,19 @@ _sig("cwt_execute_noalloc", ctypes.c_int,
 _sig("cwt_execute_batch", ctypes.c_int,
      [_vp, ctypes.POINTER(cwt_epoch), ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("cwt_plan_batch_stats", ctypes.c_int, [_vp, ctypes.POINTER(cwt_batch_stats)])
+_sig("cwt_server_options_init", ctypes.c_int, [ctypes.POINTER(cwt_server_options)])
+_sig("cwt_server_create", ctypes.c_int, [ctypes.POINTER(_vp), _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(cwt_server_options)])
+_sig("cwt_server_destroy", ctypes.c_int, [_vp])
+_sig("cwt_stream_open", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _ip])
+_sig("cwt_stream_push", ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int])
+_sig("cwt_server_step", ctypes.c_int, [_vp, _ip])
+_sig("cwt_server_sync", ctypes.c_int, [_vp])
+_sig("cwt_stream_pull", ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _ip,
+                                       ctypes.POINTER(ctypes.c_longlong)])
+_sig("cwt_stream_close", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("cwt_server_stats", ctypes.c_int, [_vp, ctypes.POINTER(cwt_server_stats_t)])
+_sig("cwt_server_reset_stats", ctypes.c_int, [_vp])
 _sig("cwt_plan_set_profiling", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("cwt_plan_profile_read", ctypes.c_int,
      [_vp, ctypes.c_int, _ip, _dp, ctypes.c_int])
@@ -314,3 +343,79 @@ class CWT:
         cwt_execute(self.plan, signal, out.get("complex"), out.get("power"), out.get("phase"),
                     stream)
         return out
+
+
+# ---- streaming server ----
+
+def cwt_server_options_init():
+    o = cwt_server_options()
+    _check(_lib.cwt_server_options_init(ctypes.byref(o)), "cwt_server_options_init")
+    return o
+
+
+def cwt_server_create(freqs_hz, n_cycles, wavelet=CWT_WAVELET_MORLET, options=None):
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64).reshape(-1))
+    c = np.ascontiguousarray(np.broadcast_to(np.asarray(n_cycles, dtype=np.float64), f.shape))
+    h = _vp()
+    _check(_lib.cwt_server_create(ctypes.byref(h), f.ctypes.data_as(_dp), c.ctypes.data_as(_dp),
+                                  len(f), int(wavelet),
+                                  ctypes.byref(options) if options is not None else None),
+           "cwt_server_create")
+    return h.value
+
+
+def cwt_server_destroy(srv):
+    _check(_lib.cwt_server_destroy(srv), "cwt_server_destroy")
+
+
+def cwt_stream_open(srv, channels, fs):
+    i = ctypes.c_int(-1)
+    _check(_lib.cwt_stream_open(srv, int(channels), float(fs), ctypes.byref(i)), "cwt_stream_open")
+    return i.value
+
+
+def cwt_stream_push(srv, stream_id, samples):
+    """samples: [C][k] float32 (numpy, C-contiguous, or a torch tensor)."""
+    if isinstance(samples, np.ndarray):
+        samples = np.ascontiguousarray(samples, dtype=np.float32)
+        k = samples.shape[-1]
+    else:
+        k = samples.shape[-1]
+    _check(_lib.cwt_stream_push(srv, int(stream_id), _ptr(samples), int(k)), "cwt_stream_push")
+
+
+def cwt_server_step(srv):
+    n = ctypes.c_int(0)
+    _check(_lib.cwt_server_step(srv, ctypes.byref(n)), "cwt_server_step")
+    return n.value
+
+
+def cwt_server_sync(srv):
+    _check(_lib.cwt_server_sync(srv), "cwt_server_sync")
+
+
+def cwt_stream_pull(srv, stream_id, out):
+    """Fill `out` ([max_hops][C][S][H] float32, C-contiguous) with completed
+    hops; returns (n_hops, first_sample) -- (0, None) when none is ready."""
+    n = ctypes.c_int(0)
+    first = ctypes.c_longlong(0)
+    st = _lib.cwt_stream_pull(srv, int(stream_id), _ptr(out), int(out.shape[0]), ctypes.byref(n),
+                              ctypes.byref(first))
+    if st == CWT_EAGAIN:
+        return 0, None
+    _check(st, "cwt_stream_pull")
+    return n.value, first.value
+
+
+def cwt_stream_close(srv, stream_id):
+    _check(_lib.cwt_stream_close(srv, int(stream_id)), "cwt_stream_close")
+
+
+def cwt_server_stats(srv):
+    s = cwt_server_stats_t()
+    _check(_lib.cwt_server_stats(srv, ctypes.byref(s)), "cwt_server_stats")
+    return s
+
+
+def cwt_server_reset_stats(srv):
+    _check(_lib.cwt_server_reset_stats(srv), "cwt_server_reset_stats")
