@@ -276,8 +276,10 @@ cwt_status cwt_server_destroy(cwt_server srv);
 cwt_status cwt_stream_open(cwt_server srv, int channels, double fs, int *stream_id);
 
 /* Append k new samples per channel: samples is [channels][k] float32, host or
- * device memory.  Hops completed by these samples become ready.  CWT_EBUSY if
- * the stream already holds 8 unpulled hops (step the server and pull first). */
+ * device memory.  Hops completed by these samples become ready.  CWT_EBUSY
+ * (nothing is pushed) if k > 8 * H or if the stream would then hold more than
+ * 8 hops not yet pulled: step the server and pull first.  One thread feeds a
+ * given stream. */
 cwt_status cwt_stream_push(cwt_server srv, int stream_id, const float *samples, int k);
 
 /* Launch one batch with every ready hop of every open stream, asynchronously

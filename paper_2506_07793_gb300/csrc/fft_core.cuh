@@ -163,63 +163,76 @@ struct FftShape {
 __device__ __forceinline__ int spad2(int i) { return i + (i >> 4); }
 
 // Whole-row FFT, X[t] = sum_k x[k] exp(SIGN 2 pi i k t / N), natural order in
-// and out.  `load(k)` supplies x[k] (pass 0 reads only through it);
-// `store(t, X[t])` receives every output exactly once from the last pass.
+// and out, split in two so that callers can choose how pass 0 is computed:
+//   fft_pass0_dense / fft_pass0_sparse  fill the thread's R registers with the
+//                                       pass-0 butterfly outputs;
+//   fft_finish                          stores them, runs passes 1.. and hands
+//                                       every output to `store(t, X[t])`.
 // `sm` is this row's padded float2 staging buffer (FftShape::SMEM_F2 slots).
-// All threads of the CTA call it together (it contains __syncthreads).
-template <int N, int R, int SIGN, typename Load, typename Store>
-__device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *__restrict__ tw,
-                                        int j, Load &load, Store &store) {
+// All threads of the CTA call them together (they contain __syncthreads).
+
+// Pass 0 (radix R0, Ns = 1, no twiddles), inputs from `load(k)`, k in [0, N).
+template <int N, int R, int SIGN, typename Load>
+__device__ __forceinline__ void fft_pass0_dense(float2 (&v)[R], int j, Load &load) {
     using S = FftShape<N, R>;
     constexpr int T = S::T, R0 = S::R0, G0 = S::G0;
-    // ---- pass 0: radix R0, Ns = 1, no twiddles; inputs from `load`
-    {
-        float2 v[R];
+#pragma unroll
+    for (int g = 0; g < G0; ++g)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[g * R0 + r] = load(j + g * T + r * (N / R0));
+#pragma unroll
+    for (int g = 0; g < G0; ++g) dft<R0, SIGN>(&v[g * R0]);
+}
+
+// Pass 0 when each butterfly's inputs {jj + r N/R0 : r < R0} hold at most one
+// nonzero value: `first(jj, r, x)` returns true with its position r and value
+// x (false: all zero).  The R0-point DFT of x at position r is
+// x * exp(SIGN 2 pi i r m / R0), m < R0 -- a twiddle chain, not a full DFT.
+template <int N, int R, int SIGN, typename First>
+__device__ __forceinline__ void fft_pass0_sparse(float2 (&v)[R], int j, const float2 *__restrict__ tw,
+                                                 First &first) {
+    using S = FftShape<N, R>;
+    constexpr int T = S::T, R0 = S::R0, G0 = S::G0;
+#pragma unroll
+    for (int g = 0; g < G0; ++g) {
+        int r = 0;
+        float2 x = make_float2(0.f, 0.f);
+        const bool nz = first(j + g * T, r, x);
+        float2 w = __ldg(&tw[(r & (R0 - 1)) * (kTwN / R0)]);
+        if (SIGN < 0) w.y = -w.y;
+        if (!nz) x = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < R0; ++m) v[g * R0 + m] = x;
+        twiddle_chain<R0>(&v[g * R0], w);
+    }
+}
+
+template <int N, int R, int SIGN, typename Store>
+__device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ sm,
+                                           const float2 *__restrict__ tw, int j, Store &store) {
+    using S = FftShape<N, R>;
+    constexpr int T = S::T, R0 = S::R0, G0 = S::G0;
+    if constexpr (S::NP == 1) {
 #pragma unroll
         for (int g = 0; g < G0; ++g)
 #pragma unroll
-            for (int r = 0; r < R0; ++r) v[g * R0 + r] = load(j + g * T + r * (N / R0));
+            for (int r = 0; r < R0; ++r) store(j + g * T + r, v[g * R0 + r]);
+        return;
+    } else {
+        __syncthreads();  // the buffer may still be read by a previous row
 #pragma unroll
-        for (int g = 0; g < G0; ++g) dft<R0, SIGN>(&v[g * R0]);
-        if constexpr (S::NP == 1) {
+        for (int g = 0; g < G0; ++g)
 #pragma unroll
-            for (int g = 0; g < G0; ++g)
-#pragma unroll
-                for (int r = 0; r < R0; ++r) store(j + g * T + r, v[g * R0 + r]);
-            return;
-        } else {
-            __syncthreads();  // the buffer may still be read by a previous row
-            // (jj*R0 + r) >> 4 == (jj*R0) >> 4 for r < R0 <= 16, and T*R0 is a
-            // multiple of 16, so each group is one base plus constant offsets.
-#pragma unroll
-            for (int g = 0; g < G0; ++g) {
-                if constexpr (R0 <= 16) {
-                    float2 *dst = sm + spad2((j + g * T) * R0);
-#pragma unroll
-                    for (int r = 0; r < R0; ++r) dst[r] = v[g * R0 + r];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
-                }
-            }
-        }
+            for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
     }
-    // ---- passes 1..NP-1: radix R, Ns = R0 * R^(p-1)
-    // Reads j + r*T (T a multiple of 16) and, for Ns >= 16, writes base + r*Ns
-    // are one padded base plus constant strides T*17/16 and Ns*17/16.
-    const float2 *src = sm + spad2(j);
+    // ---- passes 1..NP-1: radix R, Ns = R0 * R^(p-1).  (Per-element padded
+    // indices measured faster on GB300 than base-plus-stride addressing.)
     int Ns = R0;
 #pragma unroll 1
     for (int p = 1; p < S::NP; ++p) {
         __syncthreads();
-        float2 v[R];
-        if constexpr (T % 16 == 0) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = src[r * (T + T / 16)];
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
-        }
+        for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
         const int k = j & (Ns - 1);
         float2 w1 = __ldg(&tw[k * (kTwN / (Ns * R))]);
         if (SIGN < 0) w1.y = -w1.y;
@@ -231,18 +244,19 @@ __device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *_
         } else {
             __syncthreads();
             const int base = (j - k) * R + k;
-            if (Ns >= 16) {
-                float2 *dst = sm + spad2(base);
-                const int stride = Ns + (Ns >> 4);
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst[r * stride] = v[r];
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
-            }
+            for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
         }
         Ns *= R;
     }
+}
+
+template <int N, int R, int SIGN, typename Load, typename Store>
+__device__ __forceinline__ void fft_row(float2 *__restrict__ sm, const float2 *__restrict__ tw,
+                                        int j, Load &load, Store &store) {
+    float2 v[R];
+    fft_pass0_dense<N, R, SIGN>(v, j, load);
+    fft_finish<N, R, SIGN>(v, sm, tw, j, store);
 }
 
 // Points per thread: a build-time tuning knob (the largest length and the

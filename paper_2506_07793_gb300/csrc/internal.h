@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/cwt.h"
+#include "cwt.h"
 
 namespace cwtk {
 

@@ -68,6 +68,14 @@ scale_block_kernel(const SBArgs a) {
     const bool narrow = B <= M;
     auto load = [&](int jj) -> float2 {
         float2 acc = make_float2(0.f, 0.f);
+        if (fold == 1) {  // k = jj: addresses stay base + constant offsets
+            if (((jj - b0) & nmask) < B) {
+                const float2 x = X[jj];
+                const float w = W[jj];
+                acc = make_float2(x.x * w, x.y * w);
+            }
+            return acc;
+        }
         if (narrow) {
             const int delta = (jj - b0) & (M - 1);
             if (delta < B) {
@@ -112,7 +120,27 @@ scale_block_kernel(const SBArgs a) {
         if (op) op[obase + o] = (IO)fmaf(v.x, v.x, v.y * v.y);
         if (oph) store_phase(oph + obase + o, v);
     };
-    fft_row<M, RC::R, +1>(sm, a.tw, j, load, store);
+    // Narrow band (B <= M/R0): each pass-0 butterfly {jj + r M/R0} meets at
+    // most one in-band bin, k = b0 + ((jj - b0) mod M/R0); its position r
+    // follows from k's folded index k mod M = jj + r M/R0.
+    constexpr int Q = M / FftShape<M, RC::R>::R0;
+    float2 v[RC::R];
+    if (B <= Q) {
+        auto first = [&](int jj, int &r, float2 &x) -> bool {
+            const int d0 = (jj - b0) & (Q - 1);
+            if (d0 >= B) return false;
+            const int k = (b0 + d0) & nmask;
+            r = ((k & (M - 1)) - jj) / Q;
+            const float2 xv = X[k];
+            const float w = W[k];
+            x = make_float2(xv.x * w, xv.y * w);
+            return true;
+        };
+        fft_pass0_sparse<M, RC::R, +1>(v, j, a.tw, first);
+    } else {
+        fft_pass0_dense<M, RC::R, +1>(v, j, load);
+    }
+    fft_finish<M, RC::R, +1>(v, sm, a.tw, j, store);
 }
 
 template <int M, typename IO>
