@@ -146,7 +146,8 @@ cwt_status cwt_options_init(cwt_options *opt);
 /* Padded FFT length N for `samples` under `pad_policy` (Section "Fast Fourier
  * transform"): the next power of two >= max(samples, 32).  Writes *n_fft.
  * CWT_EINVAL if samples < 1; CWT_EUNSUPPORTED if the policy is not built or
- * N exceeds the largest supported length (2^14).  Host-only; no CUDA call. */
+ * N exceeds the largest supported length (2^17; lengths above 2^14 run each
+ * row on a thread-block cluster).  Host-only; no CUDA call. */
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 
 /*
@@ -319,7 +320,7 @@ cwt_status cwt_plan_bank(cwt_plan plan, float *h_bank, int *h_band_start, int *h
  * cwt_fft -- batched, unnormalised complex FFT with the library's Stockham
  * kernels (a building block, exposed for testing and reuse).
  *   d_in, d_out  device [batch][n] complex64, 16-byte aligned; may alias
- *   n            power of two, 32 <= n <= 16384
+ *   n            power of two, 32 <= n <= 131072 (above 16384: one cluster per row)
  *   direction    -1: sum x[m] e^{-2 pi i k m / n};  +1: e^{+2 pi i ...}
  * Asynchronous on `stream`.
  */

@@ -142,7 +142,7 @@ cwt_status cwt_options_init(cwt_options *opt) {
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft) {
     if (!n_fft || samples < 1) return CWT_EINVAL;
     if (pad_policy != CWT_PAD_POW2) return pad_policy == CWT_PAD_SMOOTH ? CWT_EUNSUPPORTED : CWT_EINVAL;
-    if (samples > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+    if (samples > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
     int N = cwtk::kMinFft;
     while (N < samples) N <<= 1;
     *n_fft = N;
@@ -178,7 +178,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     if (o.fft_length != 0) {
         if (o.fft_length < samples || !is_pow2(o.fft_length) || o.fft_length < cwtk::kMinFft)
             return CWT_EINVAL;
-        if (o.fft_length > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+        if (o.fft_length > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
         N = o.fft_length;
     } else {
         cwt_status st = cwt_fft_length(samples, o.pad_policy, &N);
@@ -385,7 +385,7 @@ cwt_status cwt_plan_bank(cwt_plan p, float *h_bank, int *h_band_start, int *h_ba
 cwt_status cwt_fft(const void *d_in, void *d_out, int n, int batch, int direction, void *stream) {
     if (!d_in || !d_out || batch < 0 || !is_pow2(n) || (direction != 1 && direction != -1))
         return CWT_EINVAL;
-    if (n < cwtk::kMinFft || n > cwtk::kMaxFft) return CWT_EUNSUPPORTED;
+    if (n < cwtk::kMinFft || n > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
     if (batch == 0) return CWT_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CWT_ECUDA;

@@ -117,6 +117,7 @@ cudaError_t fft_dispatch(int log2n, const float2 *in, float2 *out, int batch, co
 
 cudaError_t launch_forward(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
     const int log2n = ilog2c(p->N);
+    if (log2n > kMaxFftLog2) return launch_forward_cluster(p, signal, st);
     if (p->io == CWT_DTYPE_F64)
         return forward_dispatch<double>(log2n, signal, p->C, p->n, p->spec, p->tw, st);
     return forward_dispatch<float>(log2n, signal, p->C, p->n, p->spec, p->tw, st);
@@ -124,6 +125,7 @@ cudaError_t launch_forward(const cwt_plan_s *p, const void *signal, cudaStream_t
 
 cudaError_t launch_fft(const float2 *in, float2 *out, int log2n, int batch, int sign,
                        const float2 *tw, cudaStream_t st) {
+    if (log2n > kMaxFftLog2) return launch_fft_cluster(in, out, log2n, batch, sign, tw, st);
     if (sign < 0) return fft_dispatch<-1>(log2n, in, out, batch, tw, st);
     return fft_dispatch<+1>(log2n, in, out, batch, tw, st);
 }

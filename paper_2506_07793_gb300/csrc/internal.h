@@ -12,8 +12,10 @@
 namespace cwtk {
 
 constexpr int kMinFft = 32;        // smallest padded length (keeps radix passes >= 2)
-constexpr int kMaxFftLog2 = 14;    // largest single-pass length 16384 (shared-memory row)
+constexpr int kMaxFftLog2 = 14;    // largest one-CTA length 16384 (shared-memory row)
 constexpr int kMaxFft = 1 << kMaxFftLog2;
+constexpr int kMaxClusterFftLog2 = 17;  // up to 131072 on a cluster of 8 CTAs
+constexpr int kMaxClusterFft = 1 << kMaxClusterFftLog2;
 constexpr double kBandRelThreshold = 1e-10;  // bins below this fraction of a scale's peak are skipped
 
 // Per-device FP32 twiddle table exp(2 pi i m / 2^17), built in FP64 on first use.
@@ -88,6 +90,12 @@ cudaError_t launch_scale_block(const cwt_plan_s *p, void *out_c, void *out_p, vo
                                cudaStream_t st);
 cudaError_t launch_fft(const float2 *in, float2 *out, int log2n, int batch, int sign,
                        const float2 *tw, cudaStream_t st);
+// Rows of 2^15..2^17 points on thread-block clusters (cluster.cu).
+cudaError_t launch_forward_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+cudaError_t launch_scale_block_cluster(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
+                                       cudaStream_t st);
+cudaError_t launch_fft_cluster(const float2 *in, float2 *out, int log2n, int batch, int sign,
+                               const float2 *tw, cudaStream_t st);
 // prepare_only: build the work items, generate missing banks and autotune a
 // new batch shape (its candidate runs write valid outputs); otherwise launch
 // the chosen schedule's graph once.

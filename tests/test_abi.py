@@ -51,7 +51,7 @@ def test_options_defaults(lib):
 
 
 @pytest.mark.parametrize("n,N", [(1, 32), (31, 32), (32, 32), (33, 64), (500, 512), (10000, 16384),
-                                 (16384, 16384)])
+                                 (16384, 16384), (16385, 32768), (122880, 131072), (131072, 131072)])
 def test_pow2_padding(lib, n, N):
     assert lib.cwt_fft_length(n) == N
 
@@ -61,7 +61,7 @@ def test_padding_limits(lib):
         lib.cwt_fft_length(0)
     assert e.value.status == lib.CWT_EINVAL
     with pytest.raises(lib.CWTError) as e:
-        lib.cwt_fft_length(16385)
+        lib.cwt_fft_length(131073)
     assert e.value.status == lib.CWT_EUNSUPPORTED
     with pytest.raises(lib.CWTError) as e:
         lib.cwt_fft_length(100, lib.CWT_PAD_SMOOTH)
@@ -104,7 +104,7 @@ def test_unsupported_requests(lib, what):
     elif what == "tc_bf16":
         o.precision = lib.CWT_PREC_TC_BF16
     else:
-        samples = 20000
+        samples = 140000
     with pytest.raises(lib.CWTError) as e:
         lib.cwt_plan_create(1, samples, 500.0, [10.0], [7.0], wavelet, lib.CWT_OUT_POWER, o)
     assert e.value.status == lib.CWT_EUNSUPPORTED

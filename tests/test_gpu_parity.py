@@ -61,7 +61,7 @@ def check(res, ref, tol=FP32_TOL):
 def test_fft_matches_library_fft_and_parseval(lib):
     import torch
     rng = np.random.default_rng(1)
-    for log2n in range(5, 15):
+    for log2n in range(5, 18):  # 2^15..2^17 run on thread-block clusters
         n = 1 << log2n
         z = (rng.standard_normal((3, n)) + 1j * rng.standard_normal((3, n))).astype(np.complex64)
         d_in = torch.from_numpy(z).cuda()
@@ -246,3 +246,39 @@ def _opts(lib, **kw):
     if "io" in kw:
         o.io_dtype = kw["io"]
     return o
+
+
+def test_cluster_lengths_every_row(lib):
+    """N = 32768 and 65536 (rows on clusters of 2 and 4 CTAs), every row."""
+    for C, n, fs, freqs, cycles in [(2, 20000, 1000.0, [0.8, 13.0, 240.0], [3.0, 7.0, 12.0]),
+                                    (1, 40000, 2000.0, [3.0, 600.0], [7.0, 5.0])]:
+        x = eeg(600 + n, C, n, fs, np.float32)
+        res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"))
+        assert N > 16384
+        check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
+
+
+def test_precision_workload_full_size_sampled_rows(lib):
+    """256 ch x 122880 @2048 Hz (N = 131072: clusters of 8 CTAs), 128 log
+    freqs 0.5-200 Hz, power + phase, FP32; error per frequency on sampled rows."""
+    import os
+    import torch
+    w = workload("precision")
+    C, S = w.channels, w.scales
+    t = lib.CWT(C, w.samples, w.fs, w.freqs, w.n_cycles, outputs=("power", "phase"))
+    try:
+        assert t.info.fft_length == 131072
+        x = w.signal()
+        out = t(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        rows = [(0, 0), (255, 127), (17, 64), (200, 100), (99, 115), (3, 33), (128, 120), (64, 8)]
+        ref = oracle.cwt_rows(x.astype(np.float64), 131072, w.fs, w.freqs, w.n_cycles, rows,
+                              threads=os.cpu_count())
+        pw = np.stack([out["power"][c, s].cpu().numpy() for c, s in rows])
+        ph = np.stack([out["phase"][c, s].cpu().numpy() for c, s in rows])
+        e_p, e_ph = power_err(pw, ref), phase_err(ph, ref)
+        for (c, s), a, b in zip(rows, e_p, e_ph):
+            print(f"F={w.freqs[s]:8.3f} Hz  power err {a:.2e}  phase err {b:.2e}")
+        assert e_p.max() <= FP32_TOL and e_ph.max() <= FP32_TOL
+    finally:
+        t.close()
