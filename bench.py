@@ -114,21 +114,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, x_rows, n_channels):
-    """The FP64 oracle, as it stands, on the host cores: all scales of the first
-    n_channels channels of the same workload."""
+def cpu_baseline(w, x_rows, n_channels, n_scales=None):
+    """The FP64 oracle, as it stands, on the host cores: the first n_scales
+    (default all) scales of the first n_channels channels of the same workload."""
     import oracle
     from paper_2506_07793_gb300 import cwt_fft_length
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     N = cwt_fft_length(w.samples)
-    rows = [(c, s) for c in range(n_channels) for s in range(w.scales)]
+    ns = w.scales if n_scales is None else n_scales
+    rows = [(c, s) for c in range(n_channels) for s in range(0, w.scales, max(1, w.scales // ns))][:n_channels * ns]
     t0 = time.perf_counter()
     oracle.cwt_rows(x_rows[:n_channels].astype(np.float64), N, w.fs, w.freqs, w.n_cycles, rows,
                     threads=cores)
     dt = time.perf_counter() - t0
     coeffs = len(rows) * w.n_out
     return {"value": coeffs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_channels} of {w.channels} channels x all {w.scales} scales x "
+            "sample": f"{n_channels} of {w.channels} channels x {ns} of {w.scales} scales x "
                       f"{w.n_out} samples ({coeffs} coefficients), {dt:.2f} s wall"}
 
 
@@ -166,6 +167,41 @@ def run_reference(args):
     }), flush=True)
 
 
+def plain_fp32_pipeline(cw, plan, x, fused_power, w, args, flush, stream):
+    """The paper's own GPU design (Section "Optimizing performance": wavelets
+    generated in GPU memory, library FFT, elementwise product, library inverse
+    FFT), run with torch.fft (cuFFT) as a comparator only: FFT of the
+    zero-padded signal, broadcast product with the same FP32 bank, inverse FFT,
+    crop, |c|^2.  Same outputs (complex64 + power) as the fused kernel; its step
+    time and its largest per-row power difference from the fused result are
+    reported."""
+    import torch
+    info = cw.cwt_plan_info(plan)
+    N = info.fft_length
+    bank, _, _ = cw.cwt_plan_bank(plan)
+    Wt = torch.from_numpy(bank * N).cuda()  # the bank carries 1/N; ifft applies it again
+    xp = torch.zeros((w.channels, N), dtype=torch.float32, device="cuda")
+    out = {}
+
+    def step():
+        xp[:, :w.samples] = x
+        X = torch.fft.fft(xp)                           # [C][N] complex64
+        c = torch.fft.ifft(X[:, None, :] * Wt[None])    # [C][S][N]
+        c = c[..., :w.samples]
+        out["c"], out["p"] = c, c.real * c.real + c.imag * c.imag
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = timed_steps(step, args.steps, flush, stream) / args.steps
+    p = out["p"]
+    row_err = ((p - fused_power).abs().amax(dim=-1) / fused_power.amax(dim=-1)).max().item()
+    del out, xp, Wt
+    torch.cuda.empty_cache()
+    return {"value": w.coefficients / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "impl": "torch.fft (cuFFT): fft -> broadcast product -> ifft -> crop -> |c|^2",
+            "max_row_power_diff_vs_fused": row_err, "speedup_of_fused": None}
+
+
 def timed_steps(step, steps, flush, stream):
     """Run `steps` steps, each between CUDA events on `stream`, overwriting
     `flush` (> L2) between them outside the events; returns total ms."""
@@ -198,6 +234,9 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload("batch")
+    if args.epochs:
+        w.extra["epoch_lengths"] = w.extra["epoch_lengths"][:args.epochs]
+        w.extra["epoch_starts"] = w.extra["epoch_starts"][:args.epochs]
     lengths = w.extra["epoch_lengths"]
     C, S, d = w.channels, w.scales, w.decimation
     opt = cw.cwt_options_init()
@@ -418,8 +457,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-channels", type=int, default=2)
-    ap.add_argument("--workload", default=WORKLOAD, choices=["fused", "batch", "serving"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["fused", "batch", "serving", "precision"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--channels", type=int, default=0,
+                    help="override the workload's channel count (small profiling captures)")
+    ap.add_argument("--epochs", type=int, default=0,
+                    help="batch workload: use only the first N epochs (small profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -429,6 +473,13 @@ def main():
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    return run_plan_workload(args, args.workload)
+
+
+def run_plan_workload(args, name):
+    """One cwt_execute per step over a resident [C][n] signal: the fused
+    workload (complex64 + power, N = 16384) or the precision workload (power +
+    phase, N = 131072, each row on a cluster of 8 CTAs)."""
 
     import torch
     import paper_2506_07793_gb300 as cw
@@ -443,22 +494,28 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = workload(WORKLOAD)
+    w = workload(name)
+    if args.channels:
+        w.channels = args.channels
     # each rank transforms its own independent recording (weak scaling)
     x_host = w.signal(first_channel=rank * w.channels)
     x = torch.from_numpy(x_host).cuda()
-    kinds = cw.CWT_OUT_COMPLEX | cw.CWT_OUT_POWER
+    bits = {"complex": cw.CWT_OUT_COMPLEX, "power": cw.CWT_OUT_POWER, "phase": cw.CWT_OUT_PHASE}
+    kinds = 0
+    for o in w.outputs:
+        kinds |= bits[o]
     plan = cw.cwt_plan_create(w.channels, w.samples, w.fs, w.freqs, w.n_cycles,
                               cw.CWT_WAVELET_MORLET, kinds, cw.cwt_options_init())
     info = cw.cwt_plan_info(plan)
     shape = (w.channels, w.scales, w.n_out)
-    out_c = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    out_c = torch.empty(shape, dtype=torch.complex64, device="cuda") if "complex" in w.outputs else None
     out_p = torch.empty(shape, dtype=torch.float32, device="cuda")
+    out_ph = torch.empty(shape, dtype=torch.float32, device="cuda") if "phase" in w.outputs else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        cw.cwt_execute(plan, x, out_c, out_p, None, stream)
+        cw.cwt_execute(plan, x, out_c, out_p, out_ph, stream)
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -475,7 +532,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i))
         starts[i].record(stream)
-        cw.cwt_execute(plan, x, out_c, out_p, None, stream)
+        cw.cwt_execute(plan, x, out_c, out_p, out_ph, stream)
         ends[i].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -498,38 +555,47 @@ def main():
     # roofline of the dominant kernel (fused scale block)
     peaks, peak_kind = measured_peaks()
     N = info.fft_length
-    alg_bytes = (w.channels * w.scales * w.n_out * (8 + 4)      # complex64 + float32 power out
+    out_bytes_per_coef = 4 * (2 * ("complex" in w.outputs) + ("power" in w.outputs)
+                              + ("phase" in w.outputs))
+    alg_bytes = (w.channels * w.scales * w.n_out * out_bytes_per_coef  # requested outputs
                  + w.channels * N * 8                              # forward spectra, read once
                  + w.scales * N * 4)                               # wavelet bank, read once
     sb_s = ms_sb / max(n_sb, 1) * 1e-3
     achieved = alg_bytes / sb_s / 1e9
     traffic = profiled_traffic()
-    roofline = {"kernel": "scale_block_kernel<16384,float>", "bound": "hbm",
+    kname = (f"scale_block_kernel<{N},float>" if N <= 16384
+             else f"cl_scale_block_kernel<{N},float> (cluster of {N // 16384} CTAs)")
+    roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
-                "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                "traffic": traffic if name == "fused" else None, "alg_bytes_per_launch": alg_bytes,
                 "kernel_ms": sb_s * 1e3, "forward_fft_ms": ms_fw / max(n_fw, 1)}
 
     # end to end through the host-buffer entry point (pinned memory)
     h_in = torch.from_numpy(x_host).pin_memory()
-    h_c = torch.empty(shape, dtype=torch.complex64).pin_memory()
+    h_c = torch.empty(shape, dtype=torch.complex64).pin_memory() if out_c is not None else None
     h_p = torch.empty(shape, dtype=torch.float32).pin_memory()
-    cw.cwt_execute_host(plan, h_in, h_c, h_p, None, stream)  # allocates staging
+    h_ph = torch.empty(shape, dtype=torch.float32).pin_memory() if out_ph is not None else None
+    cw.cwt_execute_host(plan, h_in, h_c, h_p, h_ph, stream)  # allocates staging
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    e2e_steps = args.e2e_steps if name == "fused" else 1
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        cw.cwt_execute_host(plan, h_in, h_c, h_p, None, stream)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    for _ in range(e2e_steps):
+        cw.cwt_execute_host(plan, h_in, h_c, h_p, h_ph, stream)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e = {"value": coeffs_rank * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(x_host.nbytes),
-           "d2h_bytes_per_step": int(h_c.numel() * 8 + h_p.numel() * 4),
+           "d2h_bytes_per_step": int(w.coefficients * out_bytes_per_coef),
            "ms_per_step": e2e_s * 1e3}
+    del h_c, h_p, h_ph
+    plain = (plain_fp32_pipeline(cw, plan, x, out_p, w, args, flush, stream) if name == "fused"
+             else None)
     cw.cwt_plan_destroy(plan)
 
     if rank == 0:
@@ -545,11 +611,17 @@ def main():
                        "parallelism": f"weak x{world}, no collective"},
             "roofline": roofline,
             "e2e": e2e,
+            "plain_fp32_gpu": plain,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels)
+            line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels if name == "fused" else 1,
+                                                None if name == "fused" else 8)
+        if plain is not None:
+            plain["speedup_of_fused"] = plain["ms_per_step"] / ms_step
+        else:
+            del line["plain_fp32_gpu"]
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
