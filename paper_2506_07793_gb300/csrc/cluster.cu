@@ -1,8 +1,9 @@
 // cluster.cu -- forward FFT, fused scale block and generic FFT for rows of
-// 32768 to 131072 points, each row on a thread-block cluster of 2-8 CTAs
-// (see fft_cluster.cuh).  The arithmetic per row is that of fft_kernels.cu
-// and scale_block.cu (Eq. 2: forward FFT per channel; band product, inverse
-// FFT and reduction per (channel, scale) row).
+// 32768 to 131072 points, each row on a thread-block cluster of 2-8 CTAs (see
+// fft_cluster.cuh: per-CTA residue-class FFTs plus one cross-CTA stage).  The
+// arithmetic per row is that of fft_kernels.cu and scale_block.cu (Eq. 2:
+// forward FFT per channel; band product, inverse FFT and reduction per
+// (channel, scale) row).
 #include <cuda_runtime.h>
 
 #include "fft_cluster.cuh"
@@ -28,14 +29,11 @@ cl_forward_kernel(const IO *__restrict__ x, int n, float2 *__restrict__ spec,
     extern __shared__ float2 clsm[];
     constexpr int CL = ClusterShape<N>::CL;
     const int row = blockIdx.x / CL;
-    const int J = threadIdx.x * CL + (int)cg::this_cluster().block_rank();
     const IO *xr = x + (size_t)row * n;
     float2 *out = spec + (size_t)row * N;
     auto load = [&](int i) -> float2 { return make_float2(i < n ? (float)xr[i] : 0.f, 0.f); };
     auto store = [&](int t, float2 v) { out[t] = v; };
-    float2 v[kClR];
-    fft_pass0_dense<N, kClR, -1>(v, J, load);
-    fft_cluster_finish<N, -1>(v, clsm, tw, store);
+    fft_cluster_row<N, -1>(clsm, tw, load, store);
 }
 
 template <int N, int SIGN>
@@ -44,16 +42,13 @@ cl_fft_kernel(const float2 *in, float2 *out, const float2 *__restrict__ tw) {
     extern __shared__ float2 clsm[];
     constexpr int CL = ClusterShape<N>::CL;
     const int row = blockIdx.x / CL;
-    const int J = threadIdx.x * CL + (int)cg::this_cluster().block_rank();
     const float2 *ir = in + (size_t)row * N;
     float2 *orow = out + (size_t)row * N;
     auto load = [&](int i) -> float2 { return ir[i]; };
     auto store = [&](int t, float2 v) { orow[t] = v; };
-    float2 v[kClR];
-    fft_pass0_dense<N, kClR, SIGN>(v, J, load);
-    // every input is read before the first cluster barrier inside
-    // fft_cluster_finish, so `out` may alias `in`
-    fft_cluster_finish<N, SIGN>(v, clsm, tw, store);
+    // every input is read before the cluster barrier inside fft_cluster_row,
+    // so `out` may alias `in`
+    fft_cluster_row<N, SIGN>(clsm, tw, load, store);
 }
 
 struct ClArgs {
@@ -72,7 +67,6 @@ cl_scale_block_kernel(const ClArgs a) {
     extern __shared__ float2 clsm[];
     constexpr int CL = ClusterShape<N>::CL;
     const int row = blockIdx.x / CL;
-    const int J = threadIdx.x * CL + (int)cg::this_cluster().block_rank();
     const int c = row / a.S, s = row - c * a.S;
     const float2 *X = a.spec + (size_t)c * N;
     const float *W = a.bank + (size_t)s * N;
@@ -106,24 +100,27 @@ cl_scale_block_kernel(const ClArgs a) {
         if (op) op[obase + o] = (IO)fmaf(v.x, v.x, v.y * v.y);
         if (oph) cl_store_phase(oph + obase + o, v);
     };
-    constexpr int Q = N / FftShape<N, kClR>::R0;
-    float2 v[kClR];
-    if (B <= Q) {  // at most one in-band input per pass-0 butterfly (see scale_block.cu)
-        auto first = [&](int jj, int &r, float2 &x) -> bool {
-            const int d0 = (jj - b0) & (Q - 1);
-            if (d0 >= B) return false;
-            const int k = (b0 + d0) & (N - 1);
-            r = (k - jj) / Q;
-            const float2 xv = X[k];
-            const float w = W[k];
-            x = make_float2(xv.x * w, xv.y * w);
-            return true;
-        };
-        fft_pass0_sparse<N, kClR, +1>(v, J, a.tw, first);
-    } else {
-        fft_pass0_dense<N, kClR, +1>(v, J, load);
-    }
-    fft_cluster_finish<N, +1>(v, clsm, a.tw, store);
+    // Narrow band: this CTA's residue class k = rank + CL m holds Bm
+    // consecutive (cyclic) in-band m, starting at m_first; if Bm <= NL/R0 each
+    // local pass-0 butterfly {jj + r NL/R0} meets at most one of them.
+    constexpr int NL = ClusterShape<N>::NL;
+    constexpr int Q = NL / FftShape<NL, kClR>::R0;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int delta = (rank - b0) & (CL - 1);
+    const int Bm = delta < B ? (B - delta + CL - 1) / CL : 0;
+    const int m_first = ((((b0 + delta) & (N - 1)) - rank) / CL) & (NL - 1);
+    auto first = [&](int jj, int &r, float2 &x) -> bool {
+        const int d0 = (jj - m_first) & (Q - 1);
+        if (d0 >= Bm) return false;
+        const int m = (m_first + d0) & (NL - 1);
+        r = (m - jj) / Q;
+        const int k = rank + CL * m;
+        const float2 xv = X[k];
+        const float w = W[k];
+        x = make_float2(xv.x * w, xv.y * w);
+        return true;
+    };
+    fft_cluster_row<N, +1>(clsm, a.tw, load, Bm <= Q, first, store);
 }
 
 template <typename K>

@@ -1,17 +1,20 @@
-// fft_cluster.cuh -- Stockham FFT of one long row across a thread-block
-// cluster, exchanging through distributed shared memory.
+// fft_cluster.cuh -- FFT of one long row on a thread-block cluster.
 //
 // Rows longer than one CTA's shared memory (N = CL * 16384, CL = 2, 4, 8;
 // e.g. the 131072-point padding of a 60 s recording at 2048 Hz, Section "Fast
-// Fourier transform") run on a cluster of CL CTAs of 512 threads, 32 points per
-// thread.  The cluster thread index is J = tid * CL + rank and CTA `rank` owns
-// the elements idx = rank (mod CL) at slot idx / CL.  With this interleaving
-//  * every pass reads only its own CTA's shared memory (J + r*T = J mod CL);
-//  * a pass with Ns >= CL also writes only locally; only pass 0 and passes
-//    with Ns < CL write into other CTAs (st through the cluster window);
-//  * the last pass writes its outputs to the CTA that owns the contiguous
-//    range t / (N / CL), so the epilogue's global stores are coalesced.
-// Cluster barriers order the remote writes; local passes use __syncthreads.
+// Fourier transform") run on a cluster of CL CTAs of 512 threads.  With
+// k = c + CL * m (residue class c) and t = t1 + NL * t2 (NL = N / CL):
+//     X[t1 + NL t2] = sum_c w_CL^(c t2) * [ w_N^(c t1) * A_c[t1] ],
+//     A_c[t1]       = sum_m x[c + CL m] w_NL^(m t1),
+// (w_M = exp(SIGN 2 pi i / M)).  So
+//  1. CTA c runs the fast one-CTA 16384-point FFT of its residue class
+//     (fft_core.cuh) and keeps A_c in its own shared memory;
+//  2. after one cluster barrier, CTA c takes t1 in [c NL/CL, (c+1) NL/CL):
+//     each thread reads A_0..A_{CL-1}[t1] from the CTAs' shared memory
+//     (ld.shared::cluster), twiddles, runs a CL-point DFT and emits the CL
+//     outputs t1 + NL t2 -- consecutive threads write consecutive t1, so the
+//     epilogue's global stores are coalesced.
+// One bulk exchange per row; every other access stays in the CTA.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -29,80 +32,74 @@ constexpr int kClPoints = kClThreads * kClR;  // 16384 points per CTA
 template <int N>
 struct ClusterShape {
     static constexpr int CL = N / kClPoints;
-    static constexpr int LCL = ilog2c(CL);
-    static constexpr int NL = N / CL;  // elements per CTA
-    static constexpr int SMEM_F2 = NL + (NL >> 4);
+    static constexpr int NL = kClPoints;
+    static constexpr int SMEM_F2 = FftShape<NL, kClR>::SMEM_F2;
     static constexpr int SMEM_BYTES = SMEM_F2 * 8;
     static_assert(CL >= 2 && CL <= 8 && CL * kClPoints == N, "N = 2, 4 or 8 x 16384");
 };
 
-// Passes 0-store .. last of a cluster row; v holds this thread's pass-0
-// outputs (from fft_pass0_dense / fft_pass0_sparse with j = J).  `store(t, X[t])`
-// is called for the CTA's contiguous output range t in [rank*NL, (rank+1)*NL).
-template <int N, int SIGN, typename Store>
-__device__ __forceinline__ void fft_cluster_finish(float2 (&v)[kClR], float2 *__restrict__ sm,
-                                                   const float2 *__restrict__ tw, Store &store) {
-    using S = FftShape<N, kClR>;
+// Load a float2 from the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ float2 ld_cluster(const float2 *local, unsigned rank) {
+    const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
+    unsigned raddr;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(raddr) : "memory");
+    return v;
+}
+
+// Whole-row FFT on the cluster: `load(k)` gives x[k] (k in [0, N)); `store(t,
+// X[t])` receives outputs t = t1 + NL t2 for this CTA's t1 range.  When
+// `sparse` is true, `first(jj, r, x)` serves the local pass 0 instead (see
+// fft_pass0_sparse; jj and r index this CTA's residue class m = jj + r NL/R0).
+// All threads of all CTAs of the cluster call it together.
+template <int N, int SIGN, typename Load, typename First, typename Store>
+__device__ __forceinline__ void fft_cluster_row(float2 *__restrict__ sm, const float2 *__restrict__ tw,
+                                                Load &load, bool sparse, First &first, Store &store) {
     using C = ClusterShape<N>;
-    constexpr int R = kClR, T = S::T, R0 = S::R0, G0 = S::G0, TL = kClThreads;
+    constexpr int CL = C::CL, NL = C::NL, TL = kClThreads;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x;
-    const int J = tid * C::CL + rank;
-    // pass-0 outputs to their owners (every CTA must be done with its buffer)
+    // 1. local FFT of the residue class `rank`
+    auto lload = [&](int m) -> float2 { return load(rank + CL * m); };
+    auto nostore = [&](int, float2) {};
+    float2 v[kClR];
+    if (sparse)
+        fft_pass0_sparse<NL, kClR, SIGN>(v, tid, tw, first);
+    else
+        fft_pass0_dense<NL, kClR, SIGN>(v, tid, lload);
+    fft_finish<NL, kClR, SIGN, decltype(nostore), true>(v, sm, tw, tid, nostore);
+    __syncthreads();  // every thread has read its last-pass inputs
+#pragma unroll
+    for (int r = 0; r < kClR; ++r) sm[spad2(tid + r * TL)] = v[r];  // A_rank[t1], natural order
     cl.sync();
-#pragma unroll
-    for (int g = 0; g < G0; ++g)
-#pragma unroll
-        for (int r = 0; r < R0; ++r) {
-            const int idx = (J + g * T) * R0 + r;
-            float2 *dst = cl.map_shared_rank(sm, idx & (C::CL - 1));
-            dst[spad2(idx >> C::LCL)] = v[g * R0 + r];
-        }
-    cl.sync();
-    int Ns = R0;
+    // 2. cross-CTA radix-CL stage over this CTA's t1 range
 #pragma unroll 1
-    for (int p = 1; p < S::NP; ++p) {
+    for (int q = 0; q < NL / CL / TL; ++q) {
+        const int t1 = rank * (NL / CL) + q * TL + tid;
+        float2 a[CL];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm[spad2(tid + r * TL)];
-        const int k = J & (Ns - 1);
-        float2 w1 = __ldg(&tw[k * (kTwN / (Ns * R))]);
-        if (SIGN < 0) w1.y = -w1.y;
-        twiddle_chain<R>(v, w1);
-        dft<R, SIGN>(v);
-        if (p == S::NP - 1) {
-            cl.sync();  // every CTA has read its inputs
+        for (int c = 0; c < CL; ++c) a[c] = ld_cluster(&sm[spad2(t1)], (unsigned)c);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int t = J + r * Ns;
-                float2 *dst = cl.map_shared_rank(sm, t / C::NL);
-                dst[spad2(t & (C::NL - 1))] = v[r];
-            }
-            cl.sync();
-#pragma unroll 1
-            for (int m = 0; m < R; ++m) {
-                const int slot = tid + m * TL;
-                store(rank * C::NL + slot, sm[spad2(slot)]);
-            }
-        } else if (Ns >= C::CL) {  // all writes stay in this CTA
-            __syncthreads();
-            const int base = (J - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) sm[spad2((base + r * Ns) >> C::LCL)] = v[r];
-            __syncthreads();
-        } else {
-            cl.sync();
-            const int base = (J - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int idx = base + r * Ns;
-                float2 *dst = cl.map_shared_rank(sm, idx & (C::CL - 1));
-                dst[spad2(idx >> C::LCL)] = v[r];
-            }
-            cl.sync();
+        for (int c = 1; c < CL; ++c) {
+            float2 w = __ldg(&tw[(c * t1) * (kTwN / N)]);  // c * t1 < N
+            if (SIGN < 0) w.y = -w.y;
+            a[c] = cmul(a[c], w);
         }
-        Ns *= R;
+        dft<CL, SIGN>(a);
+#pragma unroll
+        for (int t2 = 0; t2 < CL; ++t2) store(t1 + NL * t2, a[t2]);
     }
+    cl.sync();  // no CTA still reads this CTA's buffer
+}
+
+// Dense-input convenience form.
+template <int N, int SIGN, typename Load, typename Store>
+__device__ __forceinline__ void fft_cluster_row(float2 *__restrict__ sm, const float2 *__restrict__ tw,
+                                                Load &load, Store &store) {
+    auto none = [](int, int &, float2 &) -> bool { return false; };
+    fft_cluster_row<N, SIGN>(sm, tw, load, false, none, store);
 }
 
 }  // namespace cwtk

@@ -207,7 +207,9 @@ __device__ __forceinline__ void fft_pass0_sparse(float2 (&v)[R], int j, const fl
     }
 }
 
-template <int N, int R, int SIGN, typename Store>
+// With KEEP = true the last pass leaves its outputs in v (output r of thread
+// j is X[j + r * N / R]) instead of calling `store`.
+template <int N, int R, int SIGN, typename Store, bool KEEP = false>
 __device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ sm,
                                            const float2 *__restrict__ tw, int j, Store &store) {
     using S = FftShape<N, R>;
@@ -239,8 +241,10 @@ __device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ 
         twiddle_chain<R>(v, w1);
         dft<R, SIGN>(v);
         if (p == S::NP - 1) {
+            if constexpr (!KEEP) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) store(j + r * Ns, v[r]);
+                for (int r = 0; r < R; ++r) store(j + r * Ns, v[r]);
+            }
         } else {
             __syncthreads();
             const int base = (j - k) * R + k;
