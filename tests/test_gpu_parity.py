@@ -282,3 +282,25 @@ def test_precision_workload_full_size_sampled_rows(lib):
         assert e_p.max() <= FP32_TOL and e_ph.max() <= FP32_TOL
     finally:
         t.close()
+
+
+def test_channel_shards_equal_the_whole(lib):
+    """Rows are independent: transforming channel blocks separately (as ranks
+    of a multi-GPU run do) gives bitwise the whole-recording result."""
+    import torch
+    from paper_2506_07793_gb300.partition import shard_channels
+    C, n, fs = 10, 3000, 500.0
+    freqs, cycles = np.geomspace(2, 120, 11), np.full(11, 7.0)
+    x = torch.from_numpy(eeg(77, C, n, fs, np.float32)).cuda()
+    whole = lib.CWT(C, n, fs, freqs, cycles, outputs=("complex", "power"))
+    ref = whole(x)
+    for world in (2, 3):
+        for r in range(world):
+            c0, c1 = shard_channels(C, world, r)
+            part = lib.CWT(c1 - c0, n, fs, freqs, cycles, outputs=("complex", "power"))
+            out = part(x[c0:c1].contiguous())
+            torch.cuda.synchronize()
+            assert torch.equal(out["complex"], ref["complex"][c0:c1])
+            assert torch.equal(out["power"], ref["power"][c0:c1])
+            part.close()
+    whole.close()
