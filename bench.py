@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["fused", "batch", "serving", "precision"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--pad", default="pow2", choices=["pow2", "smooth"],
+                    help="padding policy: next power of two, or the paper's 2,3,5,7-smooth length")
     ap.add_argument("--channels", type=int, default=0,
                     help="override the workload's channel count (small profiling captures)")
     ap.add_argument("--epochs", type=int, default=0,
@@ -504,8 +506,10 @@ def run_plan_workload(args, name):
     kinds = 0
     for o in w.outputs:
         kinds |= bits[o]
+    popt = cw.cwt_options_init()
+    popt.pad_policy = cw.CWT_PAD_SMOOTH if args.pad == "smooth" else cw.CWT_PAD_POW2
     plan = cw.cwt_plan_create(w.channels, w.samples, w.fs, w.freqs, w.n_cycles,
-                              cw.CWT_WAVELET_MORLET, kinds, cw.cwt_options_init())
+                              cw.CWT_WAVELET_MORLET, kinds, popt)
     info = cw.cwt_plan_info(plan)
     shape = (w.channels, w.scales, w.n_out)
     out_c = torch.empty(shape, dtype=torch.complex64, device="cuda") if "complex" in w.outputs else None
@@ -563,12 +567,17 @@ def run_plan_workload(args, name):
     sb_s = ms_sb / max(n_sb, 1) * 1e-3
     achieved = alg_bytes / sb_s / 1e9
     traffic = profiled_traffic()
-    kname = (f"scale_block_kernel<{N},float>" if N <= 16384
-             else f"cl_scale_block_kernel<{N},float> (cluster of {N // 16384} CTAs)")
+    if N & (N - 1):
+        kname = f"mr_scale_block_kernel (mixed radix, N = {N})"
+    elif N <= 16384:
+        kname = f"scale_block_kernel<{N},float>"
+    else:
+        kname = f"cl_scale_block_kernel<{N},float> (cluster of {N // 16384} CTAs)"
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
-                "traffic": traffic if name == "fused" else None, "alg_bytes_per_launch": alg_bytes,
+                "traffic": traffic if (name == "fused" and args.pad == "pow2") else None,
+                "alg_bytes_per_launch": alg_bytes,
                 "kernel_ms": sb_s * 1e3, "forward_fft_ms": ms_fw / max(n_fw, 1)}
 
     # end to end through the host-buffer entry point (pinned memory)
@@ -605,7 +614,8 @@ def run_plan_workload(args, name):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.notes, "channels": w.channels, "samples": w.samples,
-                       "scales": w.scales, "fft_length": N, "coefficients_per_step": coeffs_rank,
+                       "scales": w.scales, "fft_length": N, "padding": args.pad,
+                       "coefficients_per_step": coeffs_rank,
                        "l2": "256 MB buffer overwritten between timed steps (outside the events)",
                        "bank_ms": info.bank_ms, "wall_s_timed_region": wall,
                        "parallelism": f"weak x{world}, no collective"},

@@ -74,8 +74,14 @@ typedef enum { CWT_PREC_FP32 = 0, CWT_PREC_TC_FP16 = 1, CWT_PREC_TC_BF16 = 2 } c
 typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
 
 /* Padding policy (Section "Fast Fourier transform").  POW2 pads to the next
- * power of two (the choice the paper attributes to MNE-python).  SMOOTH, the
- * paper's own policy (smallest 2,3,5,7-smooth length), is not implemented. */
+ * power of two (the choice the paper attributes to MNE-python), up to 131072.
+ * SMOOTH is the paper's own policy: the smallest length >= max(samples, 32)
+ * whose prime factors are 2, 3, 5 and 7.  Smooth lengths that are not powers
+ * of two run on the mixed-radix kernels and are limited to 16384 points;
+ * the 13 smooth lengths 14406 ... 16200 whose radix-3/5/7 passes do not fit
+ * one CTA are passed over (SMOOTH then gives the next smooth length, and an
+ * explicit fft_length of one of them is CWT_EUNSUPPORTED).
+ * cwt_execute_batch does not take mixed-radix plans (CWT_EUNSUPPORTED). */
 typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
 
 /* Kernel identifiers for the profiling counters. */
@@ -117,7 +123,8 @@ typedef struct {
     int decimation; /* keep every d-th output sample, d >= 1 (default 1) */
     int pad_policy; /* cwt_pad_policy (default CWT_PAD_POW2) */
     int fft_length; /* 0: from pad_policy; else an explicit N >= samples that is a
-                       power of two the build supports (see cwt_fft_length) */
+                       power of two the build supports or a 2,3,5,7-smooth
+                       length <= 16384 (see cwt_pad_policy) */
     int io_dtype;   /* cwt_dtype of the signal and of every output (default F32);
                        F64 is converted to FP32 on load and back on store */
     int reserved[11];
@@ -144,10 +151,12 @@ const char *cwt_status_str(cwt_status s);
 cwt_status cwt_options_init(cwt_options *opt);
 
 /* Padded FFT length N for `samples` under `pad_policy` (Section "Fast Fourier
- * transform"): the next power of two >= max(samples, 32).  Writes *n_fft.
- * CWT_EINVAL if samples < 1; CWT_EUNSUPPORTED if the policy is not built or
- * N exceeds the largest supported length (2^17; lengths above 2^14 run each
- * row on a thread-block cluster).  Host-only; no CUDA call. */
+ * transform"): POW2, the next power of two >= max(samples, 32); SMOOTH, the
+ * smallest 2,3,5,7-smooth length >= max(samples, 32) that the mixed-radix
+ * kernels run (see cwt_pad_policy).  Writes *n_fft.  CWT_EINVAL if samples < 1
+ * or the policy is unknown; CWT_EUNSUPPORTED if N exceeds the largest
+ * supported length (POW2: 2^17, lengths above 2^14 running each row on a
+ * thread-block cluster; SMOOTH: 2^14).  Host-only; no CUDA call. */
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 
 /*

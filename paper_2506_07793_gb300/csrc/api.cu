@@ -93,6 +93,7 @@ void free_plan_memory(cwt_plan_s *p) {
     cudaFree(p->bank);
     cudaFree(p->band);
     cudaFree(p->spec);
+    cudaFree(p->twN);
     cudaFree(p->stage_in);
     cudaFree(p->stage_c);
     cudaFree(p->stage_p);
@@ -141,7 +142,23 @@ cwt_status cwt_options_init(cwt_options *opt) {
 
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft) {
     if (!n_fft || samples < 1) return CWT_EINVAL;
-    if (pad_policy != CWT_PAD_POW2) return pad_policy == CWT_PAD_SMOOTH ? CWT_EUNSUPPORTED : CWT_EINVAL;
+    if (pad_policy == CWT_PAD_SMOOTH) {
+        // smallest 2,3,5,7-smooth length >= max(samples, 32) that the kernels
+        // run: 13 smooth lengths in (14336, 16384) whose radix-3/5/7 passes do
+        // not fit one CTA's registers are passed over
+        for (int m = samples < cwtk::kMinFft ? cwtk::kMinFft : samples; m <= cwtk::kMaxFft; ++m) {
+            int x = m;
+            for (int f : {2, 3, 5, 7})
+                while (x % f == 0) x /= f;
+            if (x != 1) continue;
+            cwtk::MrSchedule sch;
+            if (!is_pow2(m) && !cwtk::mr_schedule(m, &sch)) continue;
+            *n_fft = m;
+            return CWT_OK;
+        }
+        return CWT_EUNSUPPORTED;
+    }
+    if (pad_policy != CWT_PAD_POW2) return CWT_EINVAL;
     if (samples > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
     int N = cwtk::kMinFft;
     while (N < samples) N <<= 1;
@@ -176,8 +193,15 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     }
     int N = 0;
     if (o.fft_length != 0) {
-        if (o.fft_length < samples || !is_pow2(o.fft_length) || o.fft_length < cwtk::kMinFft)
-            return CWT_EINVAL;
+        if (o.fft_length < samples || o.fft_length < cwtk::kMinFft) return CWT_EINVAL;
+        if (!is_pow2(o.fft_length)) {
+            cwtk::MrSchedule sch;
+            int x = o.fft_length;
+            for (int f : {2, 3, 5, 7})
+                while (x % f == 0) x /= f;
+            if (x != 1) return CWT_EINVAL;  // not 2,3,5,7-smooth
+            if (!cwtk::mr_schedule(o.fft_length, &sch)) return CWT_EUNSUPPORTED;
+        }
         if (o.fft_length > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
         N = o.fft_length;
     } else {
@@ -193,8 +217,10 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->S = n_freqs;
     p->N = N;
     p->d = o.decimation;
+    p->mr = !is_pow2(N);
+    if (p->mr) cwtk::mr_schedule(N, &p->sch);
     int f = 1;
-    while ((p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
+    while (!p->mr && (p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
     p->fold = f;
     p->M = N / f;
     p->sub = p->d / f;
@@ -218,6 +244,11 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->bytes = bank_b + band_b + spec_b;
     cudaStream_t st = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess && p->mr) {
+        e = cudaMalloc(&p->twN, sizeof(float2) * (size_t)N);
+        if (e == cudaSuccess) e = cwtk::make_twiddles_n(N, p->twN, st);
+        p->bytes += sizeof(float2) * (size_t)N;
+    }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) {
@@ -329,7 +360,7 @@ cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, 
                wph = p->outputs & CWT_OUT_PHASE;
     if (wc != (d_complex != nullptr) || wp != (d_power != nullptr) || wph != (d_phase != nullptr))
         return CWT_EINVAL;
-    if (p->io != CWT_DTYPE_F32) return CWT_EUNSUPPORTED;
+    if (p->io != CWT_DTYPE_F32 || p->mr) return CWT_EUNSUPPORTED;  // batches pad each epoch to pow2
     for (int i = 0; i < n_epochs; ++i) {
         const cwt_epoch &e = epochs[i];
         if (e.samples < 1 || e.samples > p->n || e.in_offset < 0 || e.out_offset < 0) return CWT_EINVAL;

@@ -116,6 +116,7 @@ cudaError_t fft_dispatch(int log2n, const float2 *in, float2 *out, int batch, co
 }  // namespace
 
 cudaError_t launch_forward(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    if (p->mr) return launch_forward_mr(p, signal, st);
     const int log2n = ilog2c(p->N);
     if (log2n > kMaxFftLog2) return launch_forward_cluster(p, signal, st);
     if (p->io == CWT_DTYPE_F64)

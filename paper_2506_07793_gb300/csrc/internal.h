@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "cwt.h"
+#include "mixed_radix.cuh"
 
 namespace cwtk {
 
@@ -46,6 +47,9 @@ struct cwt_plan_s {
     int io = CWT_DTYPE_F32;
     std::vector<double> freqs, cycles;
 
+    bool mr = false;            // smooth (non power-of-two) N: mixed-radix kernels
+    cwtk::MrSchedule sch{};     // their pass schedule
+    float2 *twN = nullptr;      // exp(2 pi i m / N), m < N (mixed-radix plans only)
     float *bank = nullptr;    // [S][N] W_s[k] / N (real)
     int *band = nullptr;      // [S][2]: start, length
     float2 *spec = nullptr;   // [C][N] forward spectra (workspace)
@@ -99,6 +103,12 @@ cudaError_t launch_fft_cluster(const float2 *in, float2 *out, int log2n, int bat
 // prepare_only: build the work items, generate missing banks and autotune a
 // new batch shape (its candidate runs write valid outputs); otherwise launch
 // the chosen schedule's graph once.
+// Smooth lengths (smooth.cu): schedule, per-N twiddles, kernels.
+bool mr_schedule(int N, MrSchedule *out);
+cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st);
+cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
+                                  cudaStream_t st);
 cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, const float *in,
                           float2 *oc, float *op, float *oph, cudaStream_t st, bool prepare_only);
 void batch_stats(const cwt_plan_s *p, cwt_batch_stats *s);

@@ -175,6 +175,7 @@ cudaError_t sb_dispatch(int log2m, const SBArgs &a, cudaStream_t st) {
 
 cudaError_t launch_scale_block(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
                                cudaStream_t st) {
+    if (p->mr) return launch_scale_block_mr(p, out_c, out_p, out_ph, st);
     if (p->M > kMaxFft) return launch_scale_block_cluster(p, out_c, out_p, out_ph, st);
     SBArgs a;
     a.spec = p->spec;

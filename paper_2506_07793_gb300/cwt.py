@@ -300,9 +300,10 @@ class CWT:
     """
 
     def __init__(self, channels, samples, fs, freqs, n_cycles, outputs=("power",),
-                 wavelet="morlet", dtype="f32", decimation=1, fft_length=0):
+                 wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2"):
         opt = cwt_options_init()
         opt.decimation = int(decimation)
+        opt.pad_policy = {"pow2": CWT_PAD_POW2, "smooth": CWT_PAD_SMOOTH}[pad]
         opt.io_dtype = CWT_DTYPE_F64 if dtype in ("f64", "float64") else CWT_DTYPE_F32
         opt.fft_length = int(fft_length)
         kinds = 0

@@ -56,6 +56,14 @@ def test_pow2_padding(lib, n, N):
     assert lib.cwt_fft_length(n) == N
 
 
+@pytest.mark.parametrize("n,N", [(1, 32), (97, 98), (122, 125), (500, 500), (3001, 3024),
+                                 (10000, 10000), (14000, 14000), (14401, 14580), (15000, 15000),
+                                 (15100, 15360), (16001, 16384), (16383, 16384)])
+def test_smooth_padding(lib, n, N):
+    """Section "Fast Fourier transform": smallest 2,3,5,7-smooth length >= n."""
+    assert lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) == N
+
+
 def test_padding_limits(lib):
     with pytest.raises(lib.CWTError) as e:
         lib.cwt_fft_length(0)
@@ -64,7 +72,7 @@ def test_padding_limits(lib):
         lib.cwt_fft_length(131073)
     assert e.value.status == lib.CWT_EUNSUPPORTED
     with pytest.raises(lib.CWTError) as e:
-        lib.cwt_fft_length(100, lib.CWT_PAD_SMOOTH)
+        lib.cwt_fft_length(16385, lib.CWT_PAD_SMOOTH)  # smooth lengths above 16384 are not built
     assert e.value.status == lib.CWT_EUNSUPPORTED
 
 
@@ -73,7 +81,7 @@ BAD = [
     dict(freqs=[10.0, 0.0]), dict(freqs=[10.0, 250.0]), dict(freqs=[-1.0]),
     dict(n_cycles=[7.0, 0.0]), dict(n_cycles=[7.0, float("inf")]),
     dict(wavelet=7), dict(kinds=0), dict(kinds=8), dict(decimation=0), dict(io=5),
-    dict(precision=9), dict(fft_length=100), dict(fft_length=64, samples=100),
+    dict(precision=9), dict(fft_length=101), dict(fft_length=64, samples=100),
 ]
 
 

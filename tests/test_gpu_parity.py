@@ -31,11 +31,11 @@ def lib():
 
 
 def run_gpu(lib, x, fs, freqs, cycles, outputs, dtype="f32", decimation=1, wavelet="morlet",
-            fft_length=0):
+            fft_length=0, pad="pow2"):
     import torch
     C, n = x.shape
     t = lib.CWT(C, n, fs, freqs, cycles, outputs=outputs, dtype=dtype, decimation=decimation,
-                wavelet=wavelet, fft_length=fft_length)
+                wavelet=wavelet, fft_length=fft_length, pad=pad)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = t(xt)
     torch.cuda.synchronize()
@@ -304,3 +304,40 @@ def test_channel_shards_equal_the_whole(lib):
             assert torch.equal(out["power"], ref["power"][c0:c1])
             part.close()
     whole.close()
+
+
+SMOOTH = [
+    # (C, n, fs, freqs, cycles, kwargs) -- smooth padded lengths: 98, 125, 500, 3024, 10000, 14000
+    (2, 97, 100.0, [9.0, 30.0], [3.0, 7.0], {}),
+    (3, 122, 125.0, [11.0, 50.0], [5.0, 7.0], {}),
+    (2, 500, 500.0, [4.0, 40.0, 200.0], [3.0, 7.0, 10.0], dict(dtype="f64")),
+    (3, 3001, 1000.0, np.geomspace(1, 400, 6), np.linspace(3, 10, 6), dict(decimation=3)),
+    (2, 10000, 1000.0, [0.8, 10.0, 99.0], [3.0, 6.0, 10.0], {}),
+    (1, 14000, 2000.0, [5.0, 300.0], [7.0, 7.0], {}),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SMOOTH)))
+def test_smooth_padding_every_row(lib, case):
+    """The paper's padding (Section "Fast Fourier transform"): 2,3,5,7-smooth N,
+    mixed-radix kernels; parity with the oracle at the same N."""
+    C, n, fs, freqs, cycles, kw = SMOOTH[case]
+    kw = dict(kw)
+    dtype = kw.pop("dtype", "f32")
+    x = eeg(950 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), dtype=dtype,
+                     pad="smooth", **kw)
+    assert N == lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) and N < 16384
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=kw.get("decimation", 1))
+    check(res, ref)
+
+
+def test_fused_workload_smooth_padding_sampled_rows(lib):
+    """The fused workload under the paper's own padding: N = 10000 (no padding)."""
+    w = workload("fused")
+    x = w.signal()
+    res, N = run_gpu(lib, x, w.fs, w.freqs, w.n_cycles, w.outputs, pad="smooth")
+    assert N == 10000
+    rows = [(c, s) for c in (0, 63) for s in (0, 1, 50, 99)]
+    ref = oracle.cwt_rows(x, N, w.fs, w.freqs, w.n_cycles, rows)
+    check({k: np.stack([v[c, s] for c, s in rows]) for k, v in res.items()}, ref)
