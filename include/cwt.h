@@ -64,7 +64,9 @@ typedef enum {
 typedef enum {
     CWT_WAVELET_MORLET = 0, /* Eq. 3 */
     CWT_WAVELET_GABOR = 1,  /* Eq. 4 (Morlet without the admissibility term) */
-    CWT_WAVELET_GMW = 2     /* Eq. 5: not implemented (CWT_EUNSUPPORTED) */
+    CWT_WAVELET_GMW = 2     /* Eq. 5, generalized Morse wavelet with the Heaviside
+                               step U(omega) in place of sign(omega); n_cycles[s]
+                               holds beta_s and the options hold gamma */
 } cwt_wavelet;
 
 /* Output kinds, a bitmask (Section "Precision": real/imaginary, phase, power). */
@@ -127,7 +129,10 @@ typedef struct {
                        length <= 16384 (see cwt_pad_policy) */
     int io_dtype;   /* cwt_dtype of the signal and of every output (default F32);
                        F64 is converted to FP32 on load and back on store */
-    int reserved[11];
+    int reserved0;
+    double gmw_gamma; /* gamma of the generalized Morse wavelet (Eq. 5), > 0,
+                         default 3; read only for CWT_WAVELET_GMW */
+    int reserved[8];
 } cwt_options;
 
 typedef struct {
@@ -162,13 +167,15 @@ cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 /*
  * cwt_plan_create -- validate, pick N, allocate the plan's device memory on
  * the current CUDA device and generate the wavelet bank there in FP64
- * (Eq. 3/Eq. 4 summed over aliases, normalised to unit energy, rounded to
+ * (Eq. 3/4/5 summed over aliases, normalised to unit energy, rounded to
  * FP32) together with each scale's non-negligible band (Section "Optimizing
  * performance": wavelets are generated in GPU memory first).
  *   channels, samples  C >= 1, n >= 1
  *   fs                 sampling rate in Hz, > 0
- *   freqs_hz[n_freqs]  host array, each 0 < F < fs/2
- *   n_cycles[n_freqs]  host array, each > 0 (sigma of Eq. 3)
+ *   freqs_hz[n_freqs]  host array, each 0 < F < fs/2 (Morlet/Gabor: the
+ *                      carrier; GMW: the peak frequency of the spectrum)
+ *   n_cycles[n_freqs]  host array, each > 0 (Morlet/Gabor: sigma of Eq. 3;
+ *                      GMW: beta of Eq. 5, at most 1000)
  *   wavelet            cwt_wavelet
  *   output_kinds       non-empty subset of CWT_OUT_*
  *   opt                NULL for defaults
@@ -257,7 +264,9 @@ typedef struct {
     double hop_seconds;       /* hop length in seconds (default 0.05) */
     size_t mem_budget_bytes;  /* device bytes for streams (0 = no limit) */
     unsigned output_kinds;    /* only CWT_OUT_POWER is built */
-    int reserved[7];
+    int reserved0;
+    double gmw_gamma;         /* gamma for CWT_WAVELET_GMW (default 3) */
+    int reserved[4];
 } cwt_server_options;
 
 typedef struct {

@@ -33,14 +33,17 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         lib.oracle_periodised_wavelet.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                                  ctypes.c_double, ctypes.c_int, dp, dp]
+                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                  dp, dp]
         lib.oracle_periodised_wavelet.restype = ctypes.c_int
         lib.oracle_wavelet.argtypes = lib.oracle_periodised_wavelet.argtypes
         lib.oracle_wavelet.restype = ctypes.c_int
         lib.oracle_cwt_rows.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                        dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip,
-                                        ctypes.c_int, dp, dp, ctypes.c_int]
+                                        dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, ctypes.c_int]
         lib.oracle_cwt_rows.restype = ctypes.c_int
+        lib.oracle_gmw_spectrum.argtypes = [ctypes.c_double] * 4
+        lib.oracle_gmw_spectrum.restype = ctypes.c_double
         lib.oracle_dft.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.oracle_dft.restype = ctypes.c_int
         _lib = lib
@@ -55,37 +58,46 @@ def _ip(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 
 
-WAVELETS = {"morlet": 0, "gabor": 1}
+WAVELETS = {"morlet": 0, "gabor": 1, "gmw": 2}
 
 
-def periodised_wavelet(freq, n_cycles, fs, N, wavelet="morlet"):
-    """p[m] = sum_r psi((m + rN)/fs), m in [0, N) -- before normalisation."""
+def gmw_spectrum(nu, freq, beta, gamma):
+    """Eq. 5 with the Heaviside step: the GMW spectrum at nu Hz, peak 2 at freq."""
+    return _load().oracle_gmw_spectrum(float(nu), float(freq), float(beta), float(gamma))
+
+
+def periodised_wavelet(freq, n_cycles, fs, N, wavelet="morlet", gamma=3.0):
+    """p[m] = sum_r psi((m + rN)/fs), m in [0, N) -- before normalisation.
+
+    For wavelet="gmw", n_cycles is beta and gamma is Eq. 5's gamma."""
     lib = _load()
     re = np.zeros(N)
     im = np.zeros(N)
-    rc = lib.oracle_periodised_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(fs),
-                                       int(N), _dp(re), _dp(im))
+    rc = lib.oracle_periodised_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles),
+                                       float(gamma), float(fs), int(N), _dp(re), _dp(im))
     if rc != 0:
         raise ValueError("oracle_periodised_wavelet: bad argument")
     return re + 1j * im
 
 
-def wavelet(freq, n_cycles, fs, N, wavelet="morlet"):
+def wavelet(freq, n_cycles, fs, N, wavelet="morlet", gamma=3.0):
     """Unit-energy N-periodised sampled wavelet of one scale (complex128)."""
     lib = _load()
     re = np.zeros(N)
     im = np.zeros(N)
-    rc = lib.oracle_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(fs), int(N),
-                            _dp(re), _dp(im))
+    rc = lib.oracle_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(gamma),
+                            float(fs), int(N), _dp(re), _dp(im))
     if rc != 0:
         raise ValueError("oracle_wavelet: bad argument")
     return re + 1j * im
 
 
-def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", threads=None):
+def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", threads=None,
+             gamma=3.0):
     """Complex CWT coefficients of the (channel, scale) pairs in `rows`.
 
     x: [C][n] real signal.  Returns complex128 [len(rows)][ceil(n/d)].
+    For wavelet="gmw", n_cycles holds beta per scale and gamma is shared.
     """
     lib = _load()
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
@@ -105,14 +117,15 @@ def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", th
     if threads is None:
         threads = os.cpu_count() or 1
     rc = lib.oracle_cwt_rows(_dp(x), C, n, int(N), float(fs), _dp(freqs), _dp(n_cycles),
-                             len(freqs), WAVELETS[wavelet], d, _ip(rc_), _ip(rs_), len(rows),
+                             len(freqs), WAVELETS[wavelet], float(gamma), d, _ip(rc_), _ip(rs_),
+                             len(rows),
                              _dp(out_re), _dp(out_im), int(threads))
     if rc != 0:
         raise ValueError(f"oracle_cwt_rows failed ({rc})")
     return out_re + 1j * out_im
 
 
-def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None):
+def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None, gamma=3.0):
     """Complex CWT of every row: complex128 [C][S][ceil(n/d)]."""
     x = np.asarray(x, dtype=np.float64)
     if x.ndim == 1:
@@ -120,7 +133,7 @@ def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None)
     C = x.shape[0]
     S = len(np.atleast_1d(freqs))
     rows = [(c, s) for c in range(C) for s in range(S)]
-    out = cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation, wavelet, threads)
+    out = cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation, wavelet, threads, gamma)
     return out.reshape(C, S, -1)
 
 

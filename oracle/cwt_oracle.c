@@ -19,6 +19,14 @@
  *     kappa makes the wavelet zero-mean (the Morlet correction term; with
  *     kappa = 0 it is the Gabor wavelet of Eq. 4).
  *
+ *     The generalized Morse wavelet (GMW, Eq. 5) has no closed time-domain
+ *     form: it is defined by its spectrum.  With the Heaviside step U in
+ *     place of the printed sign() (the analytic GMW), peak frequency F and
+ *     parameters beta, gamma:
+ *         Psi(nu) = U(nu) alpha w^beta exp(-w^gamma),  w = w_p nu / F,
+ *         w_p = (beta / gamma)^(1/gamma),  alpha = 2 (e gamma / beta)^(beta/gamma),
+ *     so Psi peaks at nu = F with value 2.
+ *
  *  2. The FFT path computes a CYCLIC convolution over the padded length N
  *     (Eq. 1 and Eq. 2: the inverse FFT of a product of spectra).  Sampling
  *     the analytic spectrum on N bins is the same as convolving cyclically
@@ -26,6 +34,11 @@
  *         p[m] = sum_{r in Z} psi((m + r N) / fs),   m = 0..N-1,
  *     (indices m > N/2 hold negative time).  The sum over r runs over every
  *     replica whose Gaussian envelope is not exactly zero in double.
+ *     For the GMW the same periodised sampled wavelet is reached from its
+ *     spectrum: by Poisson summation its DFT is proportional to
+ *         P[k] = sum_{q >= 0} Psi((k/N + q) fs)
+ *     (negative frequencies vanish under U), so p = IDFT_N(P), computed here
+ *     by the O(N^2) definition of the inverse DFT (no FFT).
  *
  *  3. Each scale is normalised to unit discrete energy,
  *         pn[m] = p[m] / sqrt(sum_m |p[m]|^2).
@@ -72,13 +85,84 @@ static void gabor_psi(double tau, double F, double sigma, double *re, double *im
     *im = env * sin(ph);
 }
 
-/* Step 2: p[m] = sum_r psi((m + r N) / fs).  kind 0 = Morlet, 1 = Gabor.
- * Returns 0, or -1 on a bad argument. */
-int oracle_periodised_wavelet(int kind, double F, double sigma, double fs, int N,
+/* Step 1, GMW: Psi(nu) of Eq. 5 with U(nu), peak at nu = F (value 2). */
+double oracle_gmw_spectrum(double nu, double F, double beta, double gamma)
+{
+    if (!(nu > 0.0))
+        return 0.0;
+    double wp = pow(beta / gamma, 1.0 / gamma);
+    double w = wp * nu / F;
+    double log_alpha = log(2.0) + (beta / gamma) * log(exp(1.0) * gamma / beta);
+    /* alpha w^beta exp(-w^gamma), evaluated through its logarithm so that
+     * neither w^beta nor alpha overflows on its own */
+    return exp(log_alpha + beta * log(w) - pow(w, gamma));
+}
+
+/* Step 2, GMW: P[k] = sum_{q >= 0} Psi((k/N + q) fs), then p = IDFT_N(P)
+ * (with the 1/N).  Psi rises to its peak at F and falls after it, so the sum
+ * over q stops at the first term past the peak that is exactly zero. */
+static int gmw_periodised(double F, double beta, double gamma, double fs, int N, double *p_re,
+                          double *p_im)
+{
+    double *P = (double *)malloc(sizeof(double) * (size_t)N);
+    double *c = (double *)malloc(sizeof(double) * (size_t)N);
+    double *s = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!P || !c || !s) {
+        free(P);
+        free(c);
+        free(s);
+        return -2;
+    }
+    for (int k = 0; k < N; ++k) {
+        double sum = 0.0;
+        for (long q = 0;; ++q) {
+            double nu = ((double)k / (double)N + (double)q) * fs;
+            double term = oracle_gmw_spectrum(nu, F, beta, gamma);
+            sum += term;
+            if (nu > F && term == 0.0)
+                break;
+        }
+        P[k] = sum;
+    }
+    /* the N-th roots of unity exp(+2 pi i j / N); the exponent k m is reduced
+     * mod N in integers so that every angle is exact */
+    for (int j = 0; j < N; ++j) {
+        double ang = 2.0 * ORACLE_PI * (double)j / (double)N;
+        c[j] = cos(ang);
+        s[j] = sin(ang);
+    }
+    for (int m = 0; m < N; ++m) {
+        double sre = 0.0, sim = 0.0;
+        int j = 0; /* j = k m mod N, stepped by m */
+        for (int k = 0; k < N; ++k) {
+            sre += P[k] * c[j];
+            sim += P[k] * s[j];
+            j += m;
+            if (j >= N)
+                j -= N;
+        }
+        p_re[m] = sre / (double)N;
+        p_im[m] = sim / (double)N;
+    }
+    free(P);
+    free(c);
+    free(s);
+    return 0;
+}
+
+/* Step 2: p[m] = sum_r psi((m + r N) / fs).  kind 0 = Morlet, 1 = Gabor
+ * (sigma = n_cycles), 2 = GMW (sigma = beta; gamma used only here).
+ * Returns 0, -1 on a bad argument, -2 on allocation failure. */
+int oracle_periodised_wavelet(int kind, double F, double sigma, double gamma, double fs, int N,
                               double *p_re, double *p_im)
 {
-    if (N <= 0 || !(F > 0.0) || !(sigma > 0.0) || !(fs > 0.0) || (kind != 0 && kind != 1))
+    if (N <= 0 || !(F > 0.0) || !(sigma > 0.0) || !(fs > 0.0) || kind < 0 || kind > 2)
         return -1;
+    if (kind == 2) {
+        if (!(gamma > 0.0))
+            return -1;
+        return gmw_periodised(F, sigma, gamma, fs, N, p_re, p_im);
+    }
     double a = sigma / (2.0 * ORACLE_PI * F);
     double reach = ORACLE_ENVELOPE_RADIUS * a * fs; /* in samples */
     for (int m = 0; m < N; ++m) {
@@ -102,9 +186,10 @@ int oracle_periodised_wavelet(int kind, double F, double sigma, double fs, int N
 }
 
 /* Steps 2 + 3: the unit-energy periodised wavelet of one scale. */
-int oracle_wavelet(int kind, double F, double sigma, double fs, int N, double *w_re, double *w_im)
+int oracle_wavelet(int kind, double F, double sigma, double gamma, double fs, int N, double *w_re,
+                   double *w_im)
 {
-    int rc = oracle_periodised_wavelet(kind, F, sigma, fs, N, w_re, w_im);
+    int rc = oracle_periodised_wavelet(kind, F, sigma, gamma, fs, N, w_re, w_im);
     if (rc != 0)
         return rc;
     double e = 0.0;
@@ -175,8 +260,9 @@ static void *conv_worker(void *arg)
  *   x        [C][n] signal (double)
  *   N        cyclic length (>= n)
  *   fs       sampling rate (Hz)
- *   freqs, n_cycles [S]: carrier F_s and sigma_s of each scale
- *   kind     0 = Morlet, 1 = Gabor
+ *   freqs, n_cycles [S]: carrier F_s and sigma_s of each scale (GMW: peak
+ *            frequency F_s and beta_s)
+ *   kind     0 = Morlet, 1 = Gabor, 2 = GMW (with gamma)
  *   d        decimation (>= 1); n_out = ceil(n / d)
  *   row_c, row_s [n_rows]: channel and scale index of each requested row
  *   out_re, out_im [n_rows][n_out]
@@ -184,7 +270,7 @@ static void *conv_worker(void *arg)
  * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
  */
 int oracle_cwt_rows(const double *x, int C, int n, int N, double fs, const double *freqs,
-                    const double *n_cycles, int S, int kind, int d, const int *row_c,
+                    const double *n_cycles, int S, int kind, double gamma, int d, const int *row_c,
                     const int *row_s, int n_rows, double *out_re, double *out_im, int n_threads)
 {
     if (C <= 0 || n <= 0 || N < n || S <= 0 || d < 1 || n_rows < 0 || !(fs > 0.0))
@@ -203,7 +289,7 @@ int oracle_cwt_rows(const double *x, int C, int n, int N, double fs, const doubl
     }
     int rc = 0;
     for (int s = 0; s < S && rc == 0; ++s)
-        rc = oracle_wavelet(kind, freqs[s], n_cycles[s], fs, N, wre + (size_t)s * N,
+        rc = oracle_wavelet(kind, freqs[s], n_cycles[s], gamma, fs, N, wre + (size_t)s * N,
                             wim + (size_t)s * N);
     if (rc == 0) {
         conv_job J;

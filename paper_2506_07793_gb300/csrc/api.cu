@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <new>
 
@@ -129,6 +130,9 @@ const char *cwt_status_str(cwt_status s) {
     return "CWT_UNKNOWN_STATUS";
 }
 
+// the Python binding mirrors this layout
+static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24, "cwt_options layout");
+
 cwt_status cwt_options_init(cwt_options *opt) {
     if (!opt) return CWT_EINVAL;
     std::memset(opt, 0, sizeof(*opt));
@@ -137,6 +141,7 @@ cwt_status cwt_options_init(cwt_options *opt) {
     opt->pad_policy = CWT_PAD_POW2;
     opt->fft_length = 0;
     opt->io_dtype = CWT_DTYPE_F32;
+    opt->gmw_gamma = 3.0;
     return CWT_OK;
 }
 
@@ -178,13 +183,12 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             return CWT_EINVAL;
         if (!(n_cycles[i] > 0.0) || !std::isfinite(n_cycles[i])) return CWT_EINVAL;
     }
-    if (wavelet != CWT_WAVELET_MORLET && wavelet != CWT_WAVELET_GABOR)
-        return wavelet == CWT_WAVELET_GMW ? CWT_EUNSUPPORTED : CWT_EINVAL;
     const unsigned all = CWT_OUT_COMPLEX | CWT_OUT_POWER | CWT_OUT_PHASE;
     if (output_kinds == 0 || (output_kinds & ~all)) return CWT_EINVAL;
     cwt_options o;
     cwt_options_init(&o);
     if (opt) o = *opt;
+    if (!cwtk::wavelet_params_ok(wavelet, n_cycles, n_freqs, o.gmw_gamma)) return CWT_EINVAL;
     if (o.decimation < 1) return CWT_EINVAL;
     if (o.io_dtype != CWT_DTYPE_F32 && o.io_dtype != CWT_DTYPE_F64) return CWT_EINVAL;
     if (o.precision != CWT_PREC_FP32) {
@@ -227,6 +231,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->n_out = (samples + p->d - 1) / p->d;
     p->fs = fs;
     p->wavelet = wavelet;
+    p->gmw_gamma = o.gmw_gamma;
     p->outputs = output_kinds;
     p->io = o.io_dtype;
     p->freqs.assign(freqs_hz, freqs_hz + n_freqs);

@@ -43,6 +43,7 @@ struct cwt_plan_s {
     int n_out = 0;
     double fs = 0;
     int wavelet = 0;
+    double gmw_gamma = 3.0;  // gamma of Eq. 5 (CWT_WAVELET_GMW only)
     unsigned outputs = 0;
     int io = CWT_DTYPE_F32;
     std::vector<double> freqs, cycles;
@@ -84,6 +85,18 @@ cudaError_t ensure_smem_attr(K *kernel, int bytes, unsigned *done) {
 }
 
 // Launchers (return the launch error, if any).
+// Host-side check of the wavelet kind and its shape parameters (n_cycles
+// already checked > 0 and finite): Morlet/Gabor take sigma = n_cycles; the
+// generalized Morse wavelet takes beta = n_cycles <= 1000 and 0 < gamma <= 64.
+inline bool wavelet_params_ok(int wavelet, const double *n_cycles, int n, double gamma) {
+    if (wavelet == CWT_WAVELET_MORLET || wavelet == CWT_WAVELET_GABOR) return true;
+    if (wavelet != CWT_WAVELET_GMW) return false;
+    if (!(gamma > 0.0) || !(gamma <= 64.0)) return false;
+    for (int i = 0; i < n; ++i)
+        if (!(n_cycles[i] <= 1000.0)) return false;
+    return true;
+}
+
 cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st);
 // Bank and bands of the plan's scales for padded length N into the given
 // buffers ([S][N] floats, [S][2] ints); synchronises `st`.

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -236,6 +237,7 @@ cudaError_t bank_for(cwt_server_s *srv, double fs, int *idx) {
         tmp.S = srv->S;
         tmp.fs = fs;
         tmp.wavelet = srv->wavelet;
+        tmp.gmw_gamma = srv->opt.gmw_gamma;
         tmp.freqs = srv->freqs;
         tmp.cycles = srv->cycles;
         cudaStream_t bs = nullptr;
@@ -286,6 +288,10 @@ cwt_status cuda_fail(cwt_server_s *s, cudaError_t e) {
 
 extern "C" {
 
+// the Python binding mirrors this layout
+static_assert(sizeof(cwt_server_options) == 56 && offsetof(cwt_server_options, gmw_gamma) == 32,
+              "cwt_server_options layout");
+
 cwt_status cwt_server_options_init(cwt_server_options *o) {
     if (!o) return CWT_EINVAL;
     std::memset(o, 0, sizeof(*o));
@@ -294,6 +300,7 @@ cwt_status cwt_server_options_init(cwt_server_options *o) {
     o->hop_seconds = 0.05;
     o->window = kSW;
     o->output_kinds = CWT_OUT_POWER;
+    o->gmw_gamma = 3.0;
     return CWT_OK;
 }
 
@@ -304,11 +311,10 @@ cwt_status cwt_server_create(cwt_server *out, const double *freqs_hz, const doub
         if (!(freqs_hz[i] > 0.0) || !std::isfinite(freqs_hz[i]) || !(n_cycles[i] > 0.0) ||
             !std::isfinite(n_cycles[i]))
             return CWT_EINVAL;
-    if (wavelet != CWT_WAVELET_MORLET && wavelet != CWT_WAVELET_GABOR)
-        return wavelet == CWT_WAVELET_GMW ? CWT_EUNSUPPORTED : CWT_EINVAL;
     cwt_server_options o;
     cwt_server_options_init(&o);
     if (opt) o = *opt;
+    if (!wavelet_params_ok(wavelet, n_cycles, n_freqs, o.gmw_gamma)) return CWT_EINVAL;
     if (o.max_streams < 1 || !(o.hop_seconds > 0.0) || !std::isfinite(o.hop_seconds)) return CWT_EINVAL;
     if (o.window != kSW) return CWT_EUNSUPPORTED;
     if (o.output_kinds != CWT_OUT_POWER) return CWT_EUNSUPPORTED;

@@ -19,6 +19,14 @@
 // The constant prefactors of Eq. 3 (c_sigma, pi^(-1/4)) cancel in the
 // normalisation.  The spectrum is real because psi(-t) = conj(psi(t)).
 //
+// Generalized Morse wavelet (Eq. 5, Section "Fourier transformed formula"),
+// with the Heaviside step U in place of the printed sign() so that the
+// wavelet stays analytic:  G(nu) = U(nu) alpha w^beta exp(-w^gamma) with
+// w = w_p nu / F, w_p = (beta/gamma)^(1/gamma) the peak of w^beta exp(-w^gamma)
+// (so the spectrum peaks at nu = F) and alpha = 2 (e gamma / beta)^(beta/gamma)
+// (peak value 2).  beta comes in the sigma slot, gamma per plan; the same
+// alias sum and normalisation follow.
+//
 // Band.  Bins whose |P| is below kBandRelThreshold of the scale's peak are
 // skipped by the hot kernel; the band is the signed-frequency interval
 // [kmin, kmax] holding every bin above it (it wraps modulo N).
@@ -53,23 +61,47 @@ __device__ __forceinline__ double spectrum_g(double nu, double F, double sigma, 
     return g;
 }
 
+// Eq. 5 at nu (Hz) with U(nu); wp = w_p, la = ln(alpha).
+__device__ __forceinline__ double spectrum_gmw(double nu, double F, double beta, double gamma,
+                                               double wp, double la) {
+    if (!(nu > 0.0)) return 0.0;
+    const double w = wp * nu / F;
+    return exp(la + beta * log(w) - pow(w, gamma));
+}
+
 // grid (ceil(N / 256), S): raw[s][k] = sum_q G((k/N + q) fs) and per-block
 // partial sums of raw^2 (fixed-order tree, so the result is deterministic).
+// kind: CWT_WAVELET_MORLET / _GABOR (sig = sigma) or _GMW (sig = beta).
 __global__ void __launch_bounds__(kBankThreads)
 bank_raw_kernel(int N, double fs, const double *__restrict__ F, const double *__restrict__ sig,
-                int gabor, double *__restrict__ raw, double *__restrict__ partial) {
+                int kind, double gamma, double *__restrict__ raw, double *__restrict__ partial) {
     __shared__ double red[kBankThreads];
     const int s = blockIdx.y;
     const int k = blockIdx.x * kBankThreads + threadIdx.x;
     double v = 0.0;
     if (k < N) {
         const double f = F[s], sg = sig[s];
-        const double kappa = gabor ? 0.0 : exp(-0.5 * sg * sg);
-        const double reach = 40.0 * f / sg;  // exp(-x) underflows past x ~ 745
-        const double nu_lo = -reach, nu_hi = f + reach;
         const double base = (double)k / (double)N;
-        const double q_lo = ceil(nu_lo / fs - base), q_hi = floor(nu_hi / fs - base);
-        for (double q = q_lo; q <= q_hi; q += 1.0) v += spectrum_g((base + q) * fs, f, sg, kappa);
+        if (kind == CWT_WAVELET_GMW) {
+            const double beta = sg;
+            const double wp = pow(beta / gamma, 1.0 / gamma);
+            const double la = log(2.0) + (beta / gamma) * (1.0 + log(gamma) - log(beta));
+            // past the peak G decreases; G/2 < exp(-760) (zero in double) once
+            // w^gamma - wp^gamma - beta ln(w / wp) > 760: fixed-point iteration
+            // from the right of the peak
+            const double wpg = pow(wp, gamma);
+            double w = 2.0 * wp;
+            for (int it = 0; it < 12; ++it) w = pow(wpg + 760.0 + beta * log(w / wp), 1.0 / gamma);
+            const double nu_hi = f * w / wp;
+            const double q_hi = floor(nu_hi / fs - base);
+            for (double q = 0.0; q <= q_hi; q += 1.0) v += spectrum_gmw((base + q) * fs, f, beta, gamma, wp, la);
+        } else {
+            const double kappa = kind == CWT_WAVELET_GABOR ? 0.0 : exp(-0.5 * sg * sg);
+            const double reach = 40.0 * f / sg;  // exp(-x) underflows past x ~ 745
+            const double nu_lo = -reach, nu_hi = f + reach;
+            const double q_lo = ceil(nu_lo / fs - base), q_hi = floor(nu_hi / fs - base);
+            for (double q = q_lo; q <= q_hi; q += 1.0) v += spectrum_g((base + q) * fs, f, sg, kappa);
+        }
         raw[(size_t)s * N + k] = v;
     }
     red[threadIdx.x] = v * v;
@@ -200,9 +232,8 @@ cudaError_t launch_bank_n(const cwt_plan_s *p, int N, float *bank, int *band, cu
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e == cudaSuccess) e = cudaEventRecord(t0, st);
     if (e == cudaSuccess) {
-        bank_raw_kernel<<<dim3(nblk, S), kBankThreads, 0, st>>>(N, p->fs, dF, dsig,
-                                                                p->wavelet == CWT_WAVELET_GABOR,
-                                                                raw, partial);
+        bank_raw_kernel<<<dim3(nblk, S), kBankThreads, 0, st>>>(N, p->fs, dF, dsig, p->wavelet,
+                                                                p->gmw_gamma, raw, partial);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

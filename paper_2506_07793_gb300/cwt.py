@@ -34,7 +34,8 @@ CWT_KERNEL_BANK, CWT_KERNEL_FORWARD_FFT, CWT_KERNEL_SCALE_BLOCK, CWT_KERNEL_BATC
 class cwt_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("decimation", ctypes.c_int),
                 ("pad_policy", ctypes.c_int), ("fft_length", ctypes.c_int),
-                ("io_dtype", ctypes.c_int), ("reserved", ctypes.c_int * 11)]
+                ("io_dtype", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("gmw_gamma", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
 
 
 class cwt_plan_info_t(ctypes.Structure):
@@ -60,7 +61,8 @@ class cwt_batch_stats(ctypes.Structure):
 class cwt_server_options(ctypes.Structure):
     _fields_ = [("max_streams", ctypes.c_int), ("window", ctypes.c_int),
                 ("hop_seconds", ctypes.c_double), ("mem_budget_bytes", ctypes.c_size_t),
-                ("output_kinds", ctypes.c_uint), ("reserved", ctypes.c_int * 7)]
+                ("output_kinds", ctypes.c_uint), ("reserved0", ctypes.c_int),
+                ("gmw_gamma", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
 
 
 class cwt_server_stats_t(ctypes.Structure):
@@ -300,10 +302,12 @@ class CWT:
     """
 
     def __init__(self, channels, samples, fs, freqs, n_cycles, outputs=("power",),
-                 wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2"):
+                 wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2",
+                 gmw_gamma=3.0):
         opt = cwt_options_init()
         opt.decimation = int(decimation)
         opt.pad_policy = {"pow2": CWT_PAD_POW2, "smooth": CWT_PAD_SMOOTH}[pad]
+        opt.gmw_gamma = float(gmw_gamma)
         opt.io_dtype = CWT_DTYPE_F64 if dtype in ("f64", "float64") else CWT_DTYPE_F32
         opt.fft_length = int(fft_length)
         kinds = 0

@@ -82,16 +82,19 @@ BAD = [
     dict(n_cycles=[7.0, 0.0]), dict(n_cycles=[7.0, float("inf")]),
     dict(wavelet=7), dict(kinds=0), dict(kinds=8), dict(decimation=0), dict(io=5),
     dict(precision=9), dict(fft_length=101), dict(fft_length=64, samples=100),
+    dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
+    dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]),
 ]
 
 
 @pytest.mark.parametrize("bad", BAD)
 def test_invalid_arguments_rejected_before_cuda(lib, bad):
     a = dict(channels=2, samples=100, fs=500.0, freqs=[10.0, 20.0], n_cycles=[7.0, 7.0],
-             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0)
+             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0)
     a.update(bad)
     o = lib.cwt_options_init()
     o.decimation, o.io_dtype, o.precision, o.fft_length = a["decimation"], a["io"], a["precision"], a["fft_length"]
+    o.gmw_gamma = a["gamma"]
     f = np.asarray(a["freqs"], dtype=np.float64)
     c = np.asarray(a["n_cycles"], dtype=np.float64)
     if len(c) != len(f):
@@ -101,13 +104,22 @@ def test_invalid_arguments_rejected_before_cuda(lib, bad):
     assert e.value.status == lib.CWT_EINVAL
 
 
-@pytest.mark.parametrize("what", ["gmw", "tc_fp16", "tc_bf16", "too_long"])
+def test_option_struct_layout(lib):
+    """The ctypes mirrors of the option structs match the C layout (checked
+    there by static_assert) and the defaults of the *_init functions."""
+    o = lib.cwt_options_init()
+    assert ctypes.sizeof(o) == 64 and type(o).gmw_gamma.offset == 24
+    assert o.gmw_gamma == 3.0 and o.decimation == 1
+    so = lib.cwt_server_options_init()
+    assert ctypes.sizeof(so) == 56 and type(so).gmw_gamma.offset == 32
+    assert so.gmw_gamma == 3.0 and so.max_streams == 32
+
+
+@pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long"])
 def test_unsupported_requests(lib, what):
     o = lib.cwt_options_init()
     wavelet, samples = 0, 100
-    if what == "gmw":
-        wavelet = lib.CWT_WAVELET_GMW
-    elif what == "tc_fp16":
+    if what == "tc_fp16":
         o.precision = lib.CWT_PREC_TC_FP16
     elif what == "tc_bf16":
         o.precision = lib.CWT_PREC_TC_BF16

@@ -31,11 +31,11 @@ def lib():
 
 
 def run_gpu(lib, x, fs, freqs, cycles, outputs, dtype="f32", decimation=1, wavelet="morlet",
-            fft_length=0, pad="pow2"):
+            fft_length=0, pad="pow2", gmw_gamma=3.0):
     import torch
     C, n = x.shape
     t = lib.CWT(C, n, fs, freqs, cycles, outputs=outputs, dtype=dtype, decimation=decimation,
-                wavelet=wavelet, fft_length=fft_length, pad=pad)
+                wavelet=wavelet, fft_length=fft_length, pad=pad, gmw_gamma=gmw_gamma)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = t(xt)
     torch.cuda.synchronize()
@@ -341,3 +341,29 @@ def test_fused_workload_smooth_padding_sampled_rows(lib):
     rows = [(c, s) for c in (0, 63) for s in (0, 1, 50, 99)]
     ref = oracle.cwt_rows(x, N, w.fs, w.freqs, w.n_cycles, rows)
     check({k: np.stack([v[c, s] for c, s in rows]) for k, v in res.items()}, ref)
+
+
+GMW = [
+    # (C, n, fs, freqs, betas, gamma, kwargs)
+    (2, 500, 500.0, [4.0, 40.0, 200.0], [20.0, 20.0, 20.0], 3.0, {}),
+    (3, 1000, 1000.0, np.geomspace(2, 300, 5), [3.0, 8.0, 20.0, 60.0, 120.0], 3.0, dict(decimation=2)),
+    (2, 777, 256.0, [5.0, 100.0], [3.0, 6.5], 1.0, {}),  # Cauchy; 100 Hz aliases past fs
+    (1, 3001, 1000.0, [10.0, 90.0], [8.0, 4.0], 2.0, dict(pad="smooth")),
+    (2, 300, 200.0, [1.0, 50.0], [1.5, 30.0], 0.7, dict(dtype="f64")),
+    (1, 20000, 2000.0, [3.0, 700.0], [20.0, 20.0], 3.0, {}),  # cluster path (N = 32768)
+]
+
+
+@pytest.mark.parametrize("case", range(len(GMW)))
+def test_gmw_every_row(lib, case):
+    """Generalized Morse wavelet (Eq. 5 with U(omega)): the bank generator's
+    alias-summed spectrum against the oracle's inverse-DFT definition."""
+    C, n, fs, freqs, betas, gam, kw = GMW[case]
+    kw = dict(kw)
+    dtype = kw.pop("dtype", "f32")
+    x = eeg(970 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, betas, ("complex", "power", "phase"), dtype=dtype,
+                     wavelet="gmw", gmw_gamma=gam, **kw)
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, betas, decimation=kw.get("decimation", 1),
+                     wavelet="gmw", gamma=gam)
+    check(res, ref)

@@ -33,11 +33,13 @@ def lib():
     return p
 
 
-def server(lib, max_streams=32, budget=0):
+def server(lib, max_streams=32, budget=0, wavelet=None, cycles=CYCLES, gamma=3.0):
     o = lib.cwt_server_options_init()
     o.max_streams = max_streams
     o.mem_budget_bytes = budget
-    return lib.cwt_server_create(FREQS, CYCLES, lib.CWT_WAVELET_MORLET, o)
+    o.gmw_gamma = gamma
+    wv = lib.CWT_WAVELET_MORLET if wavelet is None else wavelet
+    return lib.cwt_server_create(FREQS, cycles, wv, o)
 
 
 def feed(lib, srv, sid, x, chunks, H, C, S):
@@ -60,7 +62,7 @@ def feed(lib, srv, sid, x, chunks, H, C, S):
     return out
 
 
-def hop_reference(x, e, H, fs):
+def hop_reference(x, e, H, fs, wavelet="morlet", cycles=CYCLES, gamma=3.0):
     """Oracle coefficients of the hop, and each row's peak power over the
     whole window.  Errors are normalised by the window peak: the FFT's
     rounding scales with the window, while inside one hop the true values can
@@ -70,8 +72,28 @@ def hop_reference(x, e, H, fs):
     lo = e - W
     seg = x[:, max(lo, 0):e]
     win[:, W - seg.shape[1]:] = seg
-    c = oracle.cwt(win, W, fs, FREQS, CYCLES)
+    c = oracle.cwt(win, W, fs, FREQS, cycles, wavelet=wavelet, gamma=gamma)
     return c[..., W - D - H:W - D], oracle.power(c).max(axis=-1)
+
+
+def test_gmw_hops_match_oracle(lib):
+    """The server with the generalized Morse wavelet (Eq. 5; beta 20, gamma 3)."""
+    fs, C = 1000.0, 2
+    H = 50
+    betas = np.full(len(FREQS), 20.0)
+    x = eeg(702, C, 10 * H, fs, np.float32)
+    srv = server(lib, wavelet=lib.CWT_WAVELET_GMW, cycles=betas, gamma=3.0)
+    try:
+        sid = lib.cwt_stream_open(srv, C, fs)
+        out = feed(lib, srv, sid, x, [3 * H, 3 * H, 4 * H], H, C, len(FREQS))
+        assert len(out) == 10
+        D = (W - H) // 2
+        for first in sorted(out)[::4]:
+            ref, peak = hop_reference(x.astype(np.float64), first + D + H, H, fs, "gmw", betas, 3.0)
+            err = np.abs(out[first] - oracle.power(ref)).max(axis=-1) / peak
+            assert err.max() <= FP32_TOL, (first, err.max())
+    finally:
+        lib.cwt_server_destroy(srv)
 
 
 def test_hops_match_oracle(lib):
