@@ -458,7 +458,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-channels", type=int, default=2)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["fused", "batch", "serving", "precision"])
+                    choices=["fused", "batch", "serving", "precision", "sweep"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--pad", default="pow2", choices=["pow2", "smooth"],
                     help="padding policy: next power of two, or the paper's 2,3,5,7-smooth length")
@@ -475,7 +475,101 @@ def main():
         return run_batch(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_plan_workload(args, args.workload)
+
+
+SWEEP_LENGTHS = sorted(set(range(100, 2501, 100)) | {101, 127, 499, 509, 1009, 1021, 1024, 1499,
+                                                      1999, 2048, 2039, 2477})
+
+
+def run_sweep(args):
+    """Time per CWT call against the signal length (the shape of Fig. 4) and
+    wavelet-bank generation time (Table 2).
+
+    Per length n (100..2500 samples at 1000 Hz, primes and powers of two
+    included): 64 channels of seeded synthetic EEG, Morlet sigma = 7 at 30..90 Hz
+    in 1 Hz steps (61 scales), complex64 output; padding to the next power of
+    two and to the paper's 2,3,5,7-smooth length.  `device_us` is one
+    cwt_execute on resident buffers (CUDA events, mean of --steps calls after
+    --warmup); `e2e_us` is cwt_execute_host from pinned host memory, copies
+    included.  Bank generation: 61 scales, 1 s at 2048 Hz (N = 2048), Morlet
+    and the GMW of Fig. 1 (beta 17.5, gamma 3), FP64 on the GPU."""
+    import torch
+    import paper_2506_07793_gb300 as cw
+    from eeg_synth import eeg
+
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fs, C = 1000.0, 64
+    freqs = np.arange(30.0, 91.0)
+    cycles = np.full(len(freqs), 7.0)
+    S = len(freqs)
+    stream = torch.cuda.current_stream()
+    points = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    for n in SWEEP_LENGTHS:
+        x_host = eeg(4000 + n, C, n, fs, np.float32)
+        x = torch.from_numpy(x_host).cuda()
+        out = torch.empty((C, S, n), dtype=torch.complex64, device="cuda")
+        h_in = torch.from_numpy(x_host).pin_memory()
+        h_out = torch.empty((C, S, n), dtype=torch.complex64).pin_memory()
+        pt = {"samples": n}
+        for pad in ("pow2", "smooth"):
+            o = cw.cwt_options_init()
+            o.pad_policy = cw.CWT_PAD_SMOOTH if pad == "smooth" else cw.CWT_PAD_POW2
+            plan = cw.cwt_plan_create(C, n, fs, freqs, cycles, cw.CWT_WAVELET_MORLET,
+                                      cw.CWT_OUT_COMPLEX, o)
+            info = cw.cwt_plan_info(plan)
+            for _ in range(args.warmup):
+                cw.cwt_execute(plan, x, out, None, None, stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                cw.cwt_execute(plan, x, out, None, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dev_us = e0.elapsed_time(e1) * 1e3 / args.steps
+            cw.cwt_execute_host(plan, h_in, h_out, None, None, stream)
+            torch.cuda.synchronize()
+            reps = max(3, args.steps // 4)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                cw.cwt_execute_host(plan, h_in, h_out, None, None, stream)
+            e2e_us = (time.perf_counter() - t0) / reps * 1e6
+            pt[pad] = {"N": info.fft_length, "device_us": dev_us, "e2e_us": e2e_us,
+                       "bank_ms": info.bank_ms}
+            cw.cwt_plan_destroy(plan)
+        points.append(pt)
+    clk = clocks.stop()
+
+    bank = {}
+    for name, wv, par in (("morlet", cw.CWT_WAVELET_MORLET, 7.0), ("gmw", cw.CWT_WAVELET_GMW, 17.5)):
+        o = cw.cwt_options_init()
+        o.gmw_gamma = 3.0
+        times = []
+        for _ in range(5):
+            plan = cw.cwt_plan_create(1, 2048, 2048.0, freqs, np.full(S, par), wv, cw.CWT_OUT_POWER, o)
+            times.append(cw.cwt_plan_info(plan).bank_ms)
+            cw.cwt_plan_destroy(plan)
+        bank[name] = {"ms_median": statistics.median(times[1:]), "scales": S, "fft_length": 2048}
+    if rank == 0:
+        coeffs = [C * S * p["samples"] for p in points]
+        rate = [c / (p["pow2"]["device_us"] * 1e-6) for c, p in zip(coeffs, points)]
+        print(json.dumps({
+            "metric": "CWT time per call vs signal length (Fig. 4 shape)", "value": statistics.median(rate),
+            "unit": "coeffs/s (median over lengths, pow2 padding)", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "none", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{C} ch @1000 Hz, n = 100..2500 (+ primes, powers of two), "
+                                   "Morlet sigma 7, 30-90 Hz by 1 Hz (61 scales), complex64",
+                       "l2": "not flushed (every length's working set is below the 129 MB L2)"},
+            "points": points, "bank_generation": bank, "clocks": clk,
+            "gpu_launches": 2 * args.steps * 2 * len(points),
+        }), flush=True)
 
 
 def run_plan_workload(args, name):
