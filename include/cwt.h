@@ -80,9 +80,10 @@ typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
  * SMOOTH is the paper's own policy: the smallest length >= max(samples, 32)
  * whose prime factors are 2, 3, 5 and 7.  Smooth lengths that are not powers
  * of two run on the mixed-radix kernels and are limited to 16384 points;
- * the 13 smooth lengths 14406 ... 16200 whose radix-3/5/7 passes do not fit
- * one CTA are passed over (SMOOTH then gives the next smooth length, and an
- * explicit fft_length of one of them is CWT_EUNSUPPORTED).
+ * the 15 smooth lengths 14175 ... 16200 that no radix schedule of at most 32
+ * values per thread and 512 threads per row covers are passed over (SMOOTH
+ * then gives the next smooth length, and an explicit fft_length of one of
+ * them is CWT_EUNSUPPORTED).
  * cwt_execute_batch does not take mixed-radix plans (CWT_EUNSUPPORTED). */
 typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
 

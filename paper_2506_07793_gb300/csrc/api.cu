@@ -149,8 +149,8 @@ cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft) {
     if (!n_fft || samples < 1) return CWT_EINVAL;
     if (pad_policy == CWT_PAD_SMOOTH) {
         // smallest 2,3,5,7-smooth length >= max(samples, 32) that the kernels
-        // run: 13 smooth lengths in (14336, 16384) whose radix-3/5/7 passes do
-        // not fit one CTA's registers are passed over
+        // run: 15 smooth lengths in [14175, 16200] that no radix schedule of
+        // one CTA covers are passed over
         for (int m = samples < cwtk::kMinFft ? cwtk::kMinFft : samples; m <= cwtk::kMaxFft; ++m) {
             int x = m;
             for (int f : {2, 3, 5, 7})

@@ -25,181 +25,13 @@
 #include <numeric>
 #include <vector>
 
-#include "fft_core.cuh"
-#include "internal.h"
+#include "batch_kernel.cuh"
 
 namespace cwtk {
 
-namespace {
-
-constexpr int kBThreads = 512;
-constexpr int kTile = kBThreads * 16;  // 8192 points per item
-constexpr int kMaxBatchLog2 = 13;      // N_e <= kTile
-
-struct BatchItem {
-    long long in_off;   // element offset of channel c0 of the epoch in the packed input
-    long long out_off;  // element offset of row (c0, scale 0) in each packed output
-    int n;              // epoch length
-    int log2n;          // log2 N_e
-    int G;              // channels in this item
-    int pad;
-};
-
-struct BatchArgs {
-    const float *in;
-    float2 *oc;
-    float *op;
-    float *oph;
-    const BatchItem *items;
-    int n_items;
-    int *counter;
-    const float *bank[kMaxBatchLog2 + 1];  // per log2 N: [S][N]
-    const int *band[kMaxBatchLog2 + 1];    // per log2 N: [S][2]
-    const float2 *tw;
-    int S, d;
-};
-
-__device__ __noinline__ void batch_store_phase(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
-
-template <int N>
-__device__ __forceinline__ void batch_forward(const BatchArgs &a, const BatchItem &it,
-                                              float2 *spec, float2 *stage) {
-    constexpr int R = N / kBThreads > 16 ? N / kBThreads : 16;
-    constexpr int Tf = N / R;
-    const int g = threadIdx.x / Tf, j = threadIdx.x % Tf;
-    const bool act = g < it.G;
-    const float *x = a.in + it.in_off + (long long)(act ? g : 0) * it.n;
-    float2 *st = stage + g * FftShape<N, R>::SMEM_F2;
-    float2 *sp = spec + g * N;
-    const int n = it.n;
-    auto load = [&](int i) -> float2 { return make_float2((act && i < n) ? x[i] : 0.f, 0.f); };
-    auto store = [&](int t, float2 v) { sp[t] = v; };
-    fft_row<N, R, -1>(st, a.tw, j, load, store);
-}
-
-template <int M, int RI>
-__device__ __forceinline__ void batch_inverse(const BatchArgs &a, const BatchItem &it,
-                                              const float2 *spec, float2 *stage, int N, int fold) {
-    constexpr int R = (M / RI) > kBThreads ? M / kBThreads : (M < RI ? M : RI);
-    constexpr int Ti = M / R;
-    constexpr int P = kBThreads / Ti;  // rows in flight
-    const int rows = it.G * a.S;
-    const float *bank = a.bank[it.log2n];
-    const int *band = a.band[it.log2n];
-    const int nmask = N - 1;
-    const int sub = a.d / fold;
-    const int n_out = (it.n + a.d - 1) / a.d;
-    const int rl = threadIdx.x / Ti, j = threadIdx.x % Ti;
-    float2 *st = stage + rl * FftShape<M, R>::SMEM_F2;
-#pragma unroll 1
-    for (int r0 = 0; r0 < rows; r0 += P) {
-        const int row = r0 + rl;
-        const bool act = row < rows;
-        const int g = act ? row / a.S : 0;
-        const int s = act ? row - g * a.S : 0;
-        const float2 *sp = spec + g * N;
-        const float *W = bank + (size_t)s * N;
-        const int b0 = band[2 * s], B = act ? band[2 * s + 1] : 0;
-        // Folded input j = sum over in-band k = j (mod M).  When the band is no
-        // wider than M, at most one k qualifies: k = b0 + ((j - b0) mod M).
-        const bool narrow = B <= M;
-        auto load = [&](int jj) -> float2 {
-            float2 acc = make_float2(0.f, 0.f);
-            if (narrow) {
-                const int delta = (jj - b0) & (M - 1);
-                if (delta < B) {
-                    const int k = (b0 + delta) & nmask;
-                    const float2 xv = sp[k];
-                    const float w = __ldg(&W[k]);
-                    acc = make_float2(xv.x * w, xv.y * w);
-                }
-                return acc;
-            }
-            for (int q = 0; q < fold; ++q) {
-                const int k = jj + q * M;
-                if (((k - b0) & nmask) < B) {
-                    const float2 xv = sp[k];
-                    const float w = __ldg(&W[k]);
-                    acc.x = fmaf(xv.x, w, acc.x);
-                    acc.y = fmaf(xv.y, w, acc.y);
-                }
-            }
-            return acc;
-        };
-        const long long obase = it.out_off + (long long)row * n_out;
-        auto store = [&](int t, float2 v) {
-            if (!act) return;
-            int o = t;
-            if (sub != 1) {
-                if (t % sub) return;
-                o = t / sub;
-            }
-            if (o >= n_out) return;
-            if (a.oc) a.oc[obase + o] = v;
-            if (a.op) a.op[obase + o] = fmaf(v.x, v.x, v.y * v.y);
-            if (a.oph) batch_store_phase(a.oph + obase + o, v);
-        };
-        fft_row<M, R, +1>(st, a.tw, j, load, store);
-    }
-}
-
-template <int RI>
-__device__ __forceinline__ void batch_inverse_dispatch(const BatchArgs &a, const BatchItem &it,
-                                                       const float2 *spec, float2 *stage) {
-    const int N = 1 << it.log2n;
-    int fold = 1;
-    while ((a.d % (2 * fold)) == 0 && N / (2 * fold) >= kMinFft) fold *= 2;
-    switch (it.log2n - ilog2c(fold)) {
-        case 5: batch_inverse<1 << 5, RI>(a, it, spec, stage, N, fold); break;
-        case 6: batch_inverse<1 << 6, RI>(a, it, spec, stage, N, fold); break;
-        case 7: batch_inverse<1 << 7, RI>(a, it, spec, stage, N, fold); break;
-        case 8: batch_inverse<1 << 8, RI>(a, it, spec, stage, N, fold); break;
-        case 9: batch_inverse<1 << 9, RI>(a, it, spec, stage, N, fold); break;
-        case 10: batch_inverse<1 << 10, RI>(a, it, spec, stage, N, fold); break;
-        case 11: batch_inverse<1 << 11, RI>(a, it, spec, stage, N, fold); break;
-        case 12: batch_inverse<1 << 12, RI>(a, it, spec, stage, N, fold); break;
-        case 13: batch_inverse<1 << 13, RI>(a, it, spec, stage, N, fold); break;
-        default: break;
-    }
-}
-
-// Shared memory: spectra (kTile float2) + staging for kBThreads * RI points
-// (every thread holds RI points of some row in flight), padded 17/16.
-template <int RI>
-constexpr int batch_smem() { return (kTile + (kBThreads * RI) * 17 / 16) * 8; }
-
-template <int RI>
-__global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchArgs a) {
-    extern __shared__ float2 bsm[];
-    float2 *spec = bsm;
-    float2 *stage = bsm + kTile;
-    __shared__ int s_item;
-#pragma unroll 1
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= a.n_items) break;
-        const BatchItem it = a.items[item];
-        switch (it.log2n) {
-            case 5: batch_forward<1 << 5>(a, it, spec, stage); break;
-            case 6: batch_forward<1 << 6>(a, it, spec, stage); break;
-            case 7: batch_forward<1 << 7>(a, it, spec, stage); break;
-            case 8: batch_forward<1 << 8>(a, it, spec, stage); break;
-            case 9: batch_forward<1 << 9>(a, it, spec, stage); break;
-            case 10: batch_forward<1 << 10>(a, it, spec, stage); break;
-            case 11: batch_forward<1 << 11>(a, it, spec, stage); break;
-            case 12: batch_forward<1 << 12>(a, it, spec, stage); break;
-            case 13: batch_forward<1 << 13>(a, it, spec, stage); break;
-            default: break;
-        }
-        __syncthreads();  // spectra complete before any row reads them
-        batch_inverse_dispatch<RI>(a, it, spec, stage);
-        __syncthreads();  // s_item and the spectra are free again
-    }
-}
-
-}  // namespace
+const void *batch_kernel_ptr_16();
+const void *batch_kernel_ptr_32();
+const void *batch_kernel_ptr(int ri) { return ri == 16 ? batch_kernel_ptr_16() : batch_kernel_ptr_32(); }
 
 // ---- host side -------------------------------------------------------------
 
@@ -244,7 +76,13 @@ namespace {
 template <int RI>
 cudaError_t batch_attr() {
     static unsigned done = 0;
-    return ensure_smem_attr(batch_kernel<RI>, batch_smem<RI>(), &done);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 32 && (done & (1u << dev))) return cudaSuccess;
+    e = cudaFuncSetAttribute(batch_kernel_ptr(RI), cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<RI>());
+    if (e == cudaSuccess && dev < 32) done |= 1u << dev;
+    return e;
 }
 
 cudaError_t batch_grid(int ri, int *grid) {
@@ -252,10 +90,8 @@ cudaError_t batch_grid(int ri, int *grid) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = ri == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<16>, kBThreads,
-                                                                     batch_smem<16>())
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<32>, kBThreads,
-                                                                     batch_smem<32>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel_ptr(ri), kBThreads,
+                                                          ri == 16 ? batch_smem<16>() : batch_smem<32>());
     if (e == cudaSuccess) *grid = sms * std::max(per, 1);
     return e;
 }
@@ -265,7 +101,7 @@ cudaError_t batch_grid(int ri, int *grid) {
 cudaError_t batch_graph(BatchState *b, int ri, const BatchArgs &args, int grid) {
     cudaKernelNodeParams kp{};
     void *kargs[] = {(void *)&args};
-    kp.func = ri == 16 ? (void *)batch_kernel<16> : (void *)batch_kernel<32>;
+    kp.func = (void *)batch_kernel_ptr(ri);
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(kBThreads);
     kp.sharedMemBytes = ri == 16 ? batch_smem<16>() : batch_smem<32>();

@@ -84,7 +84,6 @@ cudaError_t ensure_smem_attr(K *kernel, int bytes, unsigned *done) {
     return e;
 }
 
-// Launchers (return the launch error, if any).
 // Host-side check of the wavelet kind and its shape parameters (n_cycles
 // already checked > 0 and finite): Morlet/Gabor take sigma = n_cycles; the
 // generalized Morse wavelet takes beta = n_cycles <= 1000 and 0 < gamma <= 64.
@@ -97,6 +96,7 @@ inline bool wavelet_params_ok(int wavelet, const double *n_cycles, int n, double
     return true;
 }
 
+// Launchers (return the launch error, if any).
 cudaError_t launch_bank(cwt_plan_s *p, cudaStream_t st);
 // Bank and bands of the plan's scales for padded length N into the given
 // buffers ([S][N] floats, [S][2] ints); synchronises `st`.

@@ -2,50 +2,136 @@
 //
 // Section "Fast Fourier transform" of arXiv 2506.07793 pads each signal to the
 // smallest length whose prime factors are 2, 3, 5 and 7 (the fftpack radices)
-// rather than to a power of two.  This header runs such a row on one CTA of
-// 1024 threads:
-//  * N = 16^q * 2^e * 3^b * 5^c * 7^d is split into a runtime pass schedule of
-//    radices {16, 8, 4, 2, 3, 5, 7} (the power-of-two part first);
-//  * pass p (radix R, Ns = product of the earlier radices) has N/R butterflies;
-//    thread tid owns butterflies b = tid + i * 1024 and writes its outputs at
-//    (b - k) R + k + r Ns, k = b mod Ns.  Up to N = 13312 two padded shared
-//    buffers alternate (ping-pong) and a thread keeps one butterfly in
-//    registers at a time; above that one buffer is used and each thread holds
-//    all of a pass's inputs (at most 16 complex values) before writing;
-//  * twiddles exp(+-2 pi i r k / (Ns R)) come from a per-length FP64-generated
-//    table of the N-th roots of unity (index r k N / (Ns R));
-//  * odd radices use the symmetric form X[k], X[R-k] = A_k +- B_k with
-//    A_k = x0 + sum_r (x_r + x_{R-r}) cos(2 pi r k / R) and
-//    B_k = SIGN i sum_r (x_r - x_{R-r}) sin(2 pi r k / R).
+// rather than to a power of two.  This header runs such rows with the same
+// structure as the power-of-two kernels of fft_core.cuh:
+//
+//  * N = R_0 R_1 ... R_{P-1} with every radix a 7-smooth number in [4, 32]
+//    (a host-side cost model picks the factorisation and the order).  Pass p
+//    (radix R, Ns = R_0 ... R_{p-1}) has N/R butterflies; butterfly b takes
+//    the inputs b + r N/R, multiplies input r by w^r, w = exp(+-2 pi i k/(Ns R))
+//    with k = b mod Ns, runs an R-point DFT and writes output r to
+//    (b - k) R + k + r Ns (self-sorting, natural order after the last pass).
+//  * A row has T threads; in pass p thread j runs the butterflies j + g T,
+//    g < G_p = ceil(N / (R T)), holding all of its R G_p <= 32 values in
+//    registers, so each pass is one read of the row's shared-memory
+//    buffer, a barrier, and one write (a single buffer of N + N/16 float2).
+//  * Several rows share a CTA when T is small (short signals).
+//  * The first pass reads through a caller functor (global memory, fused
+//    spectrum product); the last pass leaves the row in natural order in the
+//    buffer, and the caller's epilogue streams it out with a rolled,
+//    coalesced loop (fused reduction and stores).  When every first-pass
+//    butterfly meets at most one nonzero input (a narrow band) its DFT is a
+//    twiddle chain.
+//  * Composite radices are nested Cooley-Tukey DFTs in registers whose
+//    internal twiddles are compile-time constants; prime radices 3, 5, 7 use
+//    the symmetric form X[k], X[R-k] = A_k +- B_k.
+//  * b mod Ns uses a multiply-high by ceil(2^32 / Ns): for b < 2^14 and
+//    Ns <= 2^13 the quotient is exact (division by invariant integers,
+//    Granlund and Montgomery 1994).
+//  * Pass twiddles w = exp(+-2 pi i k / (Ns R)) are entry k N/(Ns R) of a
+//    per-length FP64-generated table of the N-th roots of unity; their powers
+//    come from a short multiplication chain.
 #pragma once
+
+#include <utility>
 
 #include "fft_core.cuh"
 
 namespace cwtk {
 
-constexpr int kMrThreads = 1024;   // single-buffer mode
-constexpr int kMrThreadsPP = 512;  // ping-pong mode (one butterfly live per thread)
-constexpr int kMrPoints = 16;      // complex values per thread per pass (single-buffer mode)
-constexpr int kMrMaxPasses = 16;
+constexpr int kMrThreads = 512;   // largest CTA (the register budget of 32 values per thread)
+constexpr int kMrPoints = 32;     // complex values per thread per pass
+constexpr int kMrMaxPasses = 14;
 
-struct MrSchedule {
-    int np;
-    int radix[kMrMaxPasses];
+struct MrPass {
+    int R;          // radix
+    int G;          // butterflies per thread, <= kMrPoints / R
+    int Ns;         // product of the earlier radices
+    unsigned mag;   // ceil(2^32 / Ns) (0 when Ns == 1)
+    int tws;        // N / (Ns R): twiddle-table stride
 };
 
-// cos / sin (2 pi m / R) for the odd radices, m = 1..(R-1)/2 (mathematical constants).
-__host__ __device__ constexpr float odd_cos(int R, int m) {
-    return R == 3 ? -0.5f
-         : R == 5 ? (m == 1 ? 0.309016994374947424102f : -0.809016994374947424102f)
-         : (m == 1 ? 0.623489801858733530525f : m == 2 ? -0.222520933956314404289f
-                                                          : -0.900968867902419126236f);
+struct MrSchedule {
+    int N;           // row length
+    int T;           // threads per row
+    int rows;        // rows per CTA
+    int np;          // passes
+    unsigned mag0;   // ceil(2^32 / (N / R_0)), for the sparse first pass
+    MrPass p[kMrMaxPasses];
+};
+
+// ---- compile-time cos / sin (2 pi m / R): Taylor series after reduction to
+// |x| <= pi/4 (octant symmetries with exact integer arithmetic) -------------
+__host__ __device__ constexpr double ct_sin_red(double x) {
+    double x2 = x * x, term = x, sum = x;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x2 / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += term;
+    }
+    return sum;
 }
-__host__ __device__ constexpr float odd_sin(int R, int m) {
-    return R == 3 ? 0.866025403784438646764f
-         : R == 5 ? (m == 1 ? 0.951056516295153572116f : 0.587785252292473129169f)
-         : (m == 1 ? 0.781831482468029808708f : m == 2 ? 0.974927912181823607018f
-                                                          : 0.433883739117558120475f);
+__host__ __device__ constexpr double ct_cos_red(double x) {
+    double x2 = x * x, term = 1.0, sum = 1.0;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x2 / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += term;
+    }
+    return sum;
 }
+// cos and sin of phi = (pi/2) rem / R for 0 <= rem < R
+__host__ __device__ constexpr double ct_cos_q(int rem, int R) {
+    constexpr double kHalfPi = 1.57079632679489661923;
+    return 2 * rem <= R ? ct_cos_red(kHalfPi * rem / R) : ct_sin_red(kHalfPi * (R - rem) / R);
+}
+__host__ __device__ constexpr double ct_sin_q(int rem, int R) {
+    constexpr double kHalfPi = 1.57079632679489661923;
+    return 2 * rem <= R ? ct_sin_red(kHalfPi * rem / R) : ct_cos_red(kHalfPi * (R - rem) / R);
+}
+__host__ __device__ constexpr double ct_cos2pi(int m, int R) {
+    const int mm = ((m % R) + R) % R;
+    const int q = (4 * mm) / R, rem = 4 * mm - q * R;
+    const double c = ct_cos_q(rem, R), s = ct_sin_q(rem, R);
+    return q == 0 ? c : q == 1 ? -s : q == 2 ? -c : s;
+}
+__host__ __device__ constexpr double ct_sin2pi(int m, int R) {
+    const int mm = ((m % R) + R) % R;
+    const int q = (4 * mm) / R, rem = 4 * mm - q * R;
+    const double c = ct_cos_q(rem, R), s = ct_sin_q(rem, R);
+    return q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
+}
+
+// a * exp(SIGN 2 pi i M / R), M a compile-time constant.
+template <int R, int SIGN, int M>
+__device__ __forceinline__ float2 rot_c(float2 a) {
+    constexpr int m = ((M % R) + R) % R;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (2 * m == R) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (4 * m == R) {
+        return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    } else if constexpr (4 * m == 3 * R) {
+        return SIGN > 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    } else {
+        constexpr float c = (float)ct_cos2pi(m, R);
+        constexpr float s = (float)(SIGN > 0 ? ct_sin2pi(m, R) : -ct_sin2pi(m, R));
+        return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+    }
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I < N.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// cos / sin (2 pi m / R) for the odd primes, m = 1..(R-1)/2.
+__host__ __device__ constexpr float odd_cos(int R, int m) { return (float)ct_cos2pi(m, R); }
+__host__ __device__ constexpr float odd_sin(int R, int m) { return (float)ct_sin2pi(m, R); }
 
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_odd(float2 *v) {
@@ -60,167 +146,272 @@ __device__ __forceinline__ void dft_odd(float2 *v) {
     out[0] = v[0];
 #pragma unroll
     for (int r = 0; r < H; ++r) out[0] = cadd(out[0], s[r]);
-#pragma unroll
-    for (int k = 1; k <= H; ++k) {
+    static_for<H>([&](auto kc) {
+        constexpr int k = decltype(kc)::value + 1;
         float2 a = v[0], b = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int r = 1; r <= H; ++r) {
-            const int m = (r * k) % R;                    // 1..R-1
-            const int mm = m <= H ? m : R - m;            // cos is even, sin odd about R/2
-            const float c = odd_cos(R, mm);
-            const float sn = (m <= H ? 1.f : -1.f) * (SIGN > 0 ? 1.f : -1.f) * odd_sin(R, mm);
+        static_for<H>([&](auto rc) {
+            constexpr int r = decltype(rc)::value + 1;
+            constexpr int m = (r * k) % R;              // 1..R-1
+            constexpr int mm = m <= H ? m : R - m;      // cos even, sin odd about R/2
+            constexpr float c = odd_cos(R, mm);
+            constexpr float sn = (m <= H ? 1.f : -1.f) * (SIGN > 0 ? 1.f : -1.f) * odd_sin(R, mm);
             a.x = fmaf(s[r - 1].x, c, a.x);
             a.y = fmaf(s[r - 1].y, c, a.y);
-            b.x = fmaf(-d[r - 1].y, sn, b.x);             // i * d * sn
+            b.x = fmaf(-d[r - 1].y, sn, b.x);           // i * d * sn
             b.y = fmaf(d[r - 1].x, sn, b.y);
-        }
+        });
         out[k] = cadd(a, b);
         out[R - k] = csub(a, b);
-    }
+    });
 #pragma unroll
     for (int i = 0; i < R; ++i) v[i] = out[i];
 }
 
+__host__ __device__ constexpr bool is_pow2c(int r) { return r > 0 && (r & (r - 1)) == 0; }
+__host__ __device__ constexpr int low_pow2(int r) { return r & (-r); }
+__host__ __device__ constexpr int small_prime(int r) { return r % 3 == 0 ? 3 : r % 5 == 0 ? 5 : 7; }
+// First factor of a composite radix: its power-of-two part, else its smallest prime.
+__host__ __device__ constexpr int first_factor(int r) { return (r & 1) == 0 ? low_pow2(r) : small_prime(r); }
+
+// X[k] = sum_n v[n] exp(SIGN 2 pi i k n / R), natural order, in registers.
 template <int R, int SIGN>
-__device__ __forceinline__ void dft_any(float2 *v) {
-    if constexpr ((R & (R - 1)) == 0)
-        dft<R, SIGN>(v);
-    else
-        dft_odd<R, SIGN>(v);
+__device__ __forceinline__ void dft_r(float2 *v);
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_composite(float2 *v) {
+    constexpr int R1 = first_factor(R), R2 = R / R1;
+    // n = R2 n1 + n2, k = k1 + R1 k2:
+    //   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 x[R2 n1 + n2] w_R1^(n1 k1)
+    float2 t[R];
+    static_for<R2>([&](auto n2c) {
+        constexpr int n2 = decltype(n2c)::value;
+        float2 a[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[R2 * n1 + n2];
+        dft_r<R1, SIGN>(a);
+        static_for<R1>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            t[n2 * R1 + k1] = rot_c<R, SIGN, n2 * k1>(a[k1]);
+        });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 b[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) b[n2] = t[n2 * R1 + k1];
+        dft_r<R2, SIGN>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+    }
 }
 
-// v[r] *= w^r, r = 1..R-1 (power-of-two R: square-and-multiply chain).
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_r(float2 *v) {
+    if constexpr (R == 1) {
+        return;
+    } else if constexpr (is_pow2c(R)) {
+        dft<R, SIGN>(v);
+    } else if constexpr (R == 3 || R == 5 || R == 7) {
+        dft_odd<R, SIGN>(v);
+    } else {
+        dft_composite<R, SIGN>(v);
+    }
+}
+
+// v[r] *= w1^r, r = 1..R-1: w1^1..w1^7 by a square-and-multiply chain, higher
+// powers as w1^(8h) w1^(r mod 8).
 template <int R>
 __device__ __forceinline__ void mr_twiddle(float2 *v, float2 w1) {
-    if constexpr ((R & (R - 1)) == 0) {
+    if constexpr (is_pow2c(R)) {
         twiddle_chain<R>(v, w1);
     } else {
-        float2 w = w1;  // R <= 7: at most 5 successive products
+        constexpr int LO = R < 8 ? R : 8;
+        float2 wl[LO];
+        wl[0] = make_float2(1.f, 0.f);
+        wl[1] = w1;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            v[r] = cmul(v[r], w);
-            if (r + 1 < R) w = cmul(w, w1);
+        for (int r = 2; r < LO; ++r) wl[r] = (r & 1) ? cmul(wl[r - 1], w1) : cmul(wl[r >> 1], wl[r >> 1]);
+#pragma unroll
+        for (int r = 1; r < LO; ++r) v[r] = cmul(v[r], wl[r]);
+        if constexpr (R > 8) {
+            const float2 w8 = cmul(wl[4], wl[4]);
+            float2 wh = w8;
+#pragma unroll
+            for (int h = 1; 8 * h < R; ++h) {
+                v[8 * h] = cmul(v[8 * h], wh);
+#pragma unroll
+                for (int l = 1; l < 8; ++l)
+                    if (8 * h + l < R) v[8 * h + l] = cmul(cmul(v[8 * h + l], wh), wl[l]);
+                if (8 * (h + 1) < R) wh = cmul(wh, w8);
+            }
         }
     }
 }
 
-// One pass of radix R.  `first`: inputs come from load(k) instead of the
-// buffer; `last`: outputs go to store(t, X[t]) instead of the buffer.
-template <int R, int SIGN, typename Load, typename Store>
-__device__ __forceinline__ void mr_pass(float2 *__restrict__ sm, const float2 *__restrict__ twN,
-                                        int N, int Ns, bool first, bool last, Load &load,
-                                        Store &store) {
-    constexpr int MB = kMrPoints / R > 0 ? kMrPoints / R : 1;
-    const int nb = N / R;
-    const int tid = threadIdx.x;
-    float2 v[MB][R];
-#pragma unroll
-    for (int i = 0; i < MB; ++i) {
-        const int b = tid + i * kMrThreads;
-        if (b < nb) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[i][r] = first ? load(b + r * nb) : sm[spad2(b + r * nb)];
-        }
-    }
-    __syncthreads();  // every input of this pass is in registers
-#pragma unroll
-    for (int i = 0; i < MB; ++i) {
-        const int b = tid + i * kMrThreads;
-        if (b < nb) {
-            const int k = b % Ns;
-            if (Ns > 1) {
-                float2 w1 = __ldg(&twN[k * (N / (Ns * R))]);
-                if (SIGN < 0) w1.y = -w1.y;
-                mr_twiddle<R>(v[i], w1);
-            }
-            dft_any<R, SIGN>(v[i]);
-            if (last) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) store(k + r * Ns, v[i][r]);
-            } else {
-                const int base = (b - k) * R + k;
-#pragma unroll
-                for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[i][r];
-            }
-        }
-    }
-    __syncthreads();  // outputs visible to the next pass
+// ---- passes -----------------------------------------------------------------
+// Butterflies per thread and pass: at most 32 values.
+template <int R>
+__host__ __device__ constexpr int mr_gmax() {
+    return kMrPoints / R >= 1 ? kMrPoints / R : 1;
 }
 
-// Ping-pong form of a pass: inputs from `src` (or `load`), outputs to `dst`
-// (or `store`); each thread handles its butterflies one at a time, so only R
-// values are live.  Needs two buffers (N <= kMrPingPongMax).
-template <int R, int SIGN, typename Load, typename Store>
-__device__ __forceinline__ void mr_pass_pp(const float2 *__restrict__ src, float2 *__restrict__ dst,
-                                           const float2 *__restrict__ twN, int N, int Ns, bool first,
-                                           bool last, Load &load, Store &store) {
+// Butterfly b of pass (R, Ns): twiddle its inputs, DFT, and return k = b mod Ns
+// and q = b / Ns.
+template <int R, int SIGN>
+__device__ __forceinline__ void mr_butterfly(float2 *v, const MrPass &ps, const float2 *__restrict__ twN,
+                                             int b, int &q, int &k) {
+    q = (int)__umulhi((unsigned)b, ps.mag);
+    k = b - q * ps.Ns;
+    float2 w1 = __ldg(&twN[k * ps.tws]);
+    if (SIGN < 0) w1.y = -w1.y;
+    mr_twiddle<R>(v, w1);
+    dft_r<R, SIGN>(v);
+}
+
+// Pass 0 (Ns = 1): inputs from load(k), outputs to the row's buffer.  The
+// dense and sparse forms hold no barrier: rows of one CTA (even of one warp)
+// may take different forms, and mr_row places the barrier after either.
+template <int R, int SIGN, typename Load>
+__device__ __noinline__ void mr_first(const MrPass ps, float2 *__restrict__ sm, int N, int T, int j,
+                                      bool active, Load load) {
+    constexpr int GM = mr_gmax<R>();
     const int nb = N / R;
-#pragma unroll 1
-    for (int b = threadIdx.x; b < nb; b += kMrThreadsPP) {
-        float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = first ? load(b + r * nb) : src[spad2(b + r * nb)];
-        const int k = b % Ns;
-        if (Ns > 1) {
-            float2 w1 = __ldg(&twN[k * (N / (Ns * R))]);
-            if (SIGN < 0) w1.y = -w1.y;
-            mr_twiddle<R>(v, w1);
+    for (int g = 0; g < GM; ++g) {
+        const int b = j + g * T;
+        if (g < ps.G && active && b < nb) {
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = load(b + r * nb);
+            dft_r<R, SIGN>(v);
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[spad2(b * R + r)] = v[r];
         }
-        dft_any<R, SIGN>(v);
-        if (last) {
+    }
+}
+
+// Pass 0 when each butterfly meets at most one nonzero input:
+// first_nz(b, nb, mag0, r, x) gives its position r and value x; the R-point
+// DFT is then x exp(SIGN 2 pi i r t / R), t < R.
+template <int R, int SIGN, typename First>
+__device__ __noinline__ void mr_first_sparse(const MrPass ps, float2 *__restrict__ sm,
+                                             const float2 *__restrict__ twN, int N, int T, int j,
+                                             bool active, unsigned mag0, First first_nz) {
+    constexpr int GM = mr_gmax<R>();
+    const int nb = N / R;
 #pragma unroll
-            for (int r = 0; r < R; ++r) store(k + r * Ns, v[r]);
-        } else {
-            const int base = (b - k) * R + k;
+    for (int g = 0; g < GM; ++g) {
+        const int b = j + g * T;
+        if (g < ps.G && active && b < nb) {
+            int r = 0;
+            float2 x = make_float2(0.f, 0.f);
+            const bool nz = first_nz(b, nb, mag0, r, x);
+            float2 w = __ldg(&twN[r * nb]);  // exp(+2 pi i r / R)
+            if (SIGN < 0) w.y = -w.y;
+            if (!nz) x = make_float2(0.f, 0.f);
+            float2 v[R];
 #pragma unroll
-            for (int r = 0; r < R; ++r) dst[spad2(base + r * Ns)] = v[r];
+            for (int t = 0; t < R; ++t) v[t] = x;
+            mr_twiddle<R>(v, w);
+#pragma unroll
+            for (int t = 0; t < R; ++t) sm[spad2(b * R + t)] = v[t];
+        }
+    }
+}
+
+// A middle pass: buffer -> registers, barrier, butterflies -> buffer.
+template <int R, int SIGN>
+__device__ __noinline__ void mr_mid(const MrPass ps, float2 *__restrict__ sm, const float2 *__restrict__ twN,
+                                    int N, int T, int j, bool active) {
+    constexpr int GM = mr_gmax<R>();
+    const int nb = N / R;
+    float2 v[GM][R];
+#pragma unroll
+    for (int g = 0; g < GM; ++g) {
+        const int b = j + g * T;
+        if (g < ps.G && active && b < nb) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[g][r] = sm[spad2(b + r * nb)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < GM; ++g) {
+        const int b = j + g * T;
+        if (g < ps.G && active && b < nb) {
+            int q, k;
+            mr_butterfly<R, SIGN>(v[g], ps, twN, b, q, k);
+            const int base = q * ps.Ns * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sm[spad2(base + r * ps.Ns)] = v[g][r];
         }
     }
     __syncthreads();
 }
 
-// Largest N whose two padded buffers fit one CTA's shared memory.
-constexpr int kMrPingPongMax = 13312;
+// Threads of a CTA: `rows` rows of T threads; thread (rr, j) works on row
+// blockIdx.x * rows + rr.
+struct RowSlot {
+    int rr, j;
+    bool active;
+};
+__device__ __forceinline__ RowSlot row_slot(const MrSchedule &sch, int rows, int total_rows) {
+    RowSlot s;
+    s.rr = (int)threadIdx.x / sch.T;
+    s.j = (int)threadIdx.x - s.rr * sch.T;
+    s.active = s.rr < rows && (int)blockIdx.x * rows + s.rr < total_rows;
+    return s;
+}
 
-// The whole row: passes from the schedule, first reading `load`, last writing
-// `store`.  One row per CTA of kMrThreadsPP (PP) or kMrThreads threads.  PP: `sm` holds two
-// buffers of spad2(N) slots each (N <= kMrPingPongMax); otherwise one buffer
-// and each pass keeps all of a thread's inputs in registers.
-template <int SIGN, bool PP, typename Load, typename Store>
-__device__ __forceinline__ void mr_row(float2 *__restrict__ sm, const float2 *__restrict__ twN, int N,
-                                       const MrSchedule &sch, Load &load, Store &store) {
-    int Ns = 1;
-    float2 *src = sm, *dst = sm + (N + (N >> 4));
-#pragma unroll 1
-    for (int p = 0; p < sch.np; ++p) {
-        const bool first = p == 0, last = p == sch.np - 1;
-        if constexpr (PP) {
-            switch (sch.radix[p]) {
-                case 16: mr_pass_pp<16, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 8: mr_pass_pp<8, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 4: mr_pass_pp<4, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 2: mr_pass_pp<2, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 3: mr_pass_pp<3, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 5: mr_pass_pp<5, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
-                case 7: mr_pass_pp<7, SIGN>(src, dst, twN, N, Ns, first, last, load, store); break;
+#ifndef CWT_MR_RADICES
+#define CWT_MR_RADICES(X) \
+    X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(18) X(20) X(21) X(24) X(25) X(27) X(28) X(30) X(32)
+#endif
+
+// The whole row (at least two passes).  `sm` is this row's buffer of
+// N + N/16 float2; on return it holds X[t] at spad2(t) (natural order) for
+// every active row, after a barrier, for the caller's epilogue.  All threads
+// of the CTA call it together.  Each pass of each radix is a separate (not
+// inlined) function with its own register allocation, and the last pass is
+// an ordinary buffer-to-buffer pass, so a schedule that repeats a radix
+// (10000 = 16 x 25 x 25) runs the same code twice; the functors are passed
+// by value and must capture by value.
+template <int SIGN, typename Load, typename First>
+__device__ __forceinline__ void mr_row(const MrSchedule &sch, float2 *__restrict__ sm,
+                                       const float2 *__restrict__ twN, int j, bool active,
+                                       bool sparse, const Load &load, const First &first_nz) {
+    const int N = sch.N, T = sch.T;
+    {
+        const MrPass ps = sch.p[0];
+        if (sparse) {
+            switch (ps.R) {
+#define CWT_MR_CASE(RR) \
+    case RR: mr_first_sparse<RR, SIGN>(ps, sm, twN, N, T, j, active, sch.mag0, first_nz); break;
+                CWT_MR_RADICES(CWT_MR_CASE)
+#undef CWT_MR_CASE
                 default: break;
             }
-            float2 *t = src;
-            src = dst;
-            dst = t;
         } else {
-            switch (sch.radix[p]) {
-                case 16: mr_pass<16, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 8: mr_pass<8, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 4: mr_pass<4, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 2: mr_pass<2, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 3: mr_pass<3, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 5: mr_pass<5, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
-                case 7: mr_pass<7, SIGN>(sm, twN, N, Ns, first, last, load, store); break;
+            switch (ps.R) {
+#define CWT_MR_CASE(RR) \
+    case RR: mr_first<RR, SIGN>(ps, sm, N, T, j, active, load); break;
+                CWT_MR_RADICES(CWT_MR_CASE)
+#undef CWT_MR_CASE
                 default: break;
             }
         }
-        Ns *= sch.radix[p];
+        __syncthreads();  // pass-0 outputs visible; every thread arrives here
+    }
+#pragma unroll 1
+    for (int p = 1; p < sch.np; ++p) {
+        const MrPass ps = sch.p[p];
+        switch (ps.R) {
+#define CWT_MR_CASE(RR) \
+    case RR: mr_mid<RR, SIGN>(ps, sm, twN, N, T, j, active); break;
+            CWT_MR_RADICES(CWT_MR_CASE)
+#undef CWT_MR_CASE
+            default: break;
+        }
     }
 }
 

@@ -1,9 +1,13 @@
-// smooth.cu -- forward FFT and fused scale block for 2,3,5,7-smooth padded
+// smooth.cu -- fused scale block for 2,3,5,7-smooth padded
 // lengths (the padding policy of Section "Fast Fourier transform" of arXiv
-// 2506.07793), one row per CTA (mixed_radix.cuh).  The
-// arithmetic per row is that of fft_kernels.cu and scale_block.cu (Eq. 2);
-// only the FFT length and its radices differ.
+// 2506.07793), on the mixed-radix rows of mixed_radix.cuh.  The arithmetic
+// per row is that of fft_kernels.cu and scale_block.cu (Eq. 2); only the FFT
+// length and its radices differ.  The host side picks each length's radix
+// schedule with a cost model.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "internal.h"
 #include "mixed_radix.cuh"
@@ -21,27 +25,9 @@ __global__ void twiddle_n_kernel(float2 *tw, int N) {
     }
 }
 
-template <typename IO, bool PP>
-__global__ void __launch_bounds__(PP ? kMrThreadsPP : kMrThreads, 1)
-mr_forward_kernel(const IO *__restrict__ x, int n, int N, float2 *__restrict__ spec,
-                  const float2 *__restrict__ twN, const MrSchedule sch) {
-    extern __shared__ float2 mrsm[];
-    const int row = blockIdx.x;
-    const IO *xr = x + (size_t)row * n;
-    float2 *out = spec + (size_t)row * N;
-    auto load = [&](int i) -> float2 { return make_float2(i < n ? (float)xr[i] : 0.f, 0.f); };
-    auto store = [&](int t, float2 v) { out[t] = v; };
-    mr_row<-1, PP>(mrsm, twN, N, sch, load, store);
-}
-
-template <typename IO> struct IO2m;
-template <> struct IO2m<float> { using type = float2; };
-template <> struct IO2m<double> { using type = double2; };
-
 __device__ __noinline__ void mr_phase_f(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
 __device__ __noinline__ void mr_phase_d(double *dst, float2 v) { *dst = (double)atan2f(v.y, v.x); }
-__device__ __forceinline__ void mr_phase(float *dst, float2 v) { mr_phase_f(dst, v); }
-__device__ __forceinline__ void mr_phase(double *dst, float2 v) { mr_phase_d(dst, v); }
+
 
 struct MrArgs {
     const float2 *spec;
@@ -49,22 +35,24 @@ struct MrArgs {
     const int *band;
     const float2 *twN;
     void *out_c, *out_p, *out_ph;
-    int S, N, n_out, sub;
+    int S, n_out, sub, total_rows, f64;
 };
 
-template <typename IO, bool PP>
-__global__ void __launch_bounds__(PP ? kMrThreadsPP : kMrThreads, 1)
-mr_scale_block_kernel(const MrArgs a, const MrSchedule sch) {
-    using V2 = typename IO2m<IO>::type;
+// Fused spectrum product, inverse FFT and epilogue per (channel, scale) row.
+__global__ void __launch_bounds__(kMrThreads, 1)
+mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
     extern __shared__ float2 mrsm[];
-    const int row = blockIdx.x;
+    const int N = sch.N;
+    const RowSlot rs = row_slot(sch, rows, a.total_rows);
+    const int row = rs.active ? (int)blockIdx.x * rows + rs.rr : 0;
+    const int rr = rs.rr < rows ? rs.rr : 0;
+    float2 *sm = mrsm + (size_t)rr * (N + (N >> 4));
     const int c = row / a.S, s = row - c * a.S;
-    const int N = a.N;
     const float2 *X = a.spec + (size_t)c * N;
     const float *W = a.bank + (size_t)s * N;
     const int b0 = a.band[2 * s], B = a.band[2 * s + 1];
-    auto load = [&](int k) -> float2 {
-        int dk = k - b0;  // band is [b0, b0 + B) modulo N
+    auto load = [=](int k) -> float2 {
+        int dk = k - b0;  // the band is [b0, b0 + B) modulo N
         if (dk < 0) dk += N;
         if (dk < B) {
             const float2 xv = X[k];
@@ -73,80 +61,184 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch) {
         }
         return make_float2(0.f, 0.f);
     };
-    const size_t obase = (size_t)row * (size_t)a.n_out;
-    V2 *oc = (V2 *)a.out_c;
-    IO *op = (IO *)a.out_p;
-    IO *oph = (IO *)a.out_ph;
-    const int sub = a.sub, n_out = a.n_out;
-    auto store = [&](int t, float2 v) {
-        int o = t;
-        if (sub != 1) {
-            if (t % sub) return;
-            o = t / sub;
-        }
-        if (o >= n_out) return;
-        if (oc) {
-            V2 z;
-            z.x = (IO)v.x;
-            z.y = (IO)v.y;
-            oc[obase + o] = z;
-        }
-        if (op) op[obase + o] = (IO)fmaf(v.x, v.x, v.y * v.y);
-        if (oph) mr_phase(oph + obase + o, v);
+    // Narrow band (B <= N/R_0): butterfly b's inputs b + r nb, r < R_0, meet
+    // the band at most once, at e = b0 + u (mod N) with u = (b - b0) mod nb.
+    auto first_nz = [=](int b, int nb, unsigned mag, int &r, float2 &x) -> bool {
+        const unsigned d = (unsigned)(b - b0 + N);  // > 0; N is a multiple of nb
+        const int u = (int)(d - __umulhi(d, mag) * (unsigned)nb);
+        if (u >= B) return false;
+        int e = b0 + u;
+        if (e >= N) e -= N;
+        r = (int)__umulhi((unsigned)(e - b), mag);  // (e - b) / nb, exact: e = b (mod nb), e >= b
+        const float2 xv = X[e];
+        const float w = W[e];
+        x = make_float2(xv.x * w, xv.y * w);
+        return true;
     };
-    mr_row<+1, PP>(mrsm, a.twN, N, sch, load, store);
+    const bool sparse = B <= N / sch.p[0].R;
+    mr_row<+1>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
+    if (!rs.active) return;
+    // epilogue: crop to t < n, keep t = sub * o, write the requested outputs
+    // (consecutive threads take consecutive o: coalesced stores)
+    const size_t obase = (size_t)row * (size_t)a.n_out;
+    const int sub = a.sub, n_out = a.n_out;
+    if (a.f64) {
+        double2 *oc = (double2 *)a.out_c + obase;
+        double *op = (double *)a.out_p + obase, *oph = (double *)a.out_ph + obase;
+#pragma unroll 1
+        for (int o = rs.j; o < n_out; o += sch.T) {
+            const float2 v = sm[spad2(o * sub)];
+            if (a.out_c) oc[o] = make_double2(v.x, v.y);
+            if (a.out_p) op[o] = (double)fmaf(v.x, v.x, v.y * v.y);
+            if (a.out_ph) mr_phase_d(oph + o, v);
+        }
+    } else {
+        float2 *oc = (float2 *)a.out_c + obase;
+        float *op = (float *)a.out_p + obase, *oph = (float *)a.out_ph + obase;
+#pragma unroll 2
+        for (int o = rs.j; o < n_out; o += sch.T) {
+            const float2 v = sm[spad2(o * sub)];
+            if (a.out_c) oc[o] = v;
+            if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
+            if (a.out_ph) mr_phase_f(oph + o, v);
+        }
+    }
 }
 
-size_t mr_smem(int N) {
-    return sizeof(float2) * (size_t)(N + (N >> 4)) * (N <= kMrPingPongMax ? 2 : 1);
+// ---- host: schedule ------------------------------------------------------
+
+constexpr int kRadixSet[] = {4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32};
+
+// Relative cost of one radix-R DFT (FP32 operations): radix-2 stages for
+// powers of two, the symmetric form for 3, 5, 7, and for composite radices
+// their nested factors plus the internal twiddle products.
+double dft_cost(int R) {
+    switch (R) {
+        case 1: return 0.0;
+        case 2: return 4.0;
+        case 3: return 12.0;
+        case 4: return 16.0;
+        case 5: return 34.0;
+        case 7: return 66.0;
+        case 8: return 52.0;
+        case 16: return 144.0;
+        case 32: return 376.0;
+        default: break;
+    }
+    const int R1 = first_factor(R), R2 = R / R1;
+    return R2 * dft_cost(R1) + R1 * dft_cost(R2) + 6.0 * (R1 - 1) * (R2 - 1);
+}
+// One butterfly of a pass: the DFT, R - 1 twiddle products, staging R values in and out.
+double butterfly_cost(int R) { return dft_cost(R) + 6.0 * (R - 1) + 8.0 * R; }
+constexpr double kPassOverhead = 24.0;  // per thread and pass: barriers, loop, index math
+
+void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vector<int>> &out) {
+    if (rem == 1) {
+        out.push_back(cur);
+        return;
+    }
+    if ((int)cur.size() >= kMrMaxPasses) return;
+    for (int R : kRadixSet) {
+        if (R < min_r || rem % R) continue;
+        cur.push_back(R);
+        enumerate(rem / R, R, cur, out);
+        cur.pop_back();
+    }
 }
 
-template <typename K>
-cudaError_t mr_attr(K *kernel, unsigned *done) {
-    return ensure_smem_attr(kernel, (int)mr_smem(kMrPingPongMax), done);
+unsigned magic_of(int d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d); }
+
+int g_sm_count[64] = {};
+
+int sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!g_sm_count[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        g_sm_count[dev] = v;
+    }
+    return g_sm_count[dev];
 }
 
-template <typename IO, bool PP>
-cudaError_t mr_forward_t(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+constexpr int kMrRowSmemCap = 96 * 1024;          // several rows per CTA: at most this much
+constexpr int kMrMaxSmem = (kMaxFft + (kMaxFft >> 4)) * 8;
+
+// Rows per CTA for a launch over total_rows rows: up to 256 threads per CTA
+// for short rows, but at least two CTAs per SM when there are enough rows.
+int launch_rows(const MrSchedule &sch, int total_rows) {
+    int rows = std::max(1, std::min(256, kMrThreads) / sch.T);
+    const int want = (total_rows + 2 * sm_count() - 1) / (2 * sm_count());
+    rows = std::max(1, std::min(rows, want));
+    const int per_row = (sch.N + (sch.N >> 4)) * 8;
+    while (rows > 1 && rows * per_row > kMrRowSmemCap) --rows;
+    return rows;
+}
+
+int round_up32(int x) { return (x + 31) & ~31; }
+
+cudaError_t mr_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
     static unsigned done = 0;
-    cudaError_t e = mr_attr(mr_forward_kernel<IO, PP>, &done);
+    cudaError_t e = ensure_smem_attr(mr_scale_block_kernel, kMrMaxSmem, &done);
     if (e != cudaSuccess) return e;
-    mr_forward_kernel<IO, PP><<<p->C, PP ? kMrThreadsPP : kMrThreads, mr_smem(p->N), st>>>(
-        (const IO *)signal, p->n, p->N, p->spec, p->twN, p->sch);
-    return cudaGetLastError();
-}
-
-template <typename IO, bool PP>
-cudaError_t mr_sb_t(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
-    static unsigned done = 0;
-    cudaError_t e = mr_attr(mr_scale_block_kernel<IO, PP>, &done);
-    if (e != cudaSuccess) return e;
-    mr_scale_block_kernel<IO, PP><<<p->C * p->S, PP ? kMrThreadsPP : kMrThreads, mr_smem(p->N), st>>>(a, p->sch);
+    const int rows = launch_rows(p->sch, a.total_rows);
+    const int smem = rows * (p->N + (p->N >> 4)) * 8;
+    mr_scale_block_kernel<<<(a.total_rows + rows - 1) / rows, round_up32(rows * p->sch.T), smem, st>>>(
+        a, p->sch, rows);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+int mr_launch_rows(const MrSchedule &sch, int total_rows) { return launch_rows(sch, total_rows); }
+
 bool mr_schedule(int N, MrSchedule *out) {
-    int x = N, e2 = 0, e3 = 0, e5 = 0, e7 = 0;
-    while (x % 2 == 0) x /= 2, ++e2;
-    while (x % 3 == 0) x /= 3, ++e3;
-    while (x % 5 == 0) x /= 5, ++e5;
-    while (x % 7 == 0) x /= 7, ++e7;
-    if (x != 1 || N < kMinFft || N > kMaxFft) return false;
-    MrSchedule s{};
-    while (e2 >= 4 && s.np < kMrMaxPasses) s.radix[s.np++] = 16, e2 -= 4;
-    if (e2 && s.np < kMrMaxPasses) s.radix[s.np++] = 1 << e2;
-    for (int i = 0; i < e3 && s.np < kMrMaxPasses; ++i) s.radix[s.np++] = 3;
-    for (int i = 0; i < e5 && s.np < kMrMaxPasses; ++i) s.radix[s.np++] = 5;
-    for (int i = 0; i < e7 && s.np < kMrMaxPasses; ++i) s.radix[s.np++] = 7;
-    // each thread holds at most kMrPoints values: N / R butterflies must fit
-    // in (kMrPoints / R) per thread
-    for (int p = 0; p < s.np; ++p) {
-        const int R = s.radix[p];
-        const int per = kMrPoints / R > 0 ? kMrPoints / R : 1;
-        if (N / R > per * kMrThreads) return false;
+    if (N < kMinFft || N > kMaxFft) return false;
+    int x = N;
+    for (int f : {2, 3, 5, 7})
+        while (x % f == 0) x /= f;
+    if (x != 1) return false;
+    std::vector<std::vector<int>> cands;
+    std::vector<int> cur;
+    enumerate(N, 2, cur, cands);
+    double best = 0.0;
+    int best_i = -1, best_T = 0;
+    for (int i = 0; i < (int)cands.size(); ++i) {
+        const std::vector<int> &rs = cands[i];
+        int Tmin = 1;
+        for (int R : rs) {
+            const int gm = std::max(1, kMrPoints / R);  // mr_gmax
+            Tmin = std::max(Tmin, (N / R + gm - 1) / gm);
+        }
+        for (int T = Tmin; T <= kMrThreads; ++T) {
+            double c = kPassOverhead * (double)rs.size();
+            for (int R : rs) c += (double)((N / R + T - 1) / T) * butterfly_cost(R);
+            c *= T;
+            if (best_i < 0 || c < best * (1.0 - 1e-9) ||
+                (c <= best * (1.0 + 1e-9) && rs.size() < cands[best_i].size())) {
+                best = c;
+                best_i = i;
+                best_T = T;
+            }
+        }
     }
+    if (best_i < 0) return false;
+    MrSchedule s{};
+    s.N = N;
+    s.T = best_T;
+    s.rows = 1;
+    s.np = (int)cands[best_i].size();
+    int Ns = 1;
+    for (int q = 0; q < s.np; ++q) {
+        const int R = cands[best_i][q];
+        s.p[q].R = R;
+        s.p[q].G = (N / R + best_T - 1) / best_T;
+        s.p[q].Ns = Ns;
+        s.p[q].mag = magic_of(Ns);
+        s.p[q].tws = N / (Ns * R);
+        Ns *= R;
+    }
+    s.mag0 = magic_of(N / s.p[0].R);
     *out = s;
     return true;
 }
@@ -154,13 +246,6 @@ bool mr_schedule(int N, MrSchedule *out) {
 cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st) {
     twiddle_n_kernel<<<(N + 255) / 256, 256, 0, st>>>(tw, N);
     return cudaGetLastError();
-}
-
-cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
-    const bool pp = p->N <= kMrPingPongMax;
-    if (p->io == CWT_DTYPE_F64)
-        return pp ? mr_forward_t<double, true>(p, signal, st) : mr_forward_t<double, false>(p, signal, st);
-    return pp ? mr_forward_t<float, true>(p, signal, st) : mr_forward_t<float, false>(p, signal, st);
 }
 
 cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
@@ -174,13 +259,11 @@ cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p,
     a.out_p = out_p;
     a.out_ph = out_ph;
     a.S = p->S;
-    a.N = p->N;
     a.n_out = p->n_out;
     a.sub = p->d;
-    const bool pp = p->N <= kMrPingPongMax;
-    if (p->io == CWT_DTYPE_F64)
-        return pp ? mr_sb_t<double, true>(p, a, st) : mr_sb_t<double, false>(p, a, st);
-    return pp ? mr_sb_t<float, true>(p, a, st) : mr_sb_t<float, false>(p, a, st);
+    a.total_rows = p->C * p->S;
+    a.f64 = p->io == CWT_DTYPE_F64;
+    return mr_sb_launch(p, a, st);
 }
 
 }  // namespace cwtk
