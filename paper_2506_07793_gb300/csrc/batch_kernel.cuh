@@ -9,6 +9,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "phase.cuh"
 
 namespace cwtk {
 
@@ -50,7 +51,7 @@ const void *batch_kernel_ptr(int ri);
 #ifdef CWT_BATCH_KERNELS
 namespace {
 
-__device__ __noinline__ void batch_store_phase(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
+__device__ __noinline__ void batch_store_phase(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
 
 template <int N>
 __device__ __noinline__ void batch_forward(const BatchArgs &a, const BatchItem &it,

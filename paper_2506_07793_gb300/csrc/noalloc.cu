@@ -19,6 +19,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "phase.cuh"
 
 namespace cwtk {
 namespace {
@@ -156,7 +157,7 @@ na_forward_kernel(const float *__restrict__ x, int C, int n, float2 *__restrict_
     fft_row<N, RC::R, -1>(sm, tw, j, load, store);
 }
 
-__device__ __noinline__ void na_store_phase(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
+__device__ __noinline__ void na_store_phase(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
 
 template <int N>
 __global__ void __launch_bounds__(RowConfig<N>::THREADS)

@@ -18,6 +18,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "phase.cuh"
 
 namespace cwtk {
 
@@ -36,11 +37,10 @@ template <typename IO> struct IO2;
 template <> struct IO2<float> { using type = float2; };
 template <> struct IO2<double> { using type = double2; };
 
-// Phase is rare on the hot path; keeping atan2f out of line keeps the
-// unrolled epilogue small.
+// Keeping the phase out of line keeps the unrolled epilogue small.
 template <typename IO>
 __device__ __noinline__ void store_phase(IO *dst, float2 v) {
-    *dst = (IO)atan2f(v.y, v.x);
+    *dst = (IO)phase_atan2(v.y, v.x);
 }
 
 template <int M, typename IO>

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "phase.cuh"
 #include "mixed_radix.cuh"
 
 namespace cwtk {
@@ -25,8 +26,8 @@ __global__ void twiddle_n_kernel(float2 *tw, int N) {
     }
 }
 
-__device__ __noinline__ void mr_phase_f(float *dst, float2 v) { *dst = atan2f(v.y, v.x); }
-__device__ __noinline__ void mr_phase_d(double *dst, float2 v) { *dst = (double)atan2f(v.y, v.x); }
+__device__ __noinline__ void mr_phase_f(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
+__device__ __noinline__ void mr_phase_d(double *dst, float2 v) { *dst = (double)phase_atan2(v.y, v.x); }
 
 
 struct MrArgs {
