@@ -217,9 +217,13 @@ cwt_status cwt_execute(cwt_plan plan, const void *d_signal, void *d_complex, voi
 
 /*
  * cwt_execute_host -- the same transform with HOST buffers: copies the signal
- * to the plan's device staging buffer, runs cwt_execute on `stream`, copies
- * the requested outputs back and waits for them.  Staging buffers are
- * allocated on the first call and kept by the plan.  Same layouts as
+ * to the plan's device staging buffer, runs cwt_execute on `stream` and waits
+ * for the outputs.  An output buffer in page-locked host memory that the
+ * device can address (cudaHostAlloc / cudaMallocHost, cudaHostRegister with
+ * mapping, e.g. torch pin_memory(); 16-byte aligned) is written directly by
+ * the kernels' epilogues over the host link, with no staging copy; any other
+ * output goes to a device staging buffer and is copied back.  Staging buffers
+ * are allocated on the first call and kept by the plan.  Same layouts as
  * cwt_execute.  Returns when the outputs are in host memory.
  */
 cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex, void *h_power,

@@ -316,6 +316,20 @@ cwt_status cwt_execute(cwt_plan p, const void *d_signal, void *d_complex, void *
     return run_execute(p, d_signal, d_complex, d_power, d_phase, (cudaStream_t)stream);
 }
 
+// Device address of page-locked host memory that the device can write
+// directly (cudaHostAlloc, cudaHostRegister with mapping), or nullptr.
+void *mapped_host_ptr(void *ptr) {
+    if (!ptr || (reinterpret_cast<uintptr_t>(ptr) & 15u)) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the non-sticky error
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    if (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) return nullptr;
+    return at.devicePointer;
+}
+
 cwt_status cwt_execute_host(cwt_plan p, const void *h_signal, void *h_complex, void *h_power,
                             void *h_phase, void *stream) {
     if (!p || !h_signal) return CWT_EINVAL;
@@ -347,12 +361,19 @@ cwt_status cwt_execute_host(cwt_plan p, const void *h_signal, void *h_complex, v
     cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemcpyAsync(p->stage_in, h_signal, in_b, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail_cuda(p, e);
-    cwt_status s = run_execute(p, p->stage_in, wc ? p->stage_c : nullptr, wp ? p->stage_p : nullptr,
-                               wph ? p->stage_ph : nullptr, st);
+    // outputs the device can address in host memory are written there by the
+    // kernels' epilogues (one pass over the host link); the rest are staged
+    void *mc = wc ? mapped_host_ptr(h_complex) : nullptr;
+    void *mp = wp ? mapped_host_ptr(h_power) : nullptr;
+    void *mph = wph ? mapped_host_ptr(h_phase) : nullptr;
+    cwt_status s = run_execute(p, p->stage_in, wc ? (mc ? mc : p->stage_c) : nullptr,
+                               wp ? (mp ? mp : p->stage_p) : nullptr,
+                               wph ? (mph ? mph : p->stage_ph) : nullptr, st);
     if (s != CWT_OK) return s;
-    if (wc) e = cudaMemcpyAsync(h_complex, p->stage_c, 2 * out_b, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && wp) e = cudaMemcpyAsync(h_power, p->stage_p, out_b, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && wph)
+    if (wc && !mc) e = cudaMemcpyAsync(h_complex, p->stage_c, 2 * out_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && wp && !mp)
+        e = cudaMemcpyAsync(h_power, p->stage_p, out_b, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && wph && !mph)
         e = cudaMemcpyAsync(h_phase, p->stage_ph, out_b, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);

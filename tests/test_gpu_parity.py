@@ -193,6 +193,35 @@ def test_host_buffers_match_device_path_and_repeat_bitwise(lib):
         lib.cwt_plan_destroy(plan)
 
 
+def test_pinned_host_outputs_written_directly_equal_device_path(lib):
+    """cwt_execute_host with page-locked, device-mapped outputs (written by the
+    kernels over the host link) and with a mix of pinned and pageable outputs:
+    bitwise equal to the device path."""
+    import torch
+    w = workload("fused")
+    C, n = 4, w.samples
+    x = np.ascontiguousarray(w.signal()[:C])
+    plan = lib.cwt_plan_create(C, n, w.fs, w.freqs, w.n_cycles, 0, lib.CWT_OUT_COMPLEX | lib.CWT_OUT_POWER)
+    try:
+        shape = (C, w.scales, n)
+        xt = torch.from_numpy(x).cuda()
+        dc = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        dp = torch.empty(shape, dtype=torch.float32, device="cuda")
+        lib.cwt_execute(plan, xt, dc, dp, None)
+        torch.cuda.synchronize()
+        ref_c, ref_p = dc.cpu().numpy(), dp.cpu().numpy()
+        hc = torch.empty(shape, dtype=torch.complex64).pin_memory()
+        hp = torch.empty(shape, dtype=torch.float32).pin_memory()
+        lib.cwt_execute_host(plan, torch.from_numpy(x).pin_memory(), hc, hp, None)
+        assert np.array_equal(hc.numpy(), ref_c) and np.array_equal(hp.numpy(), ref_p)
+        hp2 = np.empty(shape, np.float32)  # pageable: staged
+        hc.zero_()
+        lib.cwt_execute_host(plan, x, hc, hp2, None)
+        assert np.array_equal(hc.numpy(), ref_c) and np.array_equal(hp2, ref_p)
+    finally:
+        lib.cwt_plan_destroy(plan)
+
+
 def test_bad_pointers_rejected_on_host(lib):
     import torch
     plan = lib.cwt_plan_create(1, 100, 500.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER)
