@@ -87,6 +87,18 @@ typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
  * cwt_execute_batch does not take mixed-radix plans (CWT_EUNSUPPORTED). */
 typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
 
+/* Edge handling (Section "Fourier transformed formula": the FFT path gives a
+ * cyclic convolution, which approximates the simple convolution except near
+ * the edges).  CYCLIC: the cyclic result over N = pad_policy(samples), the
+ * paper's own computation.  LINEAR: the "same"-mode linear convolution of
+ * the signal with the wavelet, by padding to N = pad_policy(samples + R + 1),
+ * R = ceil(6.5 a fs) samples the support radius of the widest wavelet
+ * (a = n_cycles / (2 pi F); its Gaussian envelope is below 1e-9 of the peak
+ * beyond R), so that no wavelet wraps around; the result then equals the
+ * linear convolution on [0, samples) up to that envelope tail.  Morlet and
+ * Gabor only (CWT_EUNSUPPORTED for GMW, whose support has no closed form). */
+typedef enum { CWT_EDGE_CYCLIC = 0, CWT_EDGE_LINEAR = 1 } cwt_edge_mode;
+
 /* Kernel identifiers for the profiling counters. */
 typedef enum {
     CWT_KERNEL_BANK = 0,        /* wavelet-bank + band generation (plan creation) */
@@ -130,7 +142,7 @@ typedef struct {
                        length <= 16384 (see cwt_pad_policy) */
     int io_dtype;   /* cwt_dtype of the signal and of every output (default F32);
                        F64 is converted to FP32 on load and back on store */
-    int reserved0;
+    int edge_mode;  /* cwt_edge_mode (default CWT_EDGE_CYCLIC) */
     double gmw_gamma; /* gamma of the generalized Morse wavelet (Eq. 5), > 0,
                          default 3; read only for CWT_WAVELET_GMW */
     int reserved[8];
@@ -233,6 +245,7 @@ cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex
  * cwt_execute_batch -- many epochs of uneven length in one persistent launch
  * replayed from a CUDA graph.  Epoch e is the same transform as cwt_execute
  * on its own samples (padded length N_e = next power of two >= max(n_e, 32),
+ * or >= n_e + R + 1 with CWT_EDGE_LINEAR,
  * Section "Fast Fourier transform"), with the plan's channels, scales,
  * decimation and output kinds.  The paper loops over recordings in Python
  * (Section "Wavelength and flexibility"); here they share one launch.
@@ -243,7 +256,8 @@ cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex
  * for its lengths (allocating and waiting) and runs the autotuner, which times
  * four schedules on this batch and keeps the fastest; later batches of the
  * same shape only replay the graph.  Asynchronous on `stream` otherwise.
- * CWT_EUNSUPPORTED for F64 plans or epochs longer than 8192 samples.
+ * CWT_EUNSUPPORTED for F64 plans, smooth-padded plans, or epochs whose
+ * padded length would exceed 8192 samples.
  */
 cwt_status cwt_execute_batch(cwt_plan plan, const cwt_epoch *epochs, int n_epochs, const void *d_in,
                              void *d_complex, void *d_power, void *d_phase, void *stream);

@@ -6,6 +6,7 @@
 // are transformed there, and results leave the GPU only when asked for.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstddef>
@@ -18,6 +19,8 @@
 using cwtk::ilog2c;
 
 namespace {
+
+constexpr double kPi = 3.14159265358979323846;
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
@@ -195,9 +198,22 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         if (o.precision == CWT_PREC_TC_FP16 || o.precision == CWT_PREC_TC_BF16) return CWT_EUNSUPPORTED;
         return CWT_EINVAL;
     }
+    if (o.edge_mode != CWT_EDGE_CYCLIC && o.edge_mode != CWT_EDGE_LINEAR) return CWT_EINVAL;
+    // linear edges: pad by the widest wavelet's support radius R (Gaussian
+    // envelope below 1e-9 of its peak beyond R samples) so that nothing wraps
+    int pad_extra = 0;
+    if (o.edge_mode == CWT_EDGE_LINEAR) {
+        if (wavelet == CWT_WAVELET_GMW) return CWT_EUNSUPPORTED;
+        double amax = 0.0;
+        for (int i = 0; i < n_freqs; ++i) amax = std::max(amax, n_cycles[i] / (2.0 * kPi * freqs_hz[i]));
+        const double R = std::ceil(6.5 * amax * fs);
+        if (!(R + 1.0 + samples <= (double)cwtk::kMaxClusterFft)) return CWT_EUNSUPPORTED;
+        pad_extra = (int)R + 1;
+    }
+    const int min_len = samples + pad_extra;
     int N = 0;
     if (o.fft_length != 0) {
-        if (o.fft_length < samples || o.fft_length < cwtk::kMinFft) return CWT_EINVAL;
+        if (o.fft_length < min_len || o.fft_length < cwtk::kMinFft) return CWT_EINVAL;
         if (!is_pow2(o.fft_length)) {
             cwtk::MrSchedule sch;
             int x = o.fft_length;
@@ -209,7 +225,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         if (o.fft_length > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
         N = o.fft_length;
     } else {
-        cwt_status st = cwt_fft_length(samples, o.pad_policy, &N);
+        cwt_status st = cwt_fft_length(min_len, o.pad_policy, &N);
         if (st != CWT_OK) return st;
     }
     if ((long long)channels * n_freqs > (1ll << 30)) return CWT_EUNSUPPORTED;
@@ -232,6 +248,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->fs = fs;
     p->wavelet = wavelet;
     p->gmw_gamma = o.gmw_gamma;
+    p->pad_extra = pad_extra;
     p->outputs = output_kinds;
     p->io = o.io_dtype;
     p->freqs.assign(freqs_hz, freqs_hz + n_freqs);
@@ -390,7 +407,7 @@ cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, 
     for (int i = 0; i < n_epochs; ++i) {
         const cwt_epoch &e = epochs[i];
         if (e.samples < 1 || e.samples > p->n || e.in_offset < 0 || e.out_offset < 0) return CWT_EINVAL;
-        if (e.samples > 8192) return CWT_EUNSUPPORTED;
+        if (e.samples + p->pad_extra > 8192) return CWT_EUNSUPPORTED;
     }
     if (n_epochs == 0) return CWT_OK;
     DeviceGuard g(p->device);

@@ -151,7 +151,7 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
     for (int ei = 0; ei < n_epochs; ++ei) {
         const cwt_epoch &ep = epochs[ei];
         int N = kMinFft;
-        while (N < ep.samples) N <<= 1;
+        while (N < ep.samples + p->pad_extra) N <<= 1;
         const int L = ilog2c(N);
         if (!b->bank[L]) {
             e = cudaMalloc(&b->bank[L], sizeof(float) * (size_t)S * N);

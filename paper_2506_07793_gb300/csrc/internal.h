@@ -44,6 +44,7 @@ struct cwt_plan_s {
     double fs = 0;
     int wavelet = 0;
     double gmw_gamma = 3.0;  // gamma of Eq. 5 (CWT_WAVELET_GMW only)
+    int pad_extra = 0;       // linear edges: samples added before padding (R + 1)
     unsigned outputs = 0;
     int io = CWT_DTYPE_F32;
     std::vector<double> freqs, cycles;

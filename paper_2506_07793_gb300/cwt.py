@@ -24,6 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 CWT_OK, CWT_EINVAL, CWT_ENOMEM, CWT_EUNSUPPORTED, CWT_ECUDA = 0, 1, 2, 3, 4
 CWT_EAGAIN, CWT_EBUSY, CWT_ETIMEDOUT, CWT_EDEVICE = 5, 6, 7, 8
 CWT_WAVELET_MORLET, CWT_WAVELET_GABOR, CWT_WAVELET_GMW = 0, 1, 2
+CWT_EDGE_CYCLIC, CWT_EDGE_LINEAR = 0, 1
 CWT_OUT_COMPLEX, CWT_OUT_POWER, CWT_OUT_PHASE = 1, 2, 4
 CWT_PREC_FP32, CWT_PREC_TC_FP16, CWT_PREC_TC_BF16 = 0, 1, 2
 CWT_DTYPE_F32, CWT_DTYPE_F64 = 0, 1
@@ -34,7 +35,7 @@ CWT_KERNEL_BANK, CWT_KERNEL_FORWARD_FFT, CWT_KERNEL_SCALE_BLOCK, CWT_KERNEL_BATC
 class cwt_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("decimation", ctypes.c_int),
                 ("pad_policy", ctypes.c_int), ("fft_length", ctypes.c_int),
-                ("io_dtype", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("io_dtype", ctypes.c_int), ("edge_mode", ctypes.c_int),
                 ("gmw_gamma", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
 
 
@@ -303,11 +304,12 @@ class CWT:
 
     def __init__(self, channels, samples, fs, freqs, n_cycles, outputs=("power",),
                  wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2",
-                 gmw_gamma=3.0):
+                 gmw_gamma=3.0, edge="cyclic"):
         opt = cwt_options_init()
         opt.decimation = int(decimation)
         opt.pad_policy = {"pow2": CWT_PAD_POW2, "smooth": CWT_PAD_SMOOTH}[pad]
         opt.gmw_gamma = float(gmw_gamma)
+        opt.edge_mode = {"cyclic": CWT_EDGE_CYCLIC, "linear": CWT_EDGE_LINEAR}[edge]
         opt.io_dtype = CWT_DTYPE_F64 if dtype in ("f64", "float64") else CWT_DTYPE_F32
         opt.fft_length = int(fft_length)
         kinds = 0

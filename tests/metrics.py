@@ -1,7 +1,7 @@
 """Error metrics shared by the parity tests and the benchmark's checks.
 
-Per (channel, scale) row, as the north-star tolerance reads "relative error on
-power normalised by its maximum" (stricter than a global maximum):
+Per (channel, scale) row: relative error on power normalised by its maximum,
+taken row by row (stricter than a global maximum):
   power:   max_t |P_gpu - P_ref| / max_t P_ref
   complex: max_t |c_gpu - c_ref| / max_t |c_ref|
   phase:   max_t |e^{i phi_gpu} - e^{i phi_ref}| * |c_ref[t]| / max_t |c_ref|

@@ -83,18 +83,20 @@ BAD = [
     dict(wavelet=7), dict(kinds=0), dict(kinds=8), dict(decimation=0), dict(io=5),
     dict(precision=9), dict(fft_length=101), dict(fft_length=64, samples=100),
     dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
-    dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]),
+    dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]), dict(edge=2), dict(edge=-1),
+    dict(edge=1, fft_length=128),  # linear edges need N >= n + R + 1 (here 100 + 363 + 1)
 ]
 
 
 @pytest.mark.parametrize("bad", BAD)
 def test_invalid_arguments_rejected_before_cuda(lib, bad):
     a = dict(channels=2, samples=100, fs=500.0, freqs=[10.0, 20.0], n_cycles=[7.0, 7.0],
-             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0)
+             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0, edge=0)
     a.update(bad)
     o = lib.cwt_options_init()
     o.decimation, o.io_dtype, o.precision, o.fft_length = a["decimation"], a["io"], a["precision"], a["fft_length"]
     o.gmw_gamma = a["gamma"]
+    o.edge_mode = a["edge"]
     f = np.asarray(a["freqs"], dtype=np.float64)
     c = np.asarray(a["n_cycles"], dtype=np.float64)
     if len(c) != len(f):
@@ -110,9 +112,22 @@ def test_option_struct_layout(lib):
     o = lib.cwt_options_init()
     assert ctypes.sizeof(o) == 64 and type(o).gmw_gamma.offset == 24
     assert o.gmw_gamma == 3.0 and o.decimation == 1
+    assert type(o).edge_mode.offset == 20 and o.edge_mode == lib.CWT_EDGE_CYCLIC
     so = lib.cwt_server_options_init()
     assert ctypes.sizeof(so) == 56 and type(so).gmw_gamma.offset == 32
     assert so.gmw_gamma == 3.0 and so.max_streams == 32
+
+
+def test_linear_edges_unsupported_for_gmw_and_too_long(lib):
+    o = lib.cwt_options_init()
+    o.edge_mode = lib.CWT_EDGE_LINEAR
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(1, 100, 500.0, [10.0], [20.0], lib.CWT_WAVELET_GMW, lib.CWT_OUT_POWER, o)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+    # 0.01 Hz with 7 cycles at 4 kHz: the support radius alone exceeds 2^17 samples
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(1, 100, 4000.0, [0.01], [7.0], 0, lib.CWT_OUT_POWER, o)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long"])

@@ -28,10 +28,38 @@ def lib():
     return p
 
 
-def make_plan(lib, C, n_max, fs, freqs, cycles, kinds, d):
+def make_plan(lib, C, n_max, fs, freqs, cycles, kinds, d, edge=0):
     o = lib.cwt_options_init()
     o.decimation = d
+    o.edge_mode = edge
     return lib.cwt_plan_create(C, n_max, fs, freqs, cycles, 0, kinds, o)
+
+
+def test_linear_edges_batch(lib):
+    """Linear edges in a batch: each epoch padded to a power of two >= n + R + 1."""
+    import torch
+    C, fs, d = 2, 500.0, 2
+    freqs = np.array([6.0, 20.0, 70.0])
+    cycles = np.array([5.0, 7.0, 9.0])
+    R = int(np.ceil(6.5 * max(cycles / (2 * np.pi * freqs)) * fs))
+    lengths = [40, 300, 1000, 3000]
+    plan = make_plan(lib, C, 3000, fs, freqs, cycles, lib.CWT_OUT_POWER, d, edge=lib.CWT_EDGE_LINEAR)
+    try:
+        ep, n_in, n_o = lib.pack_epochs(lengths, C, len(freqs), d)
+        xs = [eeg(600 + k, C, n, fs, np.float32) for k, n in enumerate(lengths)]
+        x = torch.from_numpy(np.concatenate([a.reshape(-1) for a in xs])).cuda()
+        pw = torch.full((n_o,), np.nan, dtype=torch.float32, device="cuda")
+        lib.cwt_execute_batch(plan, ep, x, None, pw, None)
+        torch.cuda.synchronize()
+        pw = pw.cpu().numpy()
+        for k, n in enumerate(lengths):
+            N = lib.cwt_fft_length(n + R + 1)
+            ref = oracle.cwt(xs[k].astype(np.float64), N, fs, freqs, cycles, decimation=d)
+            no = -(-n // d)
+            sl = slice(ep[k].out_offset, ep[k].out_offset + C * len(freqs) * no)
+            assert power_err(pw[sl].reshape(C, len(freqs), no), ref).max() <= FP32_TOL
+    finally:
+        lib.cwt_plan_destroy(plan)
 
 
 @pytest.mark.parametrize("d", [1, 3, 4])
@@ -59,8 +87,10 @@ def test_small_ragged_batch_every_row(lib, d):
             no = -(-n // d)
             sl = slice(ep[k].out_offset, ep[k].out_offset + C * len(freqs) * no)
             # rows whose carrier sits below 2 DFT bins of N are degenerate: the
-            # periodised wavelet cancels to ~0 and only the GPU's closed form
-            # keeps precision (reading R13); compare the rest
+            # periodised wavelet cancels to ~0 (admissibility) and only the
+            # GPU's closed-form spectrum keeps precision, while the oracle's
+            # time-domain sum over many replicas is cancellation noise;
+            # compare the rest
             ok = freqs * N / fs >= 2.0
             got = pw[sl].reshape(C, len(freqs), no)[:, ok]
             assert power_err(got, ref[:, ok]).max() <= FP32_TOL, (n, power_err(got, ref[:, ok]).max())

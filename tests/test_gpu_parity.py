@@ -31,11 +31,11 @@ def lib():
 
 
 def run_gpu(lib, x, fs, freqs, cycles, outputs, dtype="f32", decimation=1, wavelet="morlet",
-            fft_length=0, pad="pow2", gmw_gamma=3.0):
+            fft_length=0, pad="pow2", gmw_gamma=3.0, edge="cyclic"):
     import torch
     C, n = x.shape
     t = lib.CWT(C, n, fs, freqs, cycles, outputs=outputs, dtype=dtype, decimation=decimation,
-                wavelet=wavelet, fft_length=fft_length, pad=pad, gmw_gamma=gmw_gamma)
+                wavelet=wavelet, fft_length=fft_length, pad=pad, gmw_gamma=gmw_gamma, edge=edge)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = t(xt)
     torch.cuda.synchronize()
@@ -396,3 +396,49 @@ def test_gmw_every_row(lib, case):
     ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, betas, decimation=kw.get("decimation", 1),
                      wavelet="gmw", gamma=gam)
     check(res, ref)
+
+
+LINEAR = [
+    # (C, n, fs, freqs, cycles, kwargs)
+    (2, 500, 500.0, [4.0, 40.0, 200.0], [3.0, 7.0, 10.0], {}),
+    (2, 1000, 1000.0, np.geomspace(2, 300, 5), np.linspace(3, 10, 5), dict(decimation=3)),
+    (1, 3000, 1000.0, [5.0, 90.0], [7.0, 7.0], dict(pad="smooth")),
+    (2, 300, 200.0, [9.0, 50.0], [5.0, 7.0], dict(wavelet="gabor", dtype="f64")),
+]
+
+
+def _support_radius(fs, freqs, cycles):
+    a = max(c / (2 * np.pi * f) for f, c in zip(freqs, cycles))
+    return int(np.ceil(6.5 * a * fs))
+
+
+@pytest.mark.parametrize("case", range(len(LINEAR)))
+def test_linear_edges_equal_linear_convolution(lib, case):
+    """Linear ("same"-mode) edges: N >= n + R + 1, parity with the oracle at
+    that N, and agreement with a direct linear convolution of the signal with
+    the sampled wavelet (normalised like the oracle's) at every output,
+    edges included."""
+    C, n, fs, freqs, cycles, kw = LINEAR[case]
+    kw = dict(kw)
+    dtype = kw.pop("dtype", "f32")
+    wavelet = kw.pop("wavelet", "morlet")
+    x = eeg(990 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), dtype=dtype, wavelet=wavelet,
+                     edge="linear", **kw)
+    R = _support_radius(fs, freqs, cycles)
+    assert N >= n + R + 1
+    d = kw.get("decimation", 1)
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=d, wavelet=wavelet)
+    check(res, ref)
+    # direct linear convolution with the unperiodised sampled wavelet
+    lin = np.empty_like(ref)
+    for s, (F, sg) in enumerate(zip(freqs, cycles)):
+        a = sg / (2 * np.pi * F)
+        Rs = int(np.ceil(40 * a * fs))
+        tau = np.arange(-Rs, Rs + 1) / fs
+        kappa = 0.0 if wavelet == "gabor" else np.exp(-0.5 * sg * sg)
+        psi = np.exp(-tau ** 2 / (2 * a * a)) * (np.exp(2j * np.pi * F * tau) - kappa)
+        psi /= np.sqrt(np.sum(np.abs(oracle.periodised_wavelet(F, sg, fs, N, wavelet=wavelet)) ** 2))
+        for c in range(C):
+            lin[c, s] = np.convolve(x[c].astype(np.float64), psi)[Rs:Rs + n][::d]
+    check({"complex": res["complex"]}, lin)
