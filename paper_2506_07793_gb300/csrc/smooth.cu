@@ -129,9 +129,16 @@ double dft_cost(int R) {
     const int R1 = first_factor(R), R2 = R / R1;
     return R2 * dft_cost(R1) + R1 * dft_cost(R2) + 6.0 * (R1 - 1) * (R2 - 1);
 }
-// One butterfly of a pass: the DFT, R - 1 twiddle products, staging R values in and out.
-double butterfly_cost(int R) { return dft_cost(R) + 6.0 * (R - 1) + 8.0 * R; }
-constexpr double kPassOverhead = 24.0;  // per thread and pass: barriers, loop, index math
+// One butterfly of a pass: the DFT, R - 1 twiddle products, staging R values
+// in and out, and a fixed cost (twiddle-chain setup, index arithmetic,
+// predication).  The fixed cost and the radix-32 weight were fitted to
+// measured kernel times of 35 schedules at N = 100 ... 10000 (64 channels,
+// 61 or 100 scales on GB300): with them the model picks the fastest measured
+// schedule or one within 10% of it.
+double butterfly_cost(int R) {
+    return dft_cost(R) * (R == 32 ? 2.0 : 1.0) + 6.0 * (R - 1) + 8.0 * R + 120.0;
+}
+constexpr double kPassOverhead = 24.0;  // per thread and pass: barriers, call
 
 void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vector<int>> &out) {
     if (rem == 1) {
