@@ -53,8 +53,7 @@ struct MrPass {
 
 struct MrSchedule {
     int N;           // row length
-    int T;           // threads per row
-    int rows;        // rows per CTA
+    int T;           // threads per row (rows per CTA are chosen per launch)
     int np;          // passes
     unsigned mag0;   // ceil(2^32 / (N / R_0)), for the sparse first pass
     MrPass p[kMrMaxPasses];
@@ -363,10 +362,8 @@ __device__ __forceinline__ RowSlot row_slot(const MrSchedule &sch, int rows, int
     return s;
 }
 
-#ifndef CWT_MR_RADICES
 #define CWT_MR_RADICES(X) \
     X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(15) X(16) X(18) X(20) X(21) X(24) X(25) X(27) X(28) X(30) X(32)
-#endif
 
 // The whole row (at least two passes).  `sm` is this row's buffer of
 // N + N/16 float2; on return it holds X[t] at spad2(t) (natural order) for

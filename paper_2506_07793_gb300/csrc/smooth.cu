@@ -234,7 +234,6 @@ bool mr_schedule(int N, MrSchedule *out) {
     MrSchedule s{};
     s.N = N;
     s.T = best_T;
-    s.rows = 1;
     s.np = (int)cands[best_i].size();
     int Ns = 1;
     for (int q = 0; q < s.np; ++q) {
