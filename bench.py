@@ -35,28 +35,33 @@ METRIC = "CWT coeffs/sec (ch x scales x samples)"
 UNIT = "coeffs/s"
 WORKLOAD = "fused"
 L2_FLUSH_BYTES = 256 << 20
-PROFILE_FILE = os.path.join(ROOT, "profiles", "scale_block_fp32_fused_64x100x10000.txt")
-KERNEL_SOURCES = ["fft_core.cuh", "scale_block.cu"]
+# committed ncu summaries of the fused workload's scale-block kernel, per
+# padding, and the sources each was captured from
+PROFILES = {
+    "pow2": ("scale_block_fp32_fused_64x100x10000.txt", ["fft_core.cuh", "scale_block.cu"]),
+    "smooth": ("mr_scale_block_fp32_fused_smooth_64x100x10000.txt",
+               ["fft_core.cuh", "mixed_radix.cuh", "smooth_kernel.cuh", "smooth.cu", "smooth_fast_a.cu"]),
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(pad="pow2"):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in PROFILES[pad][1]:
         with open(os.path.join(ROOT, "paper_2506_07793_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(pad="pow2"):
     """DRAM bytes per launch of the scale-block kernel from the committed ncu
     summary, or None when the kernel source changed since it was captured."""
     try:
-        text = open(PROFILE_FILE).read()
+        text = open(os.path.join(ROOT, "profiles", PROFILES[pad][0])).read()
     except OSError:
         return None
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(pad):
         return None
     return float(m_bytes.group(1))
 
@@ -114,13 +119,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, x_rows, n_channels, n_scales=None):
+def cpu_baseline(w, x_rows, n_channels, n_scales=None, N=None):
     """The FP64 oracle, as it stands, on the host cores: the first n_scales
-    (default all) scales of the first n_channels channels of the same workload."""
+    (default all) scales of the first n_channels channels of the same workload,
+    at the padded length N of the timed plan."""
     import oracle
     from paper_2506_07793_gb300 import cwt_fft_length
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    N = cwt_fft_length(w.samples)
+    N = cwt_fft_length(w.samples) if N is None else N
     ns = w.scales if n_scales is None else n_scales
     rows = [(c, s) for c in range(n_channels) for s in range(0, w.scales, max(1, w.scales // ns))][:n_channels * ns]
     t0 = time.perf_counter()
@@ -141,11 +147,10 @@ def run_reference(args):
         return
     from eeg_synth import workload
     import oracle
+    from paper_2506_07793_gb300 import CWT_PAD_POW2, CWT_PAD_SMOOTH, cwt_fft_length
     w = workload(WORKLOAD)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    N = 1
-    while N < max(w.samples, 32):
-        N *= 2
+    N = cwt_fft_length(w.samples, CWT_PAD_SMOOTH if args.pad == "smooth" else CWT_PAD_POW2)
     x = w.signal(channels=1).astype(np.float64)
     rows = [(0, s) for s in range(w.scales)]
     for _ in range(args.warmup):
@@ -200,6 +205,26 @@ def plain_fp32_pipeline(cw, plan, x, fused_power, w, args, flush, stream):
     return {"value": w.coefficients / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "impl": "torch.fft (cuFFT): fft -> broadcast product -> ifft -> crop -> |c|^2",
             "max_row_power_diff_vs_fused": row_err, "speedup_of_fused": None}
+
+
+def other_padding(cw, w, kinds, pad, x, outs, flush, stream, args):
+    """The same workload under the other padding policy (same outputs, same
+    timing method), reported beside the main line for comparison."""
+    o = cw.cwt_options_init()
+    o.pad_policy = cw.CWT_PAD_SMOOTH if pad == "smooth" else cw.CWT_PAD_POW2
+    plan = cw.cwt_plan_create(w.channels, w.samples, w.fs, w.freqs, w.n_cycles,
+                              cw.CWT_WAVELET_MORLET, kinds, o)
+    N = cw.cwt_plan_info(plan).fft_length
+    step = lambda: cw.cwt_execute(plan, x, *outs, stream)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    cw.cwt_plan_set_profiling(plan, True)
+    cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_SCALE_BLOCK, reset=True)
+    ms = timed_steps(step, args.steps, flush, stream) / args.steps
+    n_sb, ms_sb = cw.cwt_plan_profile_read(plan, cw.CWT_KERNEL_SCALE_BLOCK, reset=True)
+    cw.cwt_plan_destroy(plan)
+    return {"padding": pad, "fft_length": N, "value": w.coefficients / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "kernel_ms": ms_sb / max(n_sb, 1)}
 
 
 def timed_steps(step, steps, flush, stream):
@@ -506,8 +531,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["fused", "batch", "serving", "precision", "sweep"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
-    ap.add_argument("--pad", default="pow2", choices=["pow2", "smooth"],
-                    help="padding policy: next power of two, or the paper's 2,3,5,7-smooth length")
+    ap.add_argument("--pad", default="smooth", choices=["pow2", "smooth"],
+                    help="padding policy: the paper's 2,3,5,7-smooth length (default) or the next "
+                         "power of two")
     ap.add_argument("--channels", type=int, default=0,
                     help="override the workload's channel count (small profiling captures)")
     ap.add_argument("--epochs", type=int, default=0,
@@ -706,9 +732,12 @@ def run_plan_workload(args, name):
                  + w.scales * N * 4)                               # wavelet bank, read once
     sb_s = ms_sb / max(n_sb, 1) * 1e-3
     achieved = alg_bytes / sb_s / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(args.pad)
     if N & (N - 1):
-        kname = f"mr_scale_block_kernel (mixed radix, N = {N})"
+        pair = tuple(info.inlined_pair)
+        rad = "x".join(str(r) for r in info.radices if r)
+        kname = (f"mr_scale_block_kernel<{pair[0]}, {pair[1]}> (inlined radix pair; N = {N} = {rad})"
+                 if pair[0] else f"mr_scale_block_kernel<0, 0> (generic mixed radix; N = {N} = {rad})")
     elif N <= 16384:
         kname = f"scale_block_kernel<{N},float>"
     else:
@@ -716,7 +745,7 @@ def run_plan_workload(args, name):
     roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
-                "traffic": traffic if (name == "fused" and args.pad == "pow2") else None,
+                "traffic": traffic if name == "fused" else None,
                 "alg_bytes_per_launch": alg_bytes,
                 "kernel_ms": sb_s * 1e3, "forward_fft_ms": ms_fw / max(n_fw, 1)}
 
@@ -746,6 +775,9 @@ def run_plan_workload(args, name):
     plain = (plain_fp32_pipeline(cw, plan, x, out_p, w, args, flush, stream) if name == "fused"
              else None)
     cw.cwt_plan_destroy(plan)
+    other = (other_padding(cw, w, kinds, "pow2" if args.pad == "smooth" else "smooth", x,
+                           (out_c, out_p, out_ph), flush, stream, args)
+             if name == "fused" and world == 1 else None)
 
     if rank == 0:
         line = {
@@ -765,9 +797,11 @@ def run_plan_workload(args, name):
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
         }
+        if other is not None:
+            line["other_padding"] = other
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels if name == "fused" else 1,
-                                                None if name == "fused" else 8)
+                                                None if name == "fused" else 8, N=N)
         if plain is not None:
             plain["speedup_of_fused"] = plain["ms_per_step"] / ms_step
         else:

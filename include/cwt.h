@@ -160,6 +160,10 @@ typedef struct {
     unsigned output_kinds;
     size_t workspace_bytes; /* device bytes owned by the plan */
     double bank_ms;         /* GPU time of the bank generation at creation */
+    int radices[8];         /* smooth N: the inverse FFT's radix schedule, 0-terminated
+                               (all 0 for powers of two) */
+    int inlined_pair[2];    /* smooth N: the radix pair of the inlined kernel that runs
+                               it, or 0, 0 for the generic mixed-radix kernel */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */

@@ -15,6 +15,7 @@
 
 #include "fft_core.cuh"
 #include "internal.h"
+#include "smooth_kernel.cuh"
 
 using cwtk::ilog2c;
 
@@ -135,6 +136,8 @@ const char *cwt_status_str(cwt_status s) {
 
 // the Python binding mirrors this layout
 static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24, "cwt_options layout");
+static_assert(sizeof(cwt_plan_info_t) == 104 && offsetof(cwt_plan_info_t, radices) == 64,
+              "cwt_plan_info_t layout");
 
 cwt_status cwt_options_init(cwt_options *opt) {
     if (!opt) return CWT_EINVAL;
@@ -310,6 +313,18 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->output_kinds = p->outputs;
     info->workspace_bytes = p->bytes + p->stage_bytes;
     info->bank_ms = p->bank_ms;
+    if (p->mr) {
+        for (int q = 0; q < p->sch.np && q < 7; ++q) info->radices[q] = p->sch.p[q].R;
+        if (p->sch.fast >= 0) {
+            int a = 0, b = 0;
+#define CWT_MR_CASE(I, A, B) \
+    if (p->sch.fast == I) a = A, b = B;
+            CWT_MR_FAST_PAIRS(CWT_MR_CASE)
+#undef CWT_MR_CASE
+            info->inlined_pair[0] = a;
+            info->inlined_pair[1] = b;
+        }
+    }
     return CWT_OK;
 }
 

@@ -7,11 +7,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <iterator>
 #include <vector>
 
-#include "internal.h"
-#include "phase.cuh"
-#include "mixed_radix.cuh"
+#include "smooth_kernel.cuh"
 
 namespace cwtk {
 
@@ -23,86 +22,6 @@ __global__ void twiddle_n_kernel(float2 *tw, int N) {
         double s, c;
         sincospi(2.0 * (double)m / (double)N, &s, &c);
         tw[m] = make_float2((float)c, (float)s);
-    }
-}
-
-__device__ __noinline__ void mr_phase_f(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
-__device__ __noinline__ void mr_phase_d(double *dst, float2 v) { *dst = (double)phase_atan2(v.y, v.x); }
-
-
-struct MrArgs {
-    const float2 *spec;
-    const float *bank;
-    const int *band;
-    const float2 *twN;
-    void *out_c, *out_p, *out_ph;
-    int S, n_out, sub, total_rows, f64;
-};
-
-// Fused spectrum product, inverse FFT and epilogue per (channel, scale) row.
-__global__ void __launch_bounds__(kMrThreads, 1)
-mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
-    extern __shared__ float2 mrsm[];
-    const int N = sch.N;
-    const RowSlot rs = row_slot(sch, rows, a.total_rows);
-    const int row = rs.active ? (int)blockIdx.x * rows + rs.rr : 0;
-    const int rr = rs.rr < rows ? rs.rr : 0;
-    float2 *sm = mrsm + (size_t)rr * (N + (N >> 4));
-    const int c = row / a.S, s = row - c * a.S;
-    const float2 *X = a.spec + (size_t)c * N;
-    const float *W = a.bank + (size_t)s * N;
-    const int b0 = a.band[2 * s], B = a.band[2 * s + 1];
-    auto load = [=](int k) -> float2 {
-        int dk = k - b0;  // the band is [b0, b0 + B) modulo N
-        if (dk < 0) dk += N;
-        if (dk < B) {
-            const float2 xv = X[k];
-            const float w = W[k];
-            return make_float2(xv.x * w, xv.y * w);
-        }
-        return make_float2(0.f, 0.f);
-    };
-    // Narrow band (B <= N/R_0): butterfly b's inputs b + r nb, r < R_0, meet
-    // the band at most once, at e = b0 + u (mod N) with u = (b - b0) mod nb.
-    auto first_nz = [=](int b, int nb, unsigned mag, int &r, float2 &x) -> bool {
-        const unsigned d = (unsigned)(b - b0 + N);  // > 0; N is a multiple of nb
-        const int u = (int)(d - __umulhi(d, mag) * (unsigned)nb);
-        if (u >= B) return false;
-        int e = b0 + u;
-        if (e >= N) e -= N;
-        r = (int)__umulhi((unsigned)(e - b), mag);  // (e - b) / nb, exact: e = b (mod nb), e >= b
-        const float2 xv = X[e];
-        const float w = W[e];
-        x = make_float2(xv.x * w, xv.y * w);
-        return true;
-    };
-    const bool sparse = B <= N / sch.p[0].R;
-    mr_row<+1>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
-    if (!rs.active) return;
-    // epilogue: crop to t < n, keep t = sub * o, write the requested outputs
-    // (consecutive threads take consecutive o: coalesced stores)
-    const size_t obase = (size_t)row * (size_t)a.n_out;
-    const int sub = a.sub, n_out = a.n_out;
-    if (a.f64) {
-        double2 *oc = (double2 *)a.out_c + obase;
-        double *op = (double *)a.out_p + obase, *oph = (double *)a.out_ph + obase;
-#pragma unroll 1
-        for (int o = rs.j; o < n_out; o += sch.T) {
-            const float2 v = sm[spad2(o * sub)];
-            if (a.out_c) oc[o] = make_double2(v.x, v.y);
-            if (a.out_p) op[o] = (double)fmaf(v.x, v.x, v.y * v.y);
-            if (a.out_ph) mr_phase_d(oph + o, v);
-        }
-    } else {
-        float2 *oc = (float2 *)a.out_c + obase;
-        float *op = (float *)a.out_p + obase, *oph = (float *)a.out_ph + obase;
-#pragma unroll 2
-        for (int o = rs.j; o < n_out; o += sch.T) {
-            const float2 v = sm[spad2(o * sub)];
-            if (a.out_c) oc[o] = v;
-            if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
-            if (a.out_ph) mr_phase_f(oph + o, v);
-        }
     }
 }
 
@@ -140,16 +59,17 @@ double butterfly_cost(int R) {
 }
 constexpr double kPassOverhead = 24.0;  // per thread and pass: barriers, call
 
-void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vector<int>> &out) {
+void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vector<int>> &out,
+               const std::vector<int> &allowed) {
     if (rem == 1) {
         out.push_back(cur);
         return;
     }
     if ((int)cur.size() >= kMrMaxPasses) return;
-    for (int R : kRadixSet) {
+    for (int R : allowed) {
         if (R < min_r || rem % R) continue;
         cur.push_back(R);
-        enumerate(rem / R, R, cur, out);
+        enumerate(rem / R, R, cur, out, allowed);
         cur.pop_back();
     }
 }
@@ -170,7 +90,6 @@ int sm_count() {
 }
 
 constexpr int kMrRowSmemCap = 96 * 1024;          // several rows per CTA: at most this much
-constexpr int kMrMaxSmem = (kMaxFft + (kMaxFft >> 4)) * 8;
 
 // Rows per CTA for a launch over total_rows rows: up to 256 threads per CTA
 // for short rows, but at least two CTAs per SM when there are enough rows.
@@ -183,36 +102,28 @@ int launch_rows(const MrSchedule &sch, int total_rows) {
     return rows;
 }
 
-int round_up32(int x) { return (x + 31) & ~31; }
 
-cudaError_t mr_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
-    static unsigned done = 0;
-    cudaError_t e = ensure_smem_attr(mr_scale_block_kernel, kMrMaxSmem, &done);
-    if (e != cudaSuccess) return e;
-    const int rows = launch_rows(p->sch, a.total_rows);
-    const int smem = rows * (p->N + (p->N >> 4)) * 8;
-    mr_scale_block_kernel<<<(a.total_rows + rows - 1) / rows, round_up32(rows * p->sch.T), smem, st>>>(
-        a, p->sch, rows);
-    return cudaGetLastError();
-}
 
 }  // namespace
 
 int mr_launch_rows(const MrSchedule &sch, int total_rows) { return launch_rows(sch, total_rows); }
 
-bool mr_schedule(int N, MrSchedule *out) {
-    if (N < kMinFft || N > kMaxFft) return false;
-    int x = N;
-    for (int f : {2, 3, 5, 7})
-        while (x % f == 0) x /= f;
-    if (x != 1) return false;
+namespace {
+
+// Cheapest schedule of N over the given radices (cost model above), or
+// cost < 0 when none fits 32 values per thread and 512 threads per row.
+struct Plan1 {
+    double cost = -1.0;
+    std::vector<int> radices;
+    int T = 0;
+};
+
+Plan1 search(int N, const std::vector<int> &allowed) {
     std::vector<std::vector<int>> cands;
     std::vector<int> cur;
-    enumerate(N, 2, cur, cands);
-    double best = 0.0;
-    int best_i = -1, best_T = 0;
-    for (int i = 0; i < (int)cands.size(); ++i) {
-        const std::vector<int> &rs = cands[i];
+    enumerate(N, 2, cur, cands, allowed);
+    Plan1 best;
+    for (const std::vector<int> &rs : cands) {
         int Tmin = 1;
         for (int R : rs) {
             const int gm = std::max(1, kMrPoints / R);  // mr_gmax
@@ -222,24 +133,56 @@ bool mr_schedule(int N, MrSchedule *out) {
             double c = kPassOverhead * (double)rs.size();
             for (int R : rs) c += (double)((N / R + T - 1) / T) * butterfly_cost(R);
             c *= T;
-            if (best_i < 0 || c < best * (1.0 - 1e-9) ||
-                (c <= best * (1.0 + 1e-9) && rs.size() < cands[best_i].size())) {
-                best = c;
-                best_i = i;
-                best_T = T;
+            if (best.cost < 0 || c < best.cost * (1.0 - 1e-9) ||
+                (c <= best.cost * (1.0 + 1e-9) && rs.size() < best.radices.size())) {
+                best.cost = c;
+                best.radices = rs;
+                best.T = T;
             }
         }
     }
-    if (best_i < 0) return false;
+    return best;
+}
+
+// An inlined radix pair is taken when its best schedule costs at most this
+// much more than the best over all radices (the model counts operations; the
+// inlined rows run about 1.35x more of them per second).
+constexpr double kFastPairGain = 1.3;
+
+}  // namespace
+
+bool mr_schedule(int N, MrSchedule *out) {
+    if (N < kMinFft || N > kMaxFft) return false;
+    int x = N;
+    for (int f : {2, 3, 5, 7})
+        while (x % f == 0) x /= f;
+    if (x != 1) return false;
+    const std::vector<int> all(std::begin(kRadixSet), std::end(kRadixSet));
+    Plan1 best = search(N, all);
+    if (best.cost < 0) return false;
+    int fast = -1;
+    Plan1 fbest;
+#define CWT_MR_TRY(I, A, B)                                                               \
+    {                                                                                     \
+        Plan1 f = search(N, {A, B});                                                      \
+        if (f.cost >= 0 && f.cost <= kFastPairGain * best.cost && (fast < 0 || f.cost < fbest.cost)) { \
+            fast = I;                                                                     \
+            fbest = f;                                                                    \
+        }                                                                                 \
+    }
+    CWT_MR_FAST_PAIRS(CWT_MR_TRY)
+#undef CWT_MR_TRY
+    if (fast >= 0) best = fbest;
     MrSchedule s{};
     s.N = N;
-    s.T = best_T;
-    s.np = (int)cands[best_i].size();
+    s.T = best.T;
+    s.fast = fast;
+    s.np = (int)best.radices.size();
     int Ns = 1;
     for (int q = 0; q < s.np; ++q) {
-        const int R = cands[best_i][q];
+        const int R = best.radices[q];
         s.p[q].R = R;
-        s.p[q].G = (N / R + best_T - 1) / best_T;
+        s.p[q].G = (N / R + best.T - 1) / best.T;
         s.p[q].Ns = Ns;
         s.p[q].mag = magic_of(Ns);
         s.p[q].tws = N / (Ns * R);
@@ -270,7 +213,13 @@ cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p,
     a.sub = p->d;
     a.total_rows = p->C * p->S;
     a.f64 = p->io == CWT_DTYPE_F64;
-    return mr_sb_launch(p, a, st);
+    switch (p->sch.fast) {
+#define CWT_MR_CASE(I, A, B) \
+    case I: return mr_sb_launch<A, B>(p, a, st);
+        CWT_MR_FAST_PAIRS(CWT_MR_CASE)
+#undef CWT_MR_CASE
+        default: return mr_sb_launch<0, 0>(p, a, st);
+    }
 }
 
 }  // namespace cwtk

@@ -442,3 +442,34 @@ def test_linear_edges_equal_linear_convolution(lib, case):
         for c in range(C):
             lin[c, s] = np.convolve(x[c].astype(np.float64), psi)[Rs:Rs + n][::d]
     check({"complex": res["complex"]}, lin)
+
+
+@pytest.mark.parametrize("n", [250, 500, 1000, 1600, 2000, 2500, 3200, 5000, 6400, 8000])
+def test_smooth_padding_common_eeg_lengths(lib, n):
+    """Whole seconds of EEG at 250 / 500 / 1000 Hz: 2^a 5^b lengths, which the
+    scheduler runs on the inlined radix-pair kernels (every pair at least once
+    over this list) -- parity with the oracle at that N."""
+    fs = 1000.0
+    freqs, cycles = [3.0, 20.0, 90.0], [5.0, 7.0, 9.0]
+    x = eeg(1010 + n, 2, n, fs, np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), pad="smooth")
+    assert N == n
+    check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
+
+
+def test_smooth_plan_reports_schedule(lib):
+    """The fused workload's smooth length N = 10000 runs 16 x 25 x 25 on the
+    inlined (16, 25) kernel; a length outside the pairs runs the generic one."""
+    o = lib.cwt_options_init()
+    o.pad_policy = lib.CWT_PAD_SMOOTH
+    for n, pair, rad in ((10000, (16, 25), [16, 25, 25]), (3001, (0, 0), None)):
+        plan = lib.cwt_plan_create(1, n, 1000.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER, o)
+        try:
+            info = lib.cwt_plan_info(plan)
+            assert tuple(info.inlined_pair) == pair
+            got = [r for r in info.radices if r]
+            assert int(np.prod(got)) == info.fft_length
+            if rad is not None:
+                assert got == rad
+        finally:
+            lib.cwt_plan_destroy(plan)
