@@ -173,6 +173,11 @@ bool mr_schedule(int N, MrSchedule *out) {
     CWT_MR_FAST_PAIRS(CWT_MR_TRY)
 #undef CWT_MR_TRY
     if (fast >= 0) best = fbest;
+    // A row of more than 128 threads has a CTA to itself; whole warps of 128
+    // run it faster than the cost model's tightest T (measured on GB300:
+    // N = 10000 at T = 400 -> 512, 354 -> 342 us; N = 5000 at 209 -> 256,
+    // 111 -> 106 us).  A larger T never raises a pass's butterflies per thread.
+    if (best.T > 128) best.T = std::min(kMrThreads, (best.T + 127) / 128 * 128);
     MrSchedule s{};
     s.N = N;
     s.T = best.T;
