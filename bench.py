@@ -531,9 +531,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["fused", "batch", "serving", "precision", "sweep"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
-    ap.add_argument("--pad", default="smooth", choices=["pow2", "smooth"],
-                    help="padding policy: the paper's 2,3,5,7-smooth length (default) or the next "
-                         "power of two")
+    ap.add_argument("--pad", default=None, choices=["pow2", "smooth"],
+                    help="padding policy: the paper's 2,3,5,7-smooth length (default for the fused "
+                         "workload) or the next power of two (default for the precision workload, "
+                         "whose 122880 samples exceed the smooth lengths built)")
     ap.add_argument("--channels", type=int, default=0,
                     help="override the workload's channel count (small profiling captures)")
     ap.add_argument("--epochs", type=int, default=0,
@@ -541,6 +542,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.pad is None:
+        args.pad = "pow2" if args.workload == "precision" else "smooth"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

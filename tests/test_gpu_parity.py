@@ -193,15 +193,18 @@ def test_host_buffers_match_device_path_and_repeat_bitwise(lib):
         lib.cwt_plan_destroy(plan)
 
 
-def test_pinned_host_outputs_written_directly_equal_device_path(lib):
+@pytest.mark.parametrize("pad", ["pow2", "smooth"])
+def test_pinned_host_outputs_written_directly_equal_device_path(lib, pad):
     """cwt_execute_host with page-locked, device-mapped outputs (written by the
     kernels over the host link) and with a mix of pinned and pageable outputs:
-    bitwise equal to the device path."""
+    bitwise equal to the device path (power-of-two and smooth kernels)."""
     import torch
     w = workload("fused")
     C, n = 4, w.samples
     x = np.ascontiguousarray(w.signal()[:C])
-    plan = lib.cwt_plan_create(C, n, w.fs, w.freqs, w.n_cycles, 0, lib.CWT_OUT_COMPLEX | lib.CWT_OUT_POWER)
+    o = lib.cwt_options_init()
+    o.pad_policy = lib.CWT_PAD_SMOOTH if pad == "smooth" else lib.CWT_PAD_POW2
+    plan = lib.cwt_plan_create(C, n, w.fs, w.freqs, w.n_cycles, 0, lib.CWT_OUT_COMPLEX | lib.CWT_OUT_POWER, o)
     try:
         shape = (C, w.scales, n)
         xt = torch.from_numpy(x).cuda()
