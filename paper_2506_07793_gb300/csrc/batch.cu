@@ -75,13 +75,13 @@ namespace {
 
 template <int RI>
 cudaError_t batch_attr() {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 32 && (done & (1u << dev))) return cudaSuccess;
+    if (dev < 32 && (done.load(std::memory_order_acquire) & (1u << dev))) return cudaSuccess;
     e = cudaFuncSetAttribute(batch_kernel_ptr(RI), cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem<RI>());
-    if (e == cudaSuccess && dev < 32) done |= 1u << dev;
+    if (e == cudaSuccess && dev < 32) done.fetch_or(1u << dev, std::memory_order_acq_rel);
     return e;
 }
 

@@ -125,7 +125,7 @@ cl_scale_block_kernel(const ClArgs a) {
 }
 
 template <typename K>
-cudaError_t cl_attr(K *kernel, int bytes, unsigned *done) {
+cudaError_t cl_attr(K *kernel, int bytes, std::atomic<unsigned> *done) {
     cudaError_t e = ensure_smem_attr(kernel, bytes, done);
     if (e == cudaSuccess) {
         // clusters of 8 are portable; nothing larger is requested
@@ -136,7 +136,7 @@ cudaError_t cl_attr(K *kernel, int bytes, unsigned *done) {
 
 template <int N, typename IO>
 cudaError_t cl_forward_n(const void *x, int C, int n, float2 *spec, const float2 *tw, cudaStream_t st) {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     cudaError_t e = cl_attr(cl_forward_kernel<N, IO>, ClusterShape<N>::SMEM_BYTES, &done);
     if (e != cudaSuccess) return e;
     cl_forward_kernel<N, IO><<<C * ClusterShape<N>::CL, kClThreads, ClusterShape<N>::SMEM_BYTES, st>>>(
@@ -146,7 +146,7 @@ cudaError_t cl_forward_n(const void *x, int C, int n, float2 *spec, const float2
 
 template <int N, typename IO>
 cudaError_t cl_sb_n(const ClArgs &a, int rows, cudaStream_t st) {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     cudaError_t e = cl_attr(cl_scale_block_kernel<N, IO>, ClusterShape<N>::SMEM_BYTES, &done);
     if (e != cudaSuccess) return e;
     cl_scale_block_kernel<N, IO><<<rows * ClusterShape<N>::CL, kClThreads, ClusterShape<N>::SMEM_BYTES, st>>>(a);
@@ -155,7 +155,7 @@ cudaError_t cl_sb_n(const ClArgs &a, int rows, cudaStream_t st) {
 
 template <int N, int SIGN>
 cudaError_t cl_fft_n(const float2 *in, float2 *out, int batch, const float2 *tw, cudaStream_t st) {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     cudaError_t e = cl_attr(cl_fft_kernel<N, SIGN>, ClusterShape<N>::SMEM_BYTES, &done);
     if (e != cudaSuccess) return e;
     cl_fft_kernel<N, SIGN><<<batch * ClusterShape<N>::CL, kClThreads, ClusterShape<N>::SMEM_BYTES, st>>>(

@@ -58,7 +58,7 @@ fft_kernel(const float2 *in, float2 *out, int batch, const float2 *__restrict__ 
 template <int N, typename IO>
 cudaError_t forward_n(const void *x, int C, int n, float2 *spec, const float2 *tw, cudaStream_t st) {
     using RC = RowConfig<N>;
-    static unsigned attr_done = 0;
+    static std::atomic<unsigned> attr_done{0};
     cudaError_t e = ensure_smem_attr(forward_kernel<N, IO>, RC::SMEM_BYTES, &attr_done);
     if (e != cudaSuccess) return e;
     const int grid = (C + RC::ROWS - 1) / RC::ROWS;
@@ -69,7 +69,7 @@ cudaError_t forward_n(const void *x, int C, int n, float2 *spec, const float2 *t
 template <int N, int SIGN>
 cudaError_t fft_n(const float2 *in, float2 *out, int batch, const float2 *tw, cudaStream_t st) {
     using RC = RowConfig<N>;
-    static unsigned attr_done = 0;
+    static std::atomic<unsigned> attr_done{0};
     cudaError_t e = ensure_smem_attr(fft_kernel<N, SIGN>, RC::SMEM_BYTES, &attr_done);
     if (e != cudaSuccess) return e;
     const int grid = (batch + RC::ROWS - 1) / RC::ROWS;

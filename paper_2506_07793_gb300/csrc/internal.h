@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -75,13 +77,15 @@ namespace cwtk {
 // Opt a kernel into `bytes` of dynamic shared memory once per device
 // (one bit of *done per device ordinal < 32; setting it twice is harmless).
 template <typename K>
-cudaError_t ensure_smem_attr(K *kernel, int bytes, unsigned *done) {
+cudaError_t ensure_smem_attr(K *kernel, int bytes, std::atomic<unsigned> *done) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 32 && (*done & (1u << dev))) return cudaSuccess;
+    // one bit per device; host threads may race here, and setting the
+    // attribute twice is harmless
+    if (dev < 32 && (done->load(std::memory_order_acquire) & (1u << dev))) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && dev < 32) *done |= 1u << dev;
+    if (e == cudaSuccess && dev < 32) done->fetch_or(1u << dev, std::memory_order_acq_rel);
     return e;
 }
 

@@ -198,7 +198,7 @@ cudaError_t na_run(const float *x, int C, int n, int S, char *base, size_t off_p
                    size_t off_band, size_t off_bank, size_t off_spec, double fs, float2 *oc,
                    float *op, float *oph, cudaStream_t st) {
     using RC = RowConfig<N>;
-    static unsigned attr_f = 0, attr_s = 0;
+    static std::atomic<unsigned> attr_f{0}, attr_s{0};
     cudaError_t e = ensure_smem_attr(na_forward_kernel<N>, RC::SMEM_BYTES, &attr_f);
     if (e == cudaSuccess) e = ensure_smem_attr(na_scale_block_kernel<N>, RC::SMEM_BYTES, &attr_s);
     if (e != cudaSuccess) return e;

@@ -146,7 +146,7 @@ scale_block_kernel(const SBArgs a) {
 template <int M, typename IO>
 cudaError_t sb_n(const SBArgs &a, cudaStream_t st) {
     using RC = RowConfig<M>;
-    static unsigned attr_done = 0;
+    static std::atomic<unsigned> attr_done{0};
     cudaError_t e = ensure_smem_attr(scale_block_kernel<M, IO>, RC::SMEM_BYTES, &attr_done);
     if (e != cudaSuccess) return e;
     const int grid = (a.rows + RC::ROWS - 1) / RC::ROWS;

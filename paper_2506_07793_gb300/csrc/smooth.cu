@@ -76,17 +76,17 @@ void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vecto
 
 unsigned magic_of(int d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d); }
 
-int g_sm_count[64] = {};
+std::atomic<int> g_sm_count[64] = {};
 
 int sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!g_sm_count[dev]) {
-        int v = 0;
+    int v = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-        g_sm_count[dev] = v;
+        g_sm_count[dev].store(v, std::memory_order_relaxed);
     }
-    return g_sm_count[dev];
+    return v;
 }
 
 constexpr int kMrRowSmemCap = 96 * 1024;          // several rows per CTA: at most this much

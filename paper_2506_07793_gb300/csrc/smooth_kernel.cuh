@@ -106,7 +106,7 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
 
 template <int RA, int RB>
 cudaError_t mr_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     cudaError_t e = ensure_smem_attr(mr_scale_block_kernel<RA, RB>, kMrMaxSmem, &done);
     if (e != cudaSuccess) return e;
     const int rows = mr_launch_rows(p->sch, a.total_rows);
@@ -149,7 +149,7 @@ mr_forward_kernel(const void *__restrict__ x, int f64, int n, float2 *__restrict
 
 template <int RA, int RB>
 cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
-    static unsigned done = 0;
+    static std::atomic<unsigned> done{0};
     cudaError_t e = ensure_smem_attr(mr_forward_kernel<RA, RB>, kMrMaxSmem, &done);
     if (e != cudaSuccess) return e;
     const int rows = mr_launch_rows(p->sch, p->C);

@@ -329,7 +329,7 @@ cwt_status cwt_server_create(cwt_server *out, const double *freqs_hz, const doub
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = device_twiddles(&s->tw);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-    static unsigned attr = 0;
+    static std::atomic<unsigned> attr{0};
     if (e == cudaSuccess) e = ensure_smem_attr(stream_kernel, kStreamSmem, &attr);
     for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
