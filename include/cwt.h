@@ -169,7 +169,8 @@ typedef struct {
 /* Human-readable name of a status.  Never NULL. */
 const char *cwt_status_str(cwt_status s);
 
-/* Fill *opt with defaults (FP32, d=1, POW2, N from policy, F32 I/O). */
+/* Fill *opt with defaults: FP32, d = 1, CWT_PAD_POW2, N from the policy, F32
+ * I/O, CWT_EDGE_CYCLIC, gmw_gamma 3. */
 cwt_status cwt_options_init(cwt_options *opt);
 
 /* Padded FFT length N for `samples` under `pad_policy` (Section "Fast Fourier

@@ -346,6 +346,8 @@ SMOOTH = [
     (3, 3001, 1000.0, np.geomspace(1, 400, 6), np.linspace(3, 10, 6), dict(decimation=3)),
     (2, 10000, 1000.0, [0.8, 10.0, 99.0], [3.0, 6.0, 10.0], {}),
     (1, 14000, 2000.0, [5.0, 300.0], [7.0, 7.0], {}),
+    (2, 33, 100.0, [5.0, 30.0], [3.0, 7.0], {}),            # N = 35 = 5 x 7, the shortest
+    (1, 1, 100.0, [10.0], [7.0], {}),                         # one sample: N = 32
 ]
 
 
@@ -359,7 +361,7 @@ def test_smooth_padding_every_row(lib, case):
     x = eeg(950 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
     res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), dtype=dtype,
                      pad="smooth", **kw)
-    assert N == lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) and N < 16384
+    assert N == lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) and N <= 16384
     ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=kw.get("decimation", 1))
     check(res, ref)
 
@@ -476,3 +478,14 @@ def test_smooth_plan_reports_schedule(lib):
                 assert got == rad
         finally:
             lib.cwt_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("N", [4000, 4096, 1215, 2401])
+def test_explicit_smooth_fft_length(lib, N):
+    """An explicit 2,3,5,7-smooth N (on an inlined pair, a power of two, a pure
+    3-smooth and a pure 7-smooth length): parity with the oracle at that N."""
+    fs, freqs, cycles = 500.0, [6.0, 60.0], [7.0, 7.0]
+    x = eeg(1100 + N, 2, 777, fs, np.float32)
+    res, got_N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), fft_length=N)
+    assert got_N == N
+    check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
