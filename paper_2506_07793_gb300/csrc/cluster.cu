@@ -18,8 +18,8 @@ template <typename IO> struct IO2c;
 template <> struct IO2c<float> { using type = float2; };
 template <> struct IO2c<double> { using type = double2; };
 
-__device__ __noinline__ void cl_store_phase_f(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
-__device__ __noinline__ void cl_store_phase_d(double *dst, float2 v) { *dst = (double)phase_atan2(v.y, v.x); }
+__device__ __forceinline__ void cl_store_phase_f(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
+__device__ __forceinline__ void cl_store_phase_d(double *dst, float2 v) { *dst = (double)phase_atan2(v.y, v.x); }
 __device__ __forceinline__ void cl_store_phase(float *dst, float2 v) { cl_store_phase_f(dst, v); }
 __device__ __forceinline__ void cl_store_phase(double *dst, float2 v) { cl_store_phase_d(dst, v); }
 
