@@ -39,8 +39,8 @@ L2_FLUSH_BYTES = 256 << 20
 # padding, and the sources each was captured from
 PROFILES = {
     "pow2": ("scale_block_fp32_fused_64x100x10000.txt", ["fft_core.cuh", "scale_block.cu"]),
-    "smooth": ("mr_scale_block_fp32_fused_smooth_64x100x10000.txt",
-               ["fft_core.cuh", "mixed_radix.cuh", "smooth_kernel.cuh", "smooth.cu", "smooth_fast_a.cu"]),
+    "smooth": ("mr_fixed_scale_block_fp32_fused_smooth_64x100x10000.txt",
+               ["fft_core.cuh", "mixed_radix.cuh", "smooth_kernel.cuh", "smooth.cu", "smooth_fixed.cu"]),
 }
 
 
@@ -739,8 +739,12 @@ def run_plan_workload(args, name):
     if N & (N - 1):
         pair = tuple(info.inlined_pair)
         rad = "x".join(str(r) for r in info.radices if r)
-        kname = (f"mr_scale_block_kernel<{pair[0]}, {pair[1]}> (inlined radix pair; N = {N} = {rad})"
-                 if pair[0] else f"mr_scale_block_kernel<0, 0> (generic mixed radix; N = {N} = {rad})")
+        if info.fixed_kernel:
+            kname = f"mr_fixed_scale_block_kernel (compiled for N = {N} = {rad})"
+        elif pair[0]:
+            kname = f"mr_scale_block_kernel<{pair[0]}, {pair[1]}> (inlined radix pair; N = {N} = {rad})"
+        else:
+            kname = f"mr_scale_block_kernel<0, 0> (generic mixed radix; N = {N} = {rad})"
     elif N <= 16384:
         kname = f"scale_block_kernel<{N},float>"
     else:

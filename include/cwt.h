@@ -164,6 +164,10 @@ typedef struct {
                                (all 0 for powers of two) */
     int inlined_pair[2];    /* smooth N: the radix pair of the inlined kernel that runs
                                it, or 0, 0 for the generic mixed-radix kernel */
+    int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
+                               compiled for exactly this N and radix schedule (10000),
+                               else 0; the forward FFT stays on inlined_pair's kernel */
+    int reserved;
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */

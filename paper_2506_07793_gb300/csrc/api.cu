@@ -136,7 +136,8 @@ const char *cwt_status_str(cwt_status s) {
 
 // the Python binding mirrors this layout
 static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24, "cwt_options layout");
-static_assert(sizeof(cwt_plan_info_t) == 104 && offsetof(cwt_plan_info_t, radices) == 64,
+static_assert(sizeof(cwt_plan_info_t) == 112 && offsetof(cwt_plan_info_t, radices) == 64 &&
+                  offsetof(cwt_plan_info_t, fixed_kernel) == 104,
               "cwt_plan_info_t layout");
 
 cwt_status cwt_options_init(cwt_options *opt) {
@@ -324,6 +325,7 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
             info->inlined_pair[0] = a;
             info->inlined_pair[1] = b;
         }
+        info->fixed_kernel = p->sch.fixed >= 0;
     }
     return CWT_OK;
 }

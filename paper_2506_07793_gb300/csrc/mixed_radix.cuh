@@ -56,6 +56,7 @@ struct MrSchedule {
     int T;           // threads per row (rows per CTA are chosen per launch)
     int np;          // passes
     int fast;        // index of the inlined radix pair that runs it, or -1 (generic)
+    int fixed;       // index of the fixed-length kernel that runs it, or -1
     unsigned mag0;   // ceil(2^32 / (N / R_0)), for the sparse first pass
     MrPass p[kMrMaxPasses];
 };
@@ -268,10 +269,17 @@ __device__ __forceinline__ void mr_butterfly(float2 *v, const MrPass &ps, const 
     dft_r<R, SIGN>(v);
 }
 
+// Linear addressing (LIN): the buffer index spad2(i) = i + i/16 is not
+// linear in i, but spad2(x + 16 m) = spad2(x) + 17 m, so a run of accesses
+// whose stride is a multiple of 16 is one padded base plus constant offsets.
+// The fixed-length kernels (every stride a compile-time constant) take that
+// form wherever it applies; with runtime strides the extra branches cost more
+// than they save, and the runtime-schedule kernels keep the plain form.
+
 // Pass 0 (Ns = 1): inputs from load(k), outputs to the row's buffer.  The
 // dense and sparse forms hold no barrier: rows of one CTA (even of one warp)
 // may take different forms, and mr_row places the barrier after either.
-template <int R, int SIGN, typename Load>
+template <int R, int SIGN, bool LIN = false, typename Load>
 __device__ __forceinline__ void mr_first_body(const MrPass &ps, float2 *__restrict__ sm, int N, int T,
                                               int j, bool active, const Load &load) {
     constexpr int GM = mr_gmax<R>();
@@ -284,8 +292,14 @@ __device__ __forceinline__ void mr_first_body(const MrPass &ps, float2 *__restri
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = load(b + r * nb);
             dft_r<R, SIGN>(v);
+            if constexpr (LIN && R % 16 == 0) {
+                float2 *dst = sm + spad2(b * R);
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[spad2(b * R + r)] = v[r];
+                for (int r = 0; r < R; ++r) dst[spad2(r)] = v[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[spad2(b * R + r)] = v[r];
+            }
         }
     }
 }
@@ -293,7 +307,7 @@ __device__ __forceinline__ void mr_first_body(const MrPass &ps, float2 *__restri
 // Pass 0 when each butterfly meets at most one nonzero input:
 // first_nz(b, nb, mag0, r, x) gives its position r and value x; the R-point
 // DFT is then x exp(SIGN 2 pi i r t / R), t < R.
-template <int R, int SIGN, typename First>
+template <int R, int SIGN, bool LIN = false, typename First>
 __device__ __forceinline__ void mr_first_sparse_body(const MrPass &ps, float2 *__restrict__ sm,
                                                      const float2 *__restrict__ twN, int N, int T, int j,
                                                      bool active, unsigned mag0, const First &first_nz) {
@@ -313,25 +327,39 @@ __device__ __forceinline__ void mr_first_sparse_body(const MrPass &ps, float2 *_
 #pragma unroll
             for (int t = 0; t < R; ++t) v[t] = x;
             mr_twiddle<R>(v, w);
+            if constexpr (LIN && R % 16 == 0) {
+                float2 *dst = sm + spad2(b * R);
 #pragma unroll
-            for (int t = 0; t < R; ++t) sm[spad2(b * R + t)] = v[t];
+                for (int t = 0; t < R; ++t) dst[spad2(t)] = v[t];
+            } else {
+#pragma unroll
+                for (int t = 0; t < R; ++t) sm[spad2(b * R + t)] = v[t];
+            }
         }
     }
 }
 
 // A middle pass: buffer -> registers, barrier, butterflies -> buffer.
-template <int R, int SIGN>
+template <int R, int SIGN, bool LIN = false>
 __device__ __forceinline__ void mr_mid_body(const MrPass &ps, float2 *__restrict__ sm,
                                             const float2 *__restrict__ twN, int N, int T, int j, bool active) {
     constexpr int GM = mr_gmax<R>();
     const int nb = N / R;
+    const bool lin_in = LIN && (nb & 15) == 0, lin_out = LIN && (ps.Ns & 15) == 0;
+    const int nbp = nb + (nb >> 4), nsp = ps.Ns + (ps.Ns >> 4);
     float2 v[GM][R];
 #pragma unroll
     for (int g = 0; g < GM; ++g) {
         const int b = j + g * T;
         if (g < ps.G && active && b < nb) {
+            if (lin_in) {
+                const float2 *src = sm + spad2(b);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[g][r] = sm[spad2(b + r * nb)];
+                for (int r = 0; r < R; ++r) v[g][r] = src[r * nbp];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[g][r] = sm[spad2(b + r * nb)];
+            }
         }
     }
     __syncthreads();
@@ -342,8 +370,14 @@ __device__ __forceinline__ void mr_mid_body(const MrPass &ps, float2 *__restrict
             int q, k;
             mr_butterfly<R, SIGN>(v[g], ps, twN, b, q, k);
             const int base = q * ps.Ns * R + k;
+            if (lin_out) {
+                float2 *dst = sm + spad2(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[spad2(base + r * ps.Ns)] = v[g][r];
+                for (int r = 0; r < R; ++r) dst[r * nsp] = v[g][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[spad2(base + r * ps.Ns)] = v[g][r];
+            }
         }
     }
     __syncthreads();
@@ -459,6 +493,59 @@ __device__ __forceinline__ void mr_row_pair(const MrSchedule &sch, float2 *__res
         if (ps.R == RA) mr_mid_body<RA, SIGN>(ps, sm, twN, N, T, j, active);
         else mr_mid_body<RB, SIGN>(ps, sm, twN, N, T, j, active);
     }
+}
+
+// ---- fixed-length rows --------------------------------------------------------
+// A row length compiled with its whole schedule as constants: N = R_0 ... R_{P-1}
+// (the order the host scheduler picks for N), T threads, and registers for
+// MINB CTAs of T threads per SM.  Every stride, butterfly count and magic
+// divisor is then a compile-time constant, and the passes use linear
+// addressing where the strides allow it.  The host runs one only when the
+// scheduler's MrSchedule for N equals pass() field by field.
+__host__ __device__ constexpr unsigned mr_magic(int d) {
+    return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d);
+}
+
+template <int N_, int T_, int MINB_, int... Rs>
+struct MrFixed {
+    static constexpr int N = N_, T = T_, MINB = MINB_, NP = (int)sizeof...(Rs);
+    __host__ __device__ static constexpr int radix(int p) {  // R_p
+        int i = 0, r = 0;
+        ((r = (i++ == p ? Rs : r)), ...);
+        return r;
+    }
+    __host__ __device__ static constexpr int ns(int p) {
+        int v = 1;
+        for (int i = 0; i < p; ++i) v *= radix(i);
+        return v;
+    }
+    __host__ __device__ static constexpr MrPass pass(int p) {
+        return MrPass{radix(p), (N / radix(p) + T - 1) / T, ns(p), mr_magic(ns(p)), N / (ns(p) * radix(p))};
+    }
+    static constexpr unsigned mag0 = mr_magic(N / radix(0));
+    static_assert(NP >= 2 && NP <= kMrMaxPasses && ns(NP) == N, "N = R_0 ... R_{P-1}");
+    static_assert(T % 32 == 0 && T <= kMrThreads, "whole warps, one CTA per row");
+    __host__ __device__ static constexpr bool fits() {
+        for (int p = 0; p < NP; ++p)
+            if (pass(p).G * radix(p) > kMrPoints && pass(p).G > 1) return false;
+        return true;
+    }
+    static_assert(fits(), "at most 32 values per thread and pass");
+};
+
+// The row of a fixed-length schedule FX (all passes inlined).
+template <class FX, int SIGN, typename Load, typename First>
+__device__ __forceinline__ void mr_row_fixed(float2 *__restrict__ sm, const float2 *__restrict__ twN, int j,
+                                             bool active, bool sparse, const Load &load, const First &first_nz) {
+    constexpr int R0 = FX::radix(0);
+    const MrPass p0 = FX::pass(0);
+    if (sparse) mr_first_sparse_body<R0, SIGN, true>(p0, sm, twN, FX::N, FX::T, j, active, FX::mag0, first_nz);
+    else mr_first_body<R0, SIGN, true>(p0, sm, FX::N, FX::T, j, active, load);
+    __syncthreads();  // pass-0 outputs visible
+    static_for<FX::NP - 1>([&](auto P) {
+        constexpr int p = decltype(P)::value + 1;
+        mr_mid_body<FX::radix(p), SIGN, true>(FX::pass(p), sm, twN, FX::N, FX::T, j, active);
+    });
 }
 
 }  // namespace cwtk

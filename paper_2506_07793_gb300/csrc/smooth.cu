@@ -74,8 +74,6 @@ void enumerate(int rem, int min_r, std::vector<int> &cur, std::vector<std::vecto
     }
 }
 
-unsigned magic_of(int d) { return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d); }
-
 std::atomic<int> g_sm_count[64] = {};
 
 int sm_count() {
@@ -189,11 +187,12 @@ bool mr_schedule(int N, MrSchedule *out) {
         s.p[q].R = R;
         s.p[q].G = (N / R + best.T - 1) / best.T;
         s.p[q].Ns = Ns;
-        s.p[q].mag = magic_of(Ns);
+        s.p[q].mag = mr_magic(Ns);
         s.p[q].tws = N / (Ns * R);
         Ns *= R;
     }
-    s.mag0 = magic_of(N / s.p[0].R);
+    s.mag0 = mr_magic(N / s.p[0].R);
+    s.fixed = mr_fixed_index(s);
     *out = s;
     return true;
 }
@@ -218,6 +217,7 @@ cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p,
     a.sub = p->d;
     a.total_rows = p->C * p->S;
     a.f64 = p->io == CWT_DTYPE_F64;
+    if (p->sch.fixed >= 0) return mr_fixed_sb_launch(p, a, st);
     switch (p->sch.fast) {
 #define CWT_MR_CASE(I, A, B) \
     case I: return mr_sb_launch<A, B>(p, a, st);

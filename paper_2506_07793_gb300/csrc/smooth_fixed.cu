@@ -1,0 +1,52 @@
+// smooth_fixed.cu -- fixed-length scale-block kernels (smooth_kernel.cuh,
+// CWT_MR_FIXED): the row lengths whose whole schedule is compiled in, and the
+// host check that the scheduler's schedule for N is exactly that one.
+#include "smooth_kernel.cuh"
+
+namespace cwtk {
+
+namespace {
+
+template <class FX>
+bool same_schedule(const MrSchedule &s) {
+    if (s.N != FX::N || s.T != FX::T || s.np != FX::NP || s.mag0 != FX::mag0) return false;
+    for (int q = 0; q < FX::NP; ++q) {
+        const MrPass f = FX::pass(q);
+        const MrPass &h = s.p[q];
+        if (h.R != f.R || h.G != f.G || h.Ns != f.Ns || h.mag != f.mag || h.tws != f.tws) return false;
+    }
+    return true;
+}
+
+template <class FX>
+cudaError_t fixed_launch(const MrArgs &a, cudaStream_t st) {
+    static_assert(FX::N <= kMaxFft, "one shared-memory row");
+    static std::atomic<unsigned> done{0};
+    constexpr int smem = (FX::N + (FX::N >> 4)) * 8;
+    cudaError_t e = ensure_smem_attr(mr_fixed_scale_block_kernel<FX>, smem, &done);
+    if (e != cudaSuccess) return e;
+    mr_fixed_scale_block_kernel<FX><<<a.total_rows, FX::T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int mr_fixed_index(const MrSchedule &s) {
+#define CWT_MR_CASE(I, N, T, MINB, ...) \
+    if (same_schedule<MrFixed<N, T, MINB, __VA_ARGS__>>(s)) return I;
+    CWT_MR_FIXED(CWT_MR_CASE)
+#undef CWT_MR_CASE
+    return -1;
+}
+
+cudaError_t mr_fixed_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
+    switch (p->sch.fixed) {
+#define CWT_MR_CASE(I, N, T, MINB, ...) \
+    case I: return fixed_launch<MrFixed<N, T, MINB, __VA_ARGS__>>(a, st);
+        CWT_MR_FIXED(CWT_MR_CASE)
+#undef CWT_MR_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cwtk

@@ -32,13 +32,15 @@ struct MrArgs {
 __device__ __noinline__ inline void mr_phase_f(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
 __device__ __noinline__ inline void mr_phase_d(double *dst, float2 v) { *dst = (double)phase_atan2(v.y, v.x); }
 
-// Fused spectrum product, inverse FFT and epilogue per (channel, scale) row.
-template <int RA, int RB>
-__global__ void __launch_bounds__(kMrThreads, 1)
-mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
+// Fused spectrum product, inverse FFT and epilogue of one (channel, scale)
+// row, shared by the runtime-schedule and fixed-length kernels:
+// run_row(sm, sparse, load, first_nz) runs the inverse FFT of the row held
+// in `sm`.  LIN: the epilogue steps through the buffer by a constant padded
+// stride when T sub is a multiple of 16 (fixed-length kernels).
+template <bool LIN, typename RunRow>
+__device__ __forceinline__ void mr_sb_row(const MrArgs &a, int N, int T, int R0, const RowSlot &rs, int rows,
+                                          const RunRow &run_row) {
     extern __shared__ float2 mrsm[];
-    const int N = sch.N;
-    const RowSlot rs = row_slot(sch, rows, a.total_rows);
     const int row = rs.active ? (int)blockIdx.x * rows + rs.rr : 0;
     const int rr = rs.rr < rows ? rs.rr : 0;
     float2 *sm = mrsm + (size_t)rr * (N + (N >> 4));
@@ -70,11 +72,7 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
         x = make_float2(xv.x * w, xv.y * w);
         return true;
     };
-    const bool sparse = B <= N / sch.p[0].R;
-    if constexpr (RA == 0)
-        mr_row<+1>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
-    else
-        mr_row_pair<+1, RA, RB>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
+    run_row(sm, B <= N / R0, load, first_nz);
     if (!rs.active) return;
     // epilogue: crop to t < n, keep t = sub * o, write the requested outputs
     // (consecutive threads take consecutive o: coalesced stores)
@@ -84,7 +82,7 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
         double2 *oc = (double2 *)a.out_c + obase;
         double *op = (double *)a.out_p + obase, *oph = (double *)a.out_ph + obase;
 #pragma unroll 1
-        for (int o = rs.j; o < n_out; o += sch.T) {
+        for (int o = rs.j; o < n_out; o += T) {
             const float2 v = sm[spad2(o * sub)];
             if (a.out_c) oc[o] = make_double2(v.x, v.y);
             if (a.out_p) op[o] = (double)fmaf(v.x, v.x, v.y * v.y);
@@ -93,16 +91,57 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
     } else {
         float2 *oc = (float2 *)a.out_c + obase;
         float *op = (float *)a.out_p + obase, *oph = (float *)a.out_ph + obase;
+        if (LIN && ((T * sub) & 15) == 0) {
+            // spad2(o sub) advances by spad2(T sub) per step
+            const float2 *src = sm + spad2(rs.j * sub);
+            const int step = spad2(T * sub);
 #pragma unroll 2
-        for (int o = rs.j; o < n_out; o += sch.T) {
-            const float2 v = sm[spad2(o * sub)];
-            if (a.out_c) oc[o] = v;
-            if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
-            if (a.out_ph) mr_phase_f(oph + o, v);
+            for (int o = rs.j; o < n_out; o += T, src += step) {
+                const float2 v = *src;
+                if (a.out_c) oc[o] = v;
+                if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
+                if (a.out_ph) mr_phase_f(oph + o, v);
+            }
+        } else {
+#pragma unroll 2
+            for (int o = rs.j; o < n_out; o += T) {
+                const float2 v = sm[spad2(o * sub)];
+                if (a.out_c) oc[o] = v;
+                if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
+                if (a.out_ph) mr_phase_f(oph + o, v);
+            }
         }
     }
 }
 
+// The runtime-schedule kernel: RA = RB = 0 the generic row, else the inlined
+// radix pair.
+template <int RA, int RB>
+__global__ void __launch_bounds__(kMrThreads, 1)
+mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
+    const RowSlot rs = row_slot(sch, rows, a.total_rows);
+    mr_sb_row<false>(a, sch.N, sch.T, sch.p[0].R, rs, rows,
+                     [&](float2 *sm, bool sparse, const auto &load, const auto &first_nz) {
+                         if constexpr (RA == 0)
+                             mr_row<+1>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
+                         else
+                             mr_row_pair<+1, RA, RB>(sch, sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
+                     });
+}
+
+// The fixed-length kernel: one row of FX::N per CTA of FX::T threads, with
+// registers for FX::MINB such CTAs per SM.
+template <class FX>
+__global__ void __launch_bounds__(FX::T, FX::MINB) mr_fixed_scale_block_kernel(const MrArgs a) {
+    RowSlot rs;
+    rs.rr = 0;
+    rs.j = (int)threadIdx.x;
+    rs.active = (int)blockIdx.x < a.total_rows;
+    mr_sb_row<true>(a, FX::N, FX::T, FX::radix(0), rs, 1,
+                    [&](float2 *sm, bool sparse, const auto &load, const auto &first_nz) {
+                        mr_row_fixed<FX, +1>(sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
+                    });
+}
 
 template <int RA, int RB>
 cudaError_t mr_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
@@ -159,6 +198,16 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
         signal, p->io == CWT_DTYPE_F64, p->n, p->spec, p->twN, p->sch, rows, p->C);
     return cudaGetLastError();
 }
+
+// Fixed-length kernels (index = MrSchedule::fixed, smooth_fixed.cu): index,
+// N, T, CTAs per SM for the register budget, the radices in the scheduler's
+// order.  10000 = 10 s at 1 kHz; two 512-thread CTAs per SM (64 registers)
+// hide the pass barriers of one row behind the other's work.
+#define CWT_MR_FIXED(X) X(0, 10000, 512, 2, 16, 25, 25)
+
+// Index of the fixed-length kernel whose schedule equals s, or -1.
+int mr_fixed_index(const MrSchedule &s);
+cudaError_t mr_fixed_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st);
 
 // The inlined radix pairs (index = MrSchedule::fast), chosen for 2^a 5^b
 // lengths (whole seconds of EEG at 250 / 500 / 1000 Hz), each instantiated in

@@ -45,7 +45,8 @@ class cwt_plan_info_t(ctypes.Structure):
                 ("fold", ctypes.c_int), ("inverse_length", ctypes.c_int), ("device", ctypes.c_int),
                 ("io_dtype", ctypes.c_int), ("output_kinds", ctypes.c_uint),
                 ("workspace_bytes", ctypes.c_size_t), ("bank_ms", ctypes.c_double),
-                ("radices", ctypes.c_int * 8), ("inlined_pair", ctypes.c_int * 2)]
+                ("radices", ctypes.c_int * 8), ("inlined_pair", ctypes.c_int * 2),
+                ("fixed_kernel", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class cwt_epoch(ctypes.Structure):

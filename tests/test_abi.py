@@ -113,7 +113,8 @@ def test_option_struct_layout(lib):
     assert ctypes.sizeof(o) == 64 and type(o).gmw_gamma.offset == 24
     assert o.gmw_gamma == 3.0 and o.decimation == 1
     assert type(o).edge_mode.offset == 20 and o.edge_mode == lib.CWT_EDGE_CYCLIC
-    assert ctypes.sizeof(lib.cwt_plan_info_t) == 104 and lib.cwt_plan_info_t.radices.offset == 64
+    assert ctypes.sizeof(lib.cwt_plan_info_t) == 112 and lib.cwt_plan_info_t.radices.offset == 64
+    assert lib.cwt_plan_info_t.fixed_kernel.offset == 104
     so = lib.cwt_server_options_init()
     assert ctypes.sizeof(so) == 56 and type(so).gmw_gamma.offset == 32
     assert so.gmw_gamma == 3.0 and so.max_streams == 32

@@ -462,16 +462,47 @@ def test_smooth_padding_common_eeg_lengths(lib, n):
     check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
 
 
+FIXED = [
+    # (C, freqs, cycles, dtype, decimation) at n = N = 10000, fs = 1 kHz: the
+    # fixed-length scale-block kernel; bands from narrow (sparse first pass)
+    # to the widest (dense), FP64 I/O, and decimations whose epilogue stride
+    # 512 d is a multiple of 16 (the linear form)
+    (3, np.geomspace(0.5, 450.0, 8), np.linspace(3.0, 12.0, 8), "f32", 1),
+    (2, [0.7, 8.0, 120.0, 480.0], [3.0, 5.0, 9.0, 14.0], "f64", 3),
+    (2, [2.0, 40.0, 300.0], [4.0, 7.0, 10.0], "f32", 7),
+]
+
+
+@pytest.mark.parametrize("case", range(len(FIXED)))
+def test_fixed_length_kernel_every_row(lib, case):
+    """N = 10000 runs on the kernel compiled for that length and schedule;
+    parity with the oracle for every output kind."""
+    C, freqs, cycles, dtype, d = FIXED[case]
+    n, fs = 10000, 1000.0
+    x = eeg(1200 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    t = lib.CWT(C, n, fs, freqs, cycles, outputs=("complex", "power", "phase"), dtype=dtype,
+                decimation=d, pad="smooth")
+    assert t.info.fixed_kernel == 1 and t.info.fft_length == n
+    t.close()
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), dtype=dtype,
+                     decimation=d, pad="smooth")
+    check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=d))
+
+
 def test_smooth_plan_reports_schedule(lib):
     """The fused workload's smooth length N = 10000 runs 16 x 25 x 25 on the
-    inlined (16, 25) kernel; a length outside the pairs runs the generic one."""
+    kernel compiled for that length and schedule (its forward FFT on the
+    inlined (16, 25) kernel); a length outside the pairs runs the generic
+    one."""
     o = lib.cwt_options_init()
     o.pad_policy = lib.CWT_PAD_SMOOTH
-    for n, pair, rad in ((10000, (16, 25), [16, 25, 25]), (3001, (0, 0), None)):
+    for n, pair, rad, fixed in ((10000, (16, 25), [16, 25, 25], 1), (3001, (0, 0), None, 0),
+                                (5000, (8, 25), None, 0)):
         plan = lib.cwt_plan_create(1, n, 1000.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER, o)
         try:
             info = lib.cwt_plan_info(plan)
             assert tuple(info.inlined_pair) == pair
+            assert info.fixed_kernel == fixed
             got = [r for r in info.radices if r]
             assert int(np.prod(got)) == info.fft_length
             if rad is not None:
