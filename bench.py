@@ -119,23 +119,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, x_rows, n_channels, n_scales=None, N=None):
+def cpu_baseline(w, x_rows, n_channels, n_scales=None, N=None, min_seconds=10.0):
     """The FP64 oracle, as it stands, on the host cores: the first n_scales
-    (default all) scales of the first n_channels channels of the same workload,
-    at the padded length N of the timed plan."""
+    (default all) scales of the first channels of the same workload, at the
+    padded length N of the timed plan -- n_channels channels, then one more at a
+    time until at least min_seconds of work (at most every channel given)."""
     import oracle
     from paper_2506_07793_gb300 import cwt_fft_length
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     N = cwt_fft_length(w.samples) if N is None else N
     ns = w.scales if n_scales is None else n_scales
-    rows = [(c, s) for c in range(n_channels) for s in range(0, w.scales, max(1, w.scales // ns))][:n_channels * ns]
-    t0 = time.perf_counter()
-    oracle.cwt_rows(x_rows[:n_channels].astype(np.float64), N, w.fs, w.freqs, w.n_cycles, rows,
-                    threads=cores)
-    dt = time.perf_counter() - t0
-    coeffs = len(rows) * w.n_out
+    scales = list(range(0, w.scales, max(1, w.scales // ns)))[:ns]
+    x64 = x_rows.astype(np.float64)
+    done, dt = 0, 0.0
+    while done < len(x64) and (done < n_channels or dt < min_seconds):
+        take = n_channels if done == 0 else 1
+        rows = [(c, s) for c in range(take) for s in scales]
+        t0 = time.perf_counter()
+        oracle.cwt_rows(x64[done:done + take], N, w.fs, w.freqs, w.n_cycles, rows, threads=cores)
+        dt += time.perf_counter() - t0
+        done += take
+    coeffs = done * len(scales) * w.n_out
     return {"value": coeffs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_channels} of {w.channels} channels x {ns} of {w.scales} scales x "
+            "sample": f"{done} of {w.channels} channels x {len(scales)} of {w.scales} scales x "
                       f"{w.n_out} samples ({coeffs} coefficients), {dt:.2f} s wall"}
 
 
