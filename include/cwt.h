@@ -128,7 +128,9 @@ typedef struct {
     int order;              /* autotuned item order: 0 largest FFT first, 1 input order */
     int tuned;              /* 1 once the autotuner has chosen for this batch shape */
     int reserved;
-    double tune_ms[4];      /* candidate times: (16,0), (32,0), (16,1), (32,1) */
+    double tune_ms[4];      /* candidate times: (16,0), (32,0), (16,1), (32,1); -1 for a
+                               radix-16 candidate the batch rules out (an inverse row
+                               longer than 4096 points, at N_e = 8192 and odd d) */
     long long graph_launches;
     size_t bank_bytes;      /* device bytes of the per-length wavelet banks */
 } cwt_batch_stats;

@@ -173,6 +173,11 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         }
     }
     if (items.empty()) return cudaSuccess;
+    // RI = 16 stages kBThreads * 16 points of inverse rows: only for batches
+    // whose every inverse length fits (an 8192-point row at odd d needs RI = 32)
+    int max_m = 0;
+    for (const BatchItem &it : items) max_m = std::max(max_m, batch_inverse_length(1 << it.log2n, p->d));
+    const bool ri16_ok = max_m <= kBThreads * 16;
     // two orders: input order, and largest FFT first (stable)
     std::vector<BatchItem> sorted = items;
     std::stable_sort(sorted.begin(), sorted.end(),
@@ -244,6 +249,10 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         if (e == cudaSuccess) e = cudaEventCreate(&t1);
         double best = 1e300;
         for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+            if (cands[c][0] == 16 && !ri16_ok) {
+                b->tune_ms[c] = -1.f;  // not a candidate for this batch
+                continue;
+            }
             e = run(cands[c][0], cands[c][1]);  // warm (graph build, upload)
             if (e == cudaSuccess) e = cudaEventRecord(t0, st);
             if (e == cudaSuccess) e = run(cands[c][0], cands[c][1]);

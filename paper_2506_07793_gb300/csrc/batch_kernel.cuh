@@ -13,9 +13,10 @@
 
 namespace cwtk {
 
-constexpr int kBThreads = 512;
-constexpr int kTile = kBThreads * 16;  // 8192 points per item
-constexpr int kMaxBatchLog2 = 13;      // N_e <= kTile
+constexpr int kBThreads = 256;
+constexpr int kTile = 8192;                    // points per item (G channels x N_e)
+constexpr int kTileP = kTile + (kTile >> 4);   // the tile, padded: spectra / forward staging
+constexpr int kMaxBatchLog2 = 13;              // N_e <= kTile
 
 struct BatchItem {
     long long in_off;   // element offset of channel c0 of the epoch in the packed input
@@ -40,10 +41,20 @@ struct BatchArgs {
     int S, d;
 };
 
-// Shared memory: spectra (kTile float2) + staging for kBThreads * RI points
-// (every thread holds RI points of some row in flight), padded 17/16.
+// Shared memory: the item's tile (kTileP float2: the forward FFTs' padded
+// staging, then the G unpadded spectra in place) + staging for the inverse
+// rows, kBThreads * RI points (every thread holds RI points of some row in
+// flight), padded 17/16.  With RI = 16 that is 104 KB, two CTAs per SM.
 template <int RI>
-constexpr int batch_smem() { return (kTile + (kBThreads * RI) * 17 / 16) * 8; }
+constexpr int batch_smem() { return (kTileP + (kBThreads * RI) * 17 / 16) * 8; }
+
+// Inverse length of a row of N_e = N points at decimation d: N / f, f the
+// largest power of two dividing d with N / f >= kMinFft (the spectral fold).
+__host__ __device__ inline int batch_inverse_length(int N, int d) {
+    int fold = 1;
+    while ((d % (2 * fold)) == 0 && N / (2 * fold) >= kMinFft) fold *= 2;
+    return N / fold;
+}
 
 // The kernel for RI = 16 or 32 (defined in batch_k16.cu / batch_k32.cu).
 const void *batch_kernel_ptr(int ri);
@@ -53,11 +64,16 @@ namespace {
 
 __device__ __noinline__ void batch_store_phase(float *dst, float2 v) { *dst = phase_atan2(v.y, v.x); }
 
+// The G forward FFTs of an item: channel g stages its passes in the padded
+// slice spec + g (N + N/16) of the tile; the last pass keeps its outputs in
+// registers, and after a barrier they overwrite the tile as the unpadded
+// spectra spec + g N.  R = kTile / kBThreads, so G N / R = kBThreads threads
+// for every N.
 template <int N>
-__device__ __noinline__ void batch_forward(const BatchArgs &a, const BatchItem &it,
-                                              float2 *spec, float2 *stage) {
-    constexpr int R = N / kBThreads > 16 ? N / kBThreads : 16;
+__device__ __noinline__ void batch_forward(const BatchArgs &a, const BatchItem &it, float2 *spec) {
+    constexpr int R = kTile / kBThreads;
     constexpr int Tf = N / R;
+    static_assert(R <= N, "one pass at least");
     // fields are read once into registers: a and it live in local memory here
     // (this function is not inlined) and stores through generic pointers
     // would otherwise force their reloads
@@ -66,17 +82,29 @@ __device__ __noinline__ void batch_forward(const BatchArgs &a, const BatchItem &
     const int g = threadIdx.x / Tf, j = threadIdx.x % Tf;
     const bool act = g < G;
     const float *x = a.in + it.in_off + (long long)(act ? g : 0) * n;
-    float2 *st = stage + g * FftShape<N, R>::SMEM_F2;
+    float2 *st = spec + g * FftShape<N, R>::SMEM_F2;
     float2 *sp = spec + g * N;
     auto load = [&](int i) -> float2 { return make_float2((act && i < n) ? x[i] : 0.f, 0.f); };
-    auto store = [&](int t, float2 v) { sp[t] = v; };
-    fft_row<N, R, -1>(st, tw, j, load, store);
+    auto store = [&](int t, float2 v) { sp[t] = v; };  // NP = 1: no staging to overwrite
+    float2 v[R];
+    fft_pass0_dense<N, R, -1>(v, j, load);
+    fft_finish<N, R, -1, decltype(store), true>(v, st, tw, j, store);
+    if constexpr (FftShape<N, R>::NP > 1) {
+        __syncthreads();  // every staging read is done before the spectra overwrite it
+#pragma unroll
+        for (int r = 0; r < R; ++r) sp[j + r * (N / R)] = v[r];
+    }
 }
 
+// Rows of M points, RI points per thread: P = kBThreads / (M / RI) rows in
+// flight fill the inverse staging (kBThreads * RI points) exactly, which needs
+// M <= kBThreads * RI; the host takes RI = 16 only for batches whose every
+// inverse length satisfies it.
 template <int M, int RI>
 __device__ __noinline__ void batch_inverse(const BatchArgs &a, const BatchItem &it,
                                               const float2 *spec, float2 *stage, int N, int fold) {
-    constexpr int R = (M / RI) > kBThreads ? M / kBThreads : (M < RI ? M : RI);
+    static_assert(M <= kBThreads * RI, "rows in flight fit the inverse staging");
+    constexpr int R = M < RI ? M : RI;
     constexpr int Ti = M / R;
     constexpr int P = kBThreads / Ti;  // rows in flight
     // fields are read once into registers (see batch_forward)
@@ -150,27 +178,25 @@ template <int RI>
 __device__ __forceinline__ void batch_inverse_dispatch(const BatchArgs &a, const BatchItem &it,
                                                        const float2 *spec, float2 *stage) {
     const int N = 1 << it.log2n;
-    int fold = 1;
-    while ((a.d % (2 * fold)) == 0 && N / (2 * fold) >= kMinFft) fold *= 2;
-    switch (it.log2n - ilog2c(fold)) {
-        case 5: batch_inverse<1 << 5, RI>(a, it, spec, stage, N, fold); break;
-        case 6: batch_inverse<1 << 6, RI>(a, it, spec, stage, N, fold); break;
-        case 7: batch_inverse<1 << 7, RI>(a, it, spec, stage, N, fold); break;
-        case 8: batch_inverse<1 << 8, RI>(a, it, spec, stage, N, fold); break;
-        case 9: batch_inverse<1 << 9, RI>(a, it, spec, stage, N, fold); break;
-        case 10: batch_inverse<1 << 10, RI>(a, it, spec, stage, N, fold); break;
-        case 11: batch_inverse<1 << 11, RI>(a, it, spec, stage, N, fold); break;
-        case 12: batch_inverse<1 << 12, RI>(a, it, spec, stage, N, fold); break;
-        case 13: batch_inverse<1 << 13, RI>(a, it, spec, stage, N, fold); break;
+    const int M = batch_inverse_length(N, a.d);
+    const int fold = N / M;
+    switch (ilog2c(M)) {
+#define CWT_BI_CASE(L)                                                                         \
+    case L:                                                                                    \
+        if constexpr ((1 << L) <= kBThreads * RI) batch_inverse<1 << L, RI>(a, it, spec, stage, N, fold); \
+        break;
+        CWT_BI_CASE(5) CWT_BI_CASE(6) CWT_BI_CASE(7) CWT_BI_CASE(8) CWT_BI_CASE(9)
+        CWT_BI_CASE(10) CWT_BI_CASE(11) CWT_BI_CASE(12) CWT_BI_CASE(13)
+#undef CWT_BI_CASE
         default: break;
     }
 }
 
 template <int RI>
-__global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(kBThreads, 2) batch_kernel(const BatchArgs a) {
     extern __shared__ float2 bsm[];
     float2 *spec = bsm;
-    float2 *stage = bsm + kTile;
+    float2 *stage = bsm + kTileP;
     __shared__ int s_item;
 #pragma unroll 1
     for (;;) {
@@ -180,15 +206,15 @@ __global__ void __launch_bounds__(kBThreads, 1) batch_kernel(const BatchArgs a) 
         if (item >= a.n_items) break;
         const BatchItem it = a.items[item];
         switch (it.log2n) {
-            case 5: batch_forward<1 << 5>(a, it, spec, stage); break;
-            case 6: batch_forward<1 << 6>(a, it, spec, stage); break;
-            case 7: batch_forward<1 << 7>(a, it, spec, stage); break;
-            case 8: batch_forward<1 << 8>(a, it, spec, stage); break;
-            case 9: batch_forward<1 << 9>(a, it, spec, stage); break;
-            case 10: batch_forward<1 << 10>(a, it, spec, stage); break;
-            case 11: batch_forward<1 << 11>(a, it, spec, stage); break;
-            case 12: batch_forward<1 << 12>(a, it, spec, stage); break;
-            case 13: batch_forward<1 << 13>(a, it, spec, stage); break;
+            case 5: batch_forward<1 << 5>(a, it, spec); break;
+            case 6: batch_forward<1 << 6>(a, it, spec); break;
+            case 7: batch_forward<1 << 7>(a, it, spec); break;
+            case 8: batch_forward<1 << 8>(a, it, spec); break;
+            case 9: batch_forward<1 << 9>(a, it, spec); break;
+            case 10: batch_forward<1 << 10>(a, it, spec); break;
+            case 11: batch_forward<1 << 11>(a, it, spec); break;
+            case 12: batch_forward<1 << 12>(a, it, spec); break;
+            case 13: batch_forward<1 << 13>(a, it, spec); break;
             default: break;
         }
         __syncthreads();  // spectra complete before any row reads them

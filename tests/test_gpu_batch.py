@@ -98,6 +98,8 @@ def test_small_ragged_batch_every_row(lib, d):
                 assert complex_err(cx[sl].reshape(C, len(freqs), no)[:, ok], ref[:, ok]).max() <= FP32_TOL
         st = lib.cwt_plan_batch_stats(plan)
         assert st.tuned == 1 and st.items > 0 and st.inverse_radix in (16, 32)
+        if d % 2:  # an 8192-point inverse row: only the 32-point staging holds it
+            assert st.inverse_radix == 32 and st.tune_ms[0] == -1.0 and st.tune_ms[2] == -1.0
     finally:
         lib.cwt_plan_destroy(plan)
 
