@@ -167,7 +167,8 @@ typedef struct {
     int inlined_pair[2];    /* smooth N: the radix pair of the inlined kernel that runs
                                it, or 0, 0 for the generic mixed-radix kernel */
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
-                               compiled for exactly this N and radix schedule (10000),
+                               compiled for exactly this N and radix schedule (10000,
+                               8000, 5000, 4000),
                                else 0; the forward FFT stays on inlined_pair's kernel */
     int reserved;
 } cwt_plan_info_t;

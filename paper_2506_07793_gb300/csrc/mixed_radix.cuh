@@ -497,18 +497,19 @@ __device__ __forceinline__ void mr_row_pair(const MrSchedule &sch, float2 *__res
 
 // ---- fixed-length rows --------------------------------------------------------
 // A row length compiled with its whole schedule as constants: N = R_0 ... R_{P-1}
-// (the order the host scheduler picks for N), T threads, and registers for
-// MINB CTAs of T threads per SM.  Every stride, butterfly count and magic
-// divisor is then a compile-time constant, and the passes use linear
-// addressing where the strides allow it.  The host runs one only when the
-// scheduler's MrSchedule for N equals pass() field by field.
+// (the order the host scheduler picks for N), T threads per row, ROWS rows
+// per CTA, and registers for MINB such CTAs per SM.  Every stride, butterfly
+// count and magic divisor is then a compile-time constant, and the passes use
+// linear addressing where the strides allow it.  The host runs one only when
+// the scheduler's MrSchedule for N equals pass() field by field.
 __host__ __device__ constexpr unsigned mr_magic(int d) {
     return d <= 1 ? 0u : (unsigned)(((1ull << 32) + (unsigned)d - 1) / (unsigned)d);
 }
 
-template <int N_, int T_, int MINB_, int... Rs>
+template <int N_, int T_, int ROWS_, int MINB_, int... Rs>
 struct MrFixed {
-    static constexpr int N = N_, T = T_, MINB = MINB_, NP = (int)sizeof...(Rs);
+    static constexpr int N = N_, T = T_, ROWS = ROWS_, MINB = MINB_, NP = (int)sizeof...(Rs);
+    static constexpr int THREADS = (ROWS * T + 31) / 32 * 32;  // whole warps
     __host__ __device__ static constexpr int radix(int p) {  // R_p
         int i = 0, r = 0;
         ((r = (i++ == p ? Rs : r)), ...);
@@ -524,7 +525,7 @@ struct MrFixed {
     }
     static constexpr unsigned mag0 = mr_magic(N / radix(0));
     static_assert(NP >= 2 && NP <= kMrMaxPasses && ns(NP) == N, "N = R_0 ... R_{P-1}");
-    static_assert(T % 32 == 0 && T <= kMrThreads, "whole warps, one CTA per row");
+    static_assert(ROWS >= 1 && THREADS <= kMrThreads, "one CTA holds ROWS rows");
     __host__ __device__ static constexpr bool fits() {
         for (int p = 0; p < NP; ++p)
             if (pass(p).G * radix(p) > kMrPoints && pass(p).G > 1) return false;

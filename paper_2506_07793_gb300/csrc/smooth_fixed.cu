@@ -22,18 +22,20 @@ template <class FX>
 cudaError_t fixed_launch(const MrArgs &a, cudaStream_t st) {
     static_assert(FX::N <= kMaxFft, "one shared-memory row");
     static std::atomic<unsigned> done{0};
-    constexpr int smem = (FX::N + (FX::N >> 4)) * 8;
+    constexpr int smem = FX::ROWS * (FX::N + (FX::N >> 4)) * 8;
+    static_assert(smem <= kMrMaxSmem, "shared memory of one CTA");
     cudaError_t e = ensure_smem_attr(mr_fixed_scale_block_kernel<FX>, smem, &done);
     if (e != cudaSuccess) return e;
-    mr_fixed_scale_block_kernel<FX><<<a.total_rows, FX::T, smem, st>>>(a);
+    const int grid = (a.total_rows + FX::ROWS - 1) / FX::ROWS;
+    mr_fixed_scale_block_kernel<FX><<<grid, FX::THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 int mr_fixed_index(const MrSchedule &s) {
-#define CWT_MR_CASE(I, N, T, MINB, ...) \
-    if (same_schedule<MrFixed<N, T, MINB, __VA_ARGS__>>(s)) return I;
+#define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \
+    if (same_schedule<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(s)) return I;
     CWT_MR_FIXED(CWT_MR_CASE)
 #undef CWT_MR_CASE
     return -1;
@@ -41,8 +43,8 @@ int mr_fixed_index(const MrSchedule &s) {
 
 cudaError_t mr_fixed_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
     switch (p->sch.fixed) {
-#define CWT_MR_CASE(I, N, T, MINB, ...) \
-    case I: return fixed_launch<MrFixed<N, T, MINB, __VA_ARGS__>>(a, st);
+#define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \
+    case I: return fixed_launch<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(a, st);
         CWT_MR_FIXED(CWT_MR_CASE)
 #undef CWT_MR_CASE
         default: return cudaErrorInvalidValue;

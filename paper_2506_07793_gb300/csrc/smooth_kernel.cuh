@@ -129,15 +129,15 @@ mr_scale_block_kernel(const MrArgs a, const MrSchedule sch, int rows) {
                      });
 }
 
-// The fixed-length kernel: one row of FX::N per CTA of FX::T threads, with
-// registers for FX::MINB such CTAs per SM.
+// The fixed-length kernel: FX::ROWS rows of FX::N points per CTA, FX::T
+// threads each, with registers for FX::MINB such CTAs per SM.
 template <class FX>
-__global__ void __launch_bounds__(FX::T, FX::MINB) mr_fixed_scale_block_kernel(const MrArgs a) {
+__global__ void __launch_bounds__(FX::THREADS, FX::MINB) mr_fixed_scale_block_kernel(const MrArgs a) {
     RowSlot rs;
-    rs.rr = 0;
-    rs.j = (int)threadIdx.x;
-    rs.active = (int)blockIdx.x < a.total_rows;
-    mr_sb_row<true>(a, FX::N, FX::T, FX::radix(0), rs, 1,
+    rs.rr = (int)threadIdx.x / FX::T;
+    rs.j = (int)threadIdx.x - rs.rr * FX::T;
+    rs.active = rs.rr < FX::ROWS && (int)blockIdx.x * FX::ROWS + rs.rr < a.total_rows;
+    mr_sb_row<true>(a, FX::N, FX::T, FX::radix(0), rs, FX::ROWS,
                     [&](float2 *sm, bool sparse, const auto &load, const auto &first_nz) {
                         mr_row_fixed<FX, +1>(sm, a.twN, rs.j, rs.active, sparse, load, first_nz);
                     });
@@ -200,10 +200,15 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
 }
 
 // Fixed-length kernels (index = MrSchedule::fixed, smooth_fixed.cu): index,
-// N, T, CTAs per SM for the register budget, the radices in the scheduler's
-// order.  10000 = 10 s at 1 kHz; two 512-thread CTAs per SM (64 registers)
-// hide the pass barriers of one row behind the other's work.
-#define CWT_MR_FIXED(X) X(0, 10000, 512, 2, 16, 25, 25)
+// N, T, rows per CTA, CTAs per SM for the register budget, the radices in the
+// scheduler's order.  Whole seconds of EEG at 250 / 500 / 1000 Hz; the CTAs
+// per SM were measured per length (several CTAs per SM hide one row's pass
+// barriers behind the others' work).
+#define CWT_MR_FIXED(X)                    \
+    X(0, 10000, 512, 1, 2, 16, 25, 25)     \
+    X(1, 8000, 512, 1, 2, 20, 20, 20)      \
+    X(2, 5000, 256, 1, 4, 8, 25, 25)       \
+    X(3, 4000, 256, 1, 4, 10, 20, 20)
 
 // Index of the fixed-length kernel whose schedule equals s, or -1.
 int mr_fixed_index(const MrSchedule &s);

@@ -463,22 +463,28 @@ def test_smooth_padding_common_eeg_lengths(lib, n):
 
 
 FIXED = [
-    # (C, freqs, cycles, dtype, decimation) at n = N = 10000, fs = 1 kHz: the
-    # fixed-length scale-block kernel; bands from narrow (sparse first pass)
-    # to the widest (dense), FP64 I/O, and decimations whose epilogue stride
-    # 512 d is a multiple of 16 (the linear form)
-    (3, np.geomspace(0.5, 450.0, 8), np.linspace(3.0, 12.0, 8), "f32", 1),
-    (2, [0.7, 8.0, 120.0, 480.0], [3.0, 5.0, 9.0, 14.0], "f64", 3),
-    (2, [2.0, 40.0, 300.0], [4.0, 7.0, 10.0], "f32", 7),
+    # (n = N, C, freqs, cycles, dtype, decimation) at fs = 1 kHz: the
+    # fixed-length scale-block kernels; bands from narrow (sparse first pass)
+    # to the widest (dense), FP64 I/O, and decimations with and without a
+    # linear epilogue stride (T d a multiple of 16)
+    (10000, 3, np.geomspace(0.5, 450.0, 8), np.linspace(3.0, 12.0, 8), "f32", 1),
+    (10000, 2, [0.7, 8.0, 120.0, 480.0], [3.0, 5.0, 9.0, 14.0], "f64", 3),
+    (10000, 2, [2.0, 40.0, 300.0], [4.0, 7.0, 10.0], "f32", 7),
+    (8000, 3, np.geomspace(0.5, 450.0, 6), np.linspace(3.0, 12.0, 6), "f32", 1),
+    (8000, 2, [1.0, 60.0, 400.0], [4.0, 7.0, 12.0], "f64", 5),
+    (5000, 3, np.geomspace(1.0, 450.0, 6), np.linspace(3.0, 12.0, 6), "f32", 1),
+    (5000, 2, [0.9, 30.0, 250.0], [3.0, 7.0, 10.0], "f32", 3),
+    (4000, 3, np.geomspace(1.0, 450.0, 6), np.linspace(3.0, 12.0, 6), "f64", 1),
+    (4000, 2, [2.0, 45.0, 350.0], [5.0, 7.0, 11.0], "f32", 9),
 ]
 
 
 @pytest.mark.parametrize("case", range(len(FIXED)))
 def test_fixed_length_kernel_every_row(lib, case):
-    """N = 10000 runs on the kernel compiled for that length and schedule;
-    parity with the oracle for every output kind."""
-    C, freqs, cycles, dtype, d = FIXED[case]
-    n, fs = 10000, 1000.0
+    """N = 10000, 8000, 5000, 4000 run on the kernels compiled for that
+    length and schedule; parity with the oracle for every output kind."""
+    n, C, freqs, cycles, dtype, d = FIXED[case]
+    fs = 1000.0
     x = eeg(1200 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
     t = lib.CWT(C, n, fs, freqs, cycles, outputs=("complex", "power", "phase"), dtype=dtype,
                 decimation=d, pad="smooth")
@@ -492,16 +498,18 @@ def test_fixed_length_kernel_every_row(lib, case):
 def test_smooth_plan_reports_schedule(lib):
     """The fused workload's smooth length N = 10000 runs 16 x 25 x 25 on the
     kernel compiled for that length and schedule (its forward FFT on the
-    inlined (16, 25) kernel); a length outside the pairs runs the generic
-    one."""
+    inlined (16, 25) kernel), and so do 8000, 5000 and 4000; 2000 runs on an
+    inlined pair, and a length outside the pairs runs the generic one."""
     o = lib.cwt_options_init()
     o.pad_policy = lib.CWT_PAD_SMOOTH
     for n, pair, rad, fixed in ((10000, (16, 25), [16, 25, 25], 1), (3001, (0, 0), None, 0),
-                                (5000, (8, 25), None, 0)):
+                                (5000, (8, 25), [8, 25, 25], 1), (8000, (20, 25), [20, 20, 20], 1),
+                                (4000, (10, 20), [10, 20, 20], 1), (2000, None, None, 0)):
         plan = lib.cwt_plan_create(1, n, 1000.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER, o)
         try:
             info = lib.cwt_plan_info(plan)
-            assert tuple(info.inlined_pair) == pair
+            if pair is not None:
+                assert tuple(info.inlined_pair) == pair
             assert info.fixed_kernel == fixed
             got = [r for r in info.radices if r]
             assert int(np.prod(got)) == info.fft_length
