@@ -168,7 +168,7 @@ typedef struct {
                                it, or 0, 0 for the generic mixed-radix kernel */
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
                                compiled for exactly this N and radix schedule (10000,
-                               8000, 5000, 4000),
+                               8000, 5000, 4000, 2500, 2000, 1000, 500),
                                else 0; the forward FFT stays on inlined_pair's kernel */
     int reserved;
 } cwt_plan_info_t;

@@ -208,7 +208,11 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
     X(0, 10000, 512, 1, 2, 16, 25, 25)     \
     X(1, 8000, 512, 1, 2, 20, 20, 20)      \
     X(2, 5000, 256, 1, 4, 8, 25, 25)       \
-    X(3, 4000, 256, 1, 4, 10, 20, 20)
+    X(3, 4000, 256, 1, 4, 10, 20, 20)      \
+    X(4, 2500, 125, 2, 3, 10, 10, 25)      \
+    X(5, 2000, 100, 2, 4, 10, 10, 20)      \
+    X(6, 1000, 50, 5, 4, 10, 10, 10)       \
+    X(7, 500, 25, 10, 3, 20, 25)
 
 // Index of the fixed-length kernel whose schedule equals s, or -1.
 int mr_fixed_index(const MrSchedule &s);

@@ -449,11 +449,13 @@ def test_linear_edges_equal_linear_convolution(lib, case):
     check({"complex": res["complex"]}, lin)
 
 
-@pytest.mark.parametrize("n", [250, 500, 1000, 1600, 2000, 2500, 3200, 5000, 6400, 8000])
+@pytest.mark.parametrize("n", [200, 250, 320, 400, 500, 1000, 1600, 2000, 2500, 3200, 5000, 6400, 8000])
 def test_smooth_padding_common_eeg_lengths(lib, n):
-    """Whole seconds of EEG at 250 / 500 / 1000 Hz: 2^a 5^b lengths, which the
-    scheduler runs on the inlined radix-pair kernels (every pair at least once
-    over this list) -- parity with the oracle at that N."""
+    """2^a 5^b lengths (whole seconds of EEG at 250 / 500 / 1000 Hz among
+    them): the scale block runs on a fixed-length kernel (500 ... 8000) or on
+    an inlined radix pair (every pair that some smooth length schedules at
+    least once over this list: 200, 250, 320, 400, 1600, 3200, 6400), the
+    forward FFT on the pair -- parity with the oracle at that N."""
     fs = 1000.0
     freqs, cycles = [3.0, 20.0, 90.0], [5.0, 7.0, 9.0]
     x = eeg(1010 + n, 2, n, fs, np.float32)
@@ -476,13 +478,19 @@ FIXED = [
     (5000, 2, [0.9, 30.0, 250.0], [3.0, 7.0, 10.0], "f32", 3),
     (4000, 3, np.geomspace(1.0, 450.0, 6), np.linspace(3.0, 12.0, 6), "f64", 1),
     (4000, 2, [2.0, 45.0, 350.0], [5.0, 7.0, 11.0], "f32", 9),
+    (2500, 3, np.geomspace(2.0, 450.0, 5), np.linspace(3.0, 12.0, 5), "f32", 1),   # 2 rows per CTA
+    (2000, 5, [3.0, 40.0, 300.0], [4.0, 7.0, 10.0], "f64", 2),                     # odd row count
+    (1000, 7, np.geomspace(4.0, 450.0, 3), [5.0, 7.0, 12.0], "f32", 1),            # 5 rows per CTA
+    (500, 3, [10.0, 100.0, 400.0, 480.0], [6.0, 7.0, 9.0, 12.0], "f32", 4),         # 10 rows per CTA
 ]
 
 
 @pytest.mark.parametrize("case", range(len(FIXED)))
 def test_fixed_length_kernel_every_row(lib, case):
-    """N = 10000, 8000, 5000, 4000 run on the kernels compiled for that
-    length and schedule; parity with the oracle for every output kind."""
+    """N = 10000, 8000, 5000, 4000, 2500, 2000, 1000 and 500 run on the
+    kernels compiled for that length and schedule (several rows per CTA below
+    4000, row counts that leave a CTA partly idle); parity with the oracle
+    for every output kind."""
     n, C, freqs, cycles, dtype, d = FIXED[case]
     fs = 1000.0
     x = eeg(1200 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
@@ -498,13 +506,15 @@ def test_fixed_length_kernel_every_row(lib, case):
 def test_smooth_plan_reports_schedule(lib):
     """The fused workload's smooth length N = 10000 runs 16 x 25 x 25 on the
     kernel compiled for that length and schedule (its forward FFT on the
-    inlined (16, 25) kernel), and so do 8000, 5000 and 4000; 2000 runs on an
-    inlined pair, and a length outside the pairs runs the generic one."""
+    inlined (16, 25) kernel), and so do 8000, 5000, 4000 and 2000; 1600 and
+    250 run on inlined pairs, and a length outside the pairs runs the generic
+    one."""
     o = lib.cwt_options_init()
     o.pad_policy = lib.CWT_PAD_SMOOTH
     for n, pair, rad, fixed in ((10000, (16, 25), [16, 25, 25], 1), (3001, (0, 0), None, 0),
                                 (5000, (8, 25), [8, 25, 25], 1), (8000, (20, 25), [20, 20, 20], 1),
-                                (4000, (10, 20), [10, 20, 20], 1), (2000, None, None, 0)):
+                                (4000, (10, 20), [10, 20, 20], 1), (2000, (10, 20), [10, 10, 20], 1),
+                                (1600, (10, 16), None, 0), (250, (10, 25), None, 0)):
         plan = lib.cwt_plan_create(1, n, 1000.0, [10.0], [7.0], 0, lib.CWT_OUT_POWER, o)
         try:
             info = lib.cwt_plan_info(plan)
