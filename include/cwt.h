@@ -189,6 +189,20 @@ cwt_status cwt_options_init(cwt_options *opt);
  * thread-block cluster; SMOOTH: 2^14).  Host-only; no CUDA call. */
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 
+/* The schedule the mixed-radix kernels run for a 2,3,5,7-smooth length n_fft
+ * that is not a power of two (Section "Fast Fourier transform"), as
+ * cwt_plan_info reports it for a plan of that length: radices[8] the inverse
+ * FFT's passes in order, 0-terminated; *threads the threads per row;
+ * inlined_pair[2] the radix pair of the inlined kernel, or 0, 0 for the
+ * generic one; *fixed_kernel 1 when the scale block runs from a kernel
+ * compiled for exactly this length and schedule.  Outputs are host memory
+ * owned by the caller.  CWT_EINVAL for a NULL output; CWT_EUNSUPPORTED when
+ * n_fft is a power of two, not 2,3,5,7-smooth, outside [32, 16384] or one of
+ * the lengths no schedule covers (see cwt_pad_policy).  Host-only; no CUDA
+ * call. */
+cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlined_pair,
+                               int *fixed_kernel);
+
 /*
  * cwt_plan_create -- validate, pick N, allocate the plan's device memory on
  * the current CUDA device and generate the wavelet bank there in FP64

@@ -298,6 +298,21 @@ cwt_status cwt_plan_destroy(cwt_plan p) {
     return CWT_OK;
 }
 
+namespace {
+
+// radices[8] (0-terminated), the inlined pair (0, 0: generic) and the
+// fixed-kernel flag of a mixed-radix schedule; radices and pair pre-zeroed.
+void describe_schedule(const cwtk::MrSchedule &sch, int *radices, int *pair, int *fixed) {
+    for (int q = 0; q < sch.np && q < 7; ++q) radices[q] = sch.p[q].R;
+#define CWT_MR_CASE(I, A, B) \
+    if (sch.fast == I) pair[0] = A, pair[1] = B;
+    CWT_MR_FAST_PAIRS(CWT_MR_CASE)
+#undef CWT_MR_CASE
+    *fixed = sch.fixed >= 0;
+}
+
+}  // namespace
+
 cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     if (!p || !info) return CWT_EINVAL;
     std::memset(info, 0, sizeof(*info));
@@ -314,19 +329,19 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->output_kinds = p->outputs;
     info->workspace_bytes = p->bytes + p->stage_bytes;
     info->bank_ms = p->bank_ms;
-    if (p->mr) {
-        for (int q = 0; q < p->sch.np && q < 7; ++q) info->radices[q] = p->sch.p[q].R;
-        if (p->sch.fast >= 0) {
-            int a = 0, b = 0;
-#define CWT_MR_CASE(I, A, B) \
-    if (p->sch.fast == I) a = A, b = B;
-            CWT_MR_FAST_PAIRS(CWT_MR_CASE)
-#undef CWT_MR_CASE
-            info->inlined_pair[0] = a;
-            info->inlined_pair[1] = b;
-        }
-        info->fixed_kernel = p->sch.fixed >= 0;
-    }
+    if (p->mr) describe_schedule(p->sch, info->radices, info->inlined_pair, &info->fixed_kernel);
+    return CWT_OK;
+}
+
+cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlined_pair,
+                               int *fixed_kernel) {
+    if (!radices || !threads || !inlined_pair || !fixed_kernel) return CWT_EINVAL;
+    cwtk::MrSchedule sch;
+    if (is_pow2(n_fft) || !cwtk::mr_schedule(n_fft, &sch)) return CWT_EUNSUPPORTED;
+    for (int q = 0; q < 8; ++q) radices[q] = 0;
+    inlined_pair[0] = inlined_pair[1] = 0;
+    describe_schedule(sch, radices, inlined_pair, fixed_kernel);
+    *threads = sch.T;
     return CWT_OK;
 }
 

@@ -94,6 +94,7 @@ def _sig(name, res, args):
 _sig("cwt_status_str", ctypes.c_char_p, [ctypes.c_int])
 _sig("cwt_options_init", ctypes.c_int, [ctypes.POINTER(cwt_options)])
 _sig("cwt_fft_length", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip])
+_sig("cwt_smooth_schedule", ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip, _ip])
 _sig("cwt_plan_create", ctypes.c_int,
      [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, _dp,
       ctypes.c_int, ctypes.c_uint, ctypes.POINTER(cwt_options)])
@@ -177,6 +178,16 @@ def cwt_fft_length(samples, pad_policy=CWT_PAD_POW2):
     n = ctypes.c_int(0)
     _check(_lib.cwt_fft_length(int(samples), int(pad_policy), ctypes.byref(n)), "cwt_fft_length")
     return n.value
+
+
+def cwt_smooth_schedule(n_fft):
+    """(radices, threads per row, inlined pair, fixed_kernel) of a smooth length."""
+    rad = (ctypes.c_int * 8)()
+    pair = (ctypes.c_int * 2)()
+    t, fixed = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.cwt_smooth_schedule(int(n_fft), rad, ctypes.byref(t), pair, ctypes.byref(fixed)),
+           "cwt_smooth_schedule")
+    return [r for r in rad if r], t.value, (pair[0], pair[1]), fixed.value
 
 
 def cwt_plan_create(channels, samples, fs, freqs_hz, n_cycles, wavelet=CWT_WAVELET_MORLET,

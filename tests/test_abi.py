@@ -156,3 +156,55 @@ def test_null_plan_calls(lib):
     assert so.cwt_plan_info(None, None) == lib.CWT_EINVAL
     so.cwt_plan_last_error.restype = ctypes.c_char_p
     assert so.cwt_plan_last_error(None) == b""
+
+
+# The fixed-length kernels run only when the host scheduler picks exactly the
+# schedule they were compiled for: pin that choice (and the inlined pair of
+# the forward FFT) for each of them, on the host.
+FIXED_SCHEDULES = {
+    10000: ([16, 25, 25], 512, (16, 25)),
+    8000: ([20, 20, 20], 512, (20, 25)),
+    5000: ([8, 25, 25], 256, (8, 25)),
+    4000: ([10, 20, 20], 256, (10, 20)),
+    2500: ([10, 10, 25], 125, (10, 25)),
+    2000: ([10, 10, 20], 100, (10, 20)),
+    1000: ([10, 10, 10], 50, (10, 16)),
+    500: ([20, 25], 25, (20, 25)),
+}
+
+
+@pytest.mark.parametrize("N", sorted(FIXED_SCHEDULES))
+def test_fixed_length_kernels_are_scheduled(lib, N):
+    rad, threads, pair, fixed = lib.cwt_smooth_schedule(N)
+    assert (rad, threads, pair, fixed) == FIXED_SCHEDULES[N] + (1,)
+
+
+def test_smooth_schedules_on_the_host(lib):
+    """Every schedulable smooth length below 16384: passes multiply to N, at
+    most 32 values per thread and pass, T <= 512, and the pair kernels only
+    where the pair's radices suffice; the lengths no schedule covers are
+    refused."""
+    seen_fixed = set()
+    for N in range(32, 16385):
+        x = N
+        for f in (2, 3, 5, 7):
+            while x % f == 0:
+                x //= f
+        if x != 1 or (N & (N - 1)) == 0:
+            continue
+        try:
+            rad, T, pair, fixed = lib.cwt_smooth_schedule(N)
+        except lib.CWTError as e:
+            assert e.status == lib.CWT_EUNSUPPORTED and 14175 <= N <= 16200, N
+            continue
+        assert int(np.prod(rad)) == N and 1 <= T <= 512 and len(rad) >= 2
+        for R in rad:
+            assert 4 <= R <= 32 and (-(-(N // R) // T)) * R <= max(32, R), (N, rad, T)
+        if pair != (0, 0):
+            assert set(rad) <= set(pair), (N, rad, pair)
+        if fixed:
+            seen_fixed.add(N)
+    assert seen_fixed == set(FIXED_SCHEDULES)
+    for N in (1024, 3001 * 7 + 1, 20000, 16):
+        with pytest.raises(lib.CWTError):
+            lib.cwt_smooth_schedule(N)
