@@ -1,0 +1,110 @@
+"""Host-side model of the mixed-radix row (no GPU): the Stockham passes, with
+the indexing the smooth-length kernels use, run in numpy under the schedules
+the library's scheduler picks (cwt_smooth_schedule), must reproduce the DFT;
+the magic divisors must give exact quotients for every butterfly; and the
+padded shared-memory index must satisfy the identities that the fixed-length
+kernels' linear addressing relies on.
+
+The pass structure (Section "Fast Fourier transform": 2,3,5,7-smooth lengths):
+pass p has radix R and Ns = R_0 ... R_{p-1}; butterfly b < N/R takes the
+inputs b + r N/R, multiplies input r by w^r with w = exp(SIGN 2 pi i k / (Ns R))
+and k = b mod Ns, runs an R-point DFT and writes output r to
+(b - k) R + k + r Ns.
+"""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_07793_gb300 as p
+    return p
+
+
+LENGTHS = [35, 98, 250, 500, 1000, 1215, 2000, 2401, 2500, 3024, 4000, 5000, 6000, 7500, 8000,
+           10000, 12000, 14000]
+
+
+def stockham(x, radices, sign):
+    """The kernels' pass sequence on one row (complex128)."""
+    N = len(x)
+    cur = np.asarray(x, dtype=np.complex128).copy()
+    Ns = 1
+    for R in radices:
+        nb = N // R
+        b = np.arange(nb)
+        k = b % Ns
+        v = np.stack([cur[b + r * nb] for r in range(R)])              # [R][nb]
+        w = np.exp(sign * 2j * np.pi * k / (Ns * R))
+        v = v * w[None, :] ** np.arange(R)[:, None]                   # twiddles w^r
+        F = np.exp(sign * 2j * np.pi * np.outer(np.arange(R), np.arange(R)) / R)
+        y = F @ v                                                     # R-point DFT
+        out = np.empty_like(cur)
+        for r in range(R):
+            out[(b - k) * R + k + r * Ns] = y[r]
+        cur = out
+        Ns *= R
+    return cur
+
+
+@pytest.mark.parametrize("N", LENGTHS)
+def test_scheduled_passes_compute_the_dft(lib, N):
+    radices, T, pair, fixed = lib.cwt_smooth_schedule(N)
+    assert int(np.prod(radices)) == N
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    # forward (SIGN = -1) and inverse (SIGN = +1, unnormalised; the bank carries 1/N)
+    np.testing.assert_allclose(stockham(x, radices, -1), np.fft.fft(x), rtol=0, atol=1e-9 * N)
+    np.testing.assert_allclose(stockham(x, radices, +1), np.fft.ifft(x) * N, rtol=0, atol=1e-9 * N)
+
+
+def magic(d):
+    """ceil(2^32 / d), 0 for d = 1: the divisor constant of the kernels."""
+    return 0 if d <= 1 else ((1 << 32) + d - 1) // d
+
+
+@pytest.mark.parametrize("N", LENGTHS)
+def test_magic_divisors_are_exact(lib, N):
+    """q = umulhi(b, ceil(2^32 / Ns)) equals b // Ns for every butterfly b of
+    every pass (b < N/R < 2^14, Ns <= 2^13: division by invariant integers),
+    and the narrow-band first pass's divisions by N/R_0 of values below 2N."""
+    radices, _, _, _ = lib.cwt_smooth_schedule(N)
+    Ns = 1
+    for R in radices:
+        nb = N // R
+        b = np.arange(nb, dtype=np.uint64)
+        if Ns > 1:
+            q = (b * np.uint64(magic(Ns))) >> np.uint64(32)
+            np.testing.assert_array_equal(q, b // np.uint64(Ns))
+        Ns *= R
+    # first pass, narrow band: b - b0 + N (mod nb) and (e - b) / nb, both below 2N
+    nb0 = N // radices[0]
+    d = np.arange(0, 2 * N, dtype=np.uint64)
+    q = (d * np.uint64(magic(nb0))) >> np.uint64(32)
+    np.testing.assert_array_equal(q, d // np.uint64(nb0))
+
+
+def spad2(i):
+    return i + (i >> 4)
+
+
+def test_padded_index_identities():
+    """spad2(i) = i + i/16 (one pad slot every 16 float2).  A run of accesses
+    with a stride that is a multiple of 16 is one padded base plus constant
+    offsets, spad2(x + 16 m) = spad2(x) + 17 m; a first-pass butterfly of a
+    radix that is a multiple of 16 writes spad2(b R) + spad2(r)."""
+    x = np.arange(0, 20000)
+    for m in (1, 2, 25, 400, 625):
+        np.testing.assert_array_equal(spad2(x + 16 * m), spad2(x) + 17 * m)
+    b = np.arange(0, 700)
+    for R in (16, 32):
+        for r in range(R):
+            np.testing.assert_array_equal(spad2(b * R + r), spad2(b * R) + spad2(r))
+    # the strides of the 10000-point fixed kernel (16 x 25 x 25) are all multiples of 16
+    N, Ns = 10000, 1
+    for R in (16, 25, 25):
+        if Ns > 1:
+            assert (N // R) % 16 == 0 and Ns % 16 == 0
+        Ns *= R
