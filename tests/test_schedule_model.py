@@ -108,3 +108,57 @@ def test_padded_index_identities():
         if Ns > 1:
             assert (N // R) % 16 == 0 and Ns % 16 == 0
         Ns *= R
+
+
+def pow2_radices(N, R):
+    """Pass radices of a power-of-two row with R points per thread: the
+    leftover factor 2^(log2 N mod log2 R) first (or R), then R per pass."""
+    L, r = N.bit_length() - 1, R.bit_length() - 1
+    R0 = 1 << (L % r) if L % r else R
+    return [R0] + [R] * ((L - (R0.bit_length() - 1)) // r)
+
+
+@pytest.mark.parametrize("N,R", [(32, 16), (512, 16), (2048, 16), (8192, 16), (8192, 32),
+                                 (16384, 32)])
+def test_power_of_two_passes_compute_the_dft(N, R):
+    radices = pow2_radices(N, R)
+    assert int(np.prod(radices)) == N and all(q <= R for q in radices)
+    rng = np.random.default_rng(N + R)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    np.testing.assert_allclose(stockham(x, radices, -1), np.fft.fft(x), rtol=0, atol=1e-9 * N)
+    np.testing.assert_allclose(stockham(x, radices, +1), np.fft.ifft(x) * N, rtol=0, atol=1e-9 * N)
+
+
+@pytest.mark.parametrize("N,f", [(64, 2), (1024, 4), (4096, 8), (16384, 16)])
+def test_spectral_fold_gives_every_fth_sample(N, f):
+    """Decimation by a power-of-two factor f: the N/f-point inverse DFT of the
+    folded spectrum Y'[j] = sum_q Y[j + q N/f] is exactly every f-th sample of
+    the N-point inverse DFT (up to the 1/N vs f/N scaling)."""
+    rng = np.random.default_rng(N * f)
+    Y = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    M = N // f
+    folded = Y.reshape(f, M).sum(axis=0)
+    np.testing.assert_allclose(np.fft.ifft(folded) / f, np.fft.ifft(Y)[::f], rtol=0, atol=1e-12)
+
+
+def test_narrow_band_first_pass_position():
+    """Pass 0 with a band [b0, b0 + B) (mod N) no wider than nb = N/R_0: the
+    inputs b + r nb of butterfly b meet the band at most once, at
+    e = b0 + ((b - b0) mod nb) (mod N) when (b - b0) mod nb < B, in position
+    r = (e - b) / nb -- brute force over every butterfly."""
+    rng = np.random.default_rng(7)
+    for N, R0 in ((10000, 16), (5000, 8), (2000, 10), (16384, 16), (500, 20)):
+        nb = N // R0
+        for _ in range(20):
+            b0 = int(rng.integers(0, N))
+            B = int(rng.integers(1, nb + 1))
+            band = set(((b0 + np.arange(B)) % N).tolist())
+            for b in range(nb):
+                hits = [r for r in range(R0) if b + r * nb in band]
+                u = (b - b0) % nb
+                if u < B:
+                    e = (b0 + u) % N
+                    assert e % nb == b % nb and e >= b
+                    assert hits == [(e - b) // nb]
+                else:
+                    assert hits == []
