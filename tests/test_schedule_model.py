@@ -162,3 +162,30 @@ def test_narrow_band_first_pass_position():
                     assert hits == [(e - b) // nb]
                 else:
                     assert hits == []
+
+
+@pytest.mark.parametrize("CL,NL", [(2, 64), (4, 256), (8, 512), (8, 16384)])
+def test_cluster_decomposition(CL, NL):
+    """Rows of N = CL NL points on a cluster of CL CTAs: with k = c + CL m and
+    t = t1 + NL t2, X[t1 + NL t2] = sum_c w_CL^(c t2) w_N^(c t1) A_c[t1], A_c
+    the NL-point DFT of residue class c; CTA c emits t1 in [c NL/CL,
+    (c+1) NL/CL) for every t2, so the CTAs' outputs cover the row once."""
+    N = CL * NL
+    rng = np.random.default_rng(CL * NL)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for sign, ref in ((-1, np.fft.fft(x)), (+1, np.fft.ifft(x) * N)):
+        A = np.stack([stockham(x[c::CL], pow2_radices(NL, 32 if NL >= 32 else NL), sign)
+                      for c in range(CL)])                                # [CL][NL]
+        t1 = np.arange(NL)
+        X = np.empty(N, dtype=np.complex128)
+        owner = np.full(N, -1)
+        for cta in range(CL):
+            span = slice(cta * NL // CL, (cta + 1) * NL // CL)
+            for t2 in range(CL):
+                acc = sum(np.exp(sign * 2j * np.pi * c * t2 / CL)
+                          * np.exp(sign * 2j * np.pi * c * t1[span] / N) * A[c, span] for c in range(CL))
+                X[t1[span] + NL * t2] = acc
+                assert (owner[t1[span] + NL * t2] == -1).all()
+                owner[t1[span] + NL * t2] = cta
+        assert (owner >= 0).all()
+        np.testing.assert_allclose(X, ref, rtol=0, atol=1e-9 * N)
