@@ -156,6 +156,13 @@ def test_null_plan_calls(lib):
     assert so.cwt_plan_info(None, None) == lib.CWT_EINVAL
     so.cwt_plan_last_error.restype = ctypes.c_char_p
     assert so.cwt_plan_last_error(None) == b""
+    rad, pair = (ctypes.c_int * 8)(), (ctypes.c_int * 2)()
+    t, fixed = ctypes.c_int(), ctypes.c_int()
+    assert so.cwt_smooth_schedule(10000, None, ctypes.byref(t), pair, ctypes.byref(fixed)) == lib.CWT_EINVAL
+    assert so.cwt_smooth_schedule(10000, rad, None, pair, ctypes.byref(fixed)) == lib.CWT_EINVAL
+    assert so.cwt_smooth_schedule(10000, rad, ctypes.byref(t), None, ctypes.byref(fixed)) == lib.CWT_EINVAL
+    assert so.cwt_smooth_schedule(10000, rad, ctypes.byref(t), pair, None) == lib.CWT_EINVAL
+    assert so.cwt_smooth_schedule(-5, rad, ctypes.byref(t), pair, ctypes.byref(fixed)) == lib.CWT_EUNSUPPORTED
 
 
 # The fixed-length kernels run only when the host scheduler picks exactly the
