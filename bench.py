@@ -119,15 +119,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, x_rows, n_channels, n_scales=None, N=None, min_seconds=10.0):
+def padded_length(n, pad):
+    """The workload's padded length, written out here so that the oracle legs
+    need nothing from the product library: the next power of two >= max(n, 32),
+    or the smallest 2,3,5,7-smooth length >= max(n, 32) (Section "Fast Fourier
+    transform").  For the workloads timed here (n = 10000, 122880, 500) this is
+    the length the library's plan reports."""
+    m = max(int(n), 32)
+    if pad == "pow2":
+        return 1 << (m - 1).bit_length()
+    while True:
+        x = m
+        for f in (2, 3, 5, 7):
+            while x % f == 0:
+                x //= f
+        if x == 1:
+            return m
+        m += 1
+
+
+def cpu_baseline(w, x_rows, n_channels, N, n_scales=None, min_seconds=10.0):
     """The FP64 oracle, as it stands, on the host cores: the first n_scales
     (default all) scales of the first channels of the same workload, at the
     padded length N of the timed plan -- n_channels channels, then one more at a
     time until at least min_seconds of work (at most every channel given)."""
     import oracle
-    from paper_2506_07793_gb300 import cwt_fft_length
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    N = cwt_fft_length(w.samples) if N is None else N
     ns = w.scales if n_scales is None else n_scales
     scales = list(range(0, w.scales, max(1, w.scales // ns)))[:ns]
     x64 = x_rows.astype(np.float64)
@@ -153,10 +170,9 @@ def run_reference(args):
         return
     from eeg_synth import workload
     import oracle
-    from paper_2506_07793_gb300 import CWT_PAD_POW2, CWT_PAD_SMOOTH, cwt_fft_length
     w = workload(WORKLOAD)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    N = cwt_fft_length(w.samples, CWT_PAD_SMOOTH if args.pad == "smooth" else CWT_PAD_POW2)
+    N = padded_length(w.samples, args.pad)
     x = w.signal(channels=1).astype(np.float64)
     rows = [(0, s) for s in range(w.scales)]
     for _ in range(args.warmup):
@@ -359,7 +375,7 @@ def run_batch(args):
             while n_ep < len(lengths) and (n_ep < 2 or time.perf_counter() - t0 < 10.0):
                 n = int(lengths[n_ep])
                 xe = x_host[ep[n_ep].in_offset:ep[n_ep].in_offset + C * n].reshape(C, n)
-                oracle.cwt(xe.astype(np.float64), cw.cwt_fft_length(n), w.fs, w.freqs, w.n_cycles,
+                oracle.cwt(xe.astype(np.float64), padded_length(n, "pow2"), w.fs, w.freqs, w.n_cycles,
                            decimation=d, threads=cores)
                 done += C * S * (-(-n // d))
                 n_ep += 1
@@ -816,8 +832,8 @@ def run_plan_workload(args, name):
         if other is not None:
             line["other_padding"] = other
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels if name == "fused" else 1,
-                                                None if name == "fused" else 8, N=N)
+            line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels if name == "fused" else 1, N,
+                                                n_scales=None if name == "fused" else 8)
         if plain is not None:
             plain["speedup_of_fused"] = plain["ms_per_step"] / ms_step
         else:

@@ -220,6 +220,12 @@ cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlin
  *   opt                NULL for defaults
  * On CWT_OK *out holds a new plan (free with cwt_plan_destroy).  Argument
  * errors are reported before any CUDA call.  Blocks until the bank is built.
+ * A scale that the N-point grid cannot represent is CWT_EINVAL: one whose
+ * alias-summed spectrum is below 1e-150 on every DFT bin, so that its
+ * unit-energy normalisation would underflow in FP64 (a carrier far below
+ * the first bin, e.g. 1.5 Hz with 7 cycles in a 32-point window at 500 Hz,
+ * where the first bin lies at ten times the carrier).  Scales below the
+ * first bins but above that floor are computed exactly like the others.
  */
 cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
                            const double *freqs_hz, int n_freqs, const double *n_cycles,
@@ -283,7 +289,9 @@ cwt_status cwt_execute_host(cwt_plan plan, const void *h_signal, void *h_complex
  * four schedules on this batch and keeps the fastest; later batches of the
  * same shape only replay the graph.  Asynchronous on `stream` otherwise.
  * CWT_EUNSUPPORTED for F64 plans, smooth-padded plans, or epochs whose
- * padded length would exceed 8192 samples.
+ * padded length would exceed 8192 samples.  CWT_EINVAL (before any device
+ * work) when an epoch's N_e cannot represent one of the plan's scales (the
+ * 1e-150 floor of cwt_plan_create).
  */
 cwt_status cwt_execute_batch(cwt_plan plan, const cwt_epoch *epochs, int n_epochs, const void *d_in,
                              void *d_complex, void *d_power, void *d_phase, void *stream);
@@ -335,8 +343,10 @@ cwt_status cwt_server_create(cwt_server *out, const double *freqs_hz, const doub
 cwt_status cwt_server_destroy(cwt_server srv);
 
 /* Admit a stream of `channels` channels sampled at fs Hz (every frequency must
- * be < fs/2).  CWT_EBUSY when no slot is free or its device memory would
- * exceed the budget (the refusal is counted).  Generates the bank for a new fs. */
+ * be < fs/2 and representable on the window's W-point grid at fs, as in
+ * cwt_plan_create; else CWT_EINVAL).  CWT_EBUSY when no slot is free or its
+ * device memory would exceed the budget (the refusal is counted).  Generates
+ * the bank for a new fs. */
 cwt_status cwt_stream_open(cwt_server srv, int channels, double fs, int *stream_id);
 
 /* Append k new samples per channel: samples is [channels][k] float32, host or

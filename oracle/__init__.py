@@ -11,9 +11,8 @@ of the CWT result).  See cwt_oracle.c for the definition being computed:
 the cyclic convolution of the zero-padded signal with the N-periodised,
 unit-energy Morlet wavelet of Eq. 3, which is what Eq. 2 evaluates.
 
-Parity pins live in tests/test_oracle_pins.py.  Every function here is pinned
-except `paper_style_error`, which restates the error metric of Table 1 and is
-marked "parity unpinned" (it is a report, not a result).
+Parity pins live in tests/test_oracle_pins.py and tests/test_oracle_pins_gmw.py;
+every function here is pinned.
 """
 import ctypes
 import os
@@ -158,22 +157,3 @@ def dft(z, sign=-1):
     if lib.oracle_dft(_dp(re), _dp(im), len(z), int(sign), _dp(ore), _dp(oim)) != 0:
         raise ValueError("oracle_dft: bad argument")
     return ore + 1j * oim
-
-
-def paper_style_error(test, ref, interior=(0.2, 0.8), threshold_sd=1e-5):
-    """Table 1's metric: |test - ref| / SD(ref) over the interior of each row.
-
-    Parity unpinned: this is a secondary report, not a result of the method.
-    Returns (max, mean, count above threshold) over the interior window for
-    the real and imaginary parts.
-    """
-    n = ref.shape[-1]
-    lo, hi = int(round(interior[0] * n)), int(round(interior[1] * n))
-    out = {}
-    for name, f in (("real", np.real), ("imag", np.imag)):
-        r = f(ref)[..., lo:hi]
-        t = f(test)[..., lo:hi]
-        sd = np.std(r)
-        diff = np.abs(t - r) / sd
-        out[name] = (float(diff.max()), float(diff.mean()), int((diff > threshold_sd).sum()))
-    return out

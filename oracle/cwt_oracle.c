@@ -34,6 +34,17 @@
  *         p[m] = sum_{r in Z} psi((m + r N) / fs),   m = 0..N-1,
  *     (indices m > N/2 hold negative time).  The sum over r runs over every
  *     replica whose Gaussian envelope is not exactly zero in double.
+ *     When the wavelet is not resolved by the N-point grid (its carrier lies
+ *     below the first DFT bins, so the replicas cancel almost completely:
+ *     the periodised energy is below 1e-6 of the replicas' own energy), that
+ *     sum keeps only a few correct digits.  The same p is then reached from
+ *     the other side of Poisson summation, as for the GMW below:
+ *         p[m] = fs * IDFT_N(P)[m],  P[k] = sum_q Psi((k/N + q) fs),
+ *     with Psi(nu) = a sqrt(2 pi) (exp(-sigma^2 (nu/F - 1)^2 / 2)
+ *                                  - kappa exp(-sigma^2 (nu/F)^2 / 2))
+ *     the continuous Fourier transform of psi (Eq. 3 in Hz with its
+ *     absolute constant).  Each P[k] is a sum of positive-or-tiny terms
+ *     evaluated to full relative precision, so nothing cancels.
  *     For the GMW the same periodised sampled wavelet is reached from its
  *     spectrum: by Poisson summation its DFT is proportional to
  *         P[k] = sum_{q >= 0} Psi((k/N + q) fs)
@@ -98,34 +109,18 @@ double oracle_gmw_spectrum(double nu, double F, double beta, double gamma)
     return exp(log_alpha + beta * log(w) - pow(w, gamma));
 }
 
-/* Step 2, GMW: P[k] = sum_{q >= 0} Psi((k/N + q) fs), then p = IDFT_N(P)
- * (with the 1/N).  Psi rises to its peak at F and falls after it, so the sum
- * over q stops at the first term past the peak that is exactly zero. */
-static int gmw_periodised(double F, double beta, double gamma, double fs, int N, double *p_re,
-                          double *p_im)
+/* p = scale * IDFT_N(P) (with the 1/N) of a real spectrum P, by the O(N^2)
+ * definition: the N-th roots of unity exp(+2 pi i j / N) with the exponent
+ * k m reduced mod N in integers, so that every angle is exact. */
+static int idft_real_spectrum(const double *P, int N, double scale, double *p_re, double *p_im)
 {
-    double *P = (double *)malloc(sizeof(double) * (size_t)N);
     double *c = (double *)malloc(sizeof(double) * (size_t)N);
     double *s = (double *)malloc(sizeof(double) * (size_t)N);
-    if (!P || !c || !s) {
-        free(P);
+    if (!c || !s) {
         free(c);
         free(s);
         return -2;
     }
-    for (int k = 0; k < N; ++k) {
-        double sum = 0.0;
-        for (long q = 0;; ++q) {
-            double nu = ((double)k / (double)N + (double)q) * fs;
-            double term = oracle_gmw_spectrum(nu, F, beta, gamma);
-            sum += term;
-            if (nu > F && term == 0.0)
-                break;
-        }
-        P[k] = sum;
-    }
-    /* the N-th roots of unity exp(+2 pi i j / N); the exponent k m is reduced
-     * mod N in integers so that every angle is exact */
     for (int j = 0; j < N; ++j) {
         double ang = 2.0 * ORACLE_PI * (double)j / (double)N;
         c[j] = cos(ang);
@@ -141,13 +136,73 @@ static int gmw_periodised(double F, double beta, double gamma, double fs, int N,
             if (j >= N)
                 j -= N;
         }
-        p_re[m] = sre / (double)N;
-        p_im[m] = sim / (double)N;
+        p_re[m] = scale * sre / (double)N;
+        p_im[m] = scale * sim / (double)N;
     }
-    free(P);
     free(c);
     free(s);
     return 0;
+}
+
+/* Step 2, GMW: P[k] = sum_{q >= 0} Psi((k/N + q) fs), then p = IDFT_N(P)
+ * (with the 1/N).  Psi rises to its peak at F and falls after it, so the sum
+ * over q stops at the first term past the peak that is exactly zero. */
+static int gmw_periodised(double F, double beta, double gamma, double fs, int N, double *p_re,
+                          double *p_im)
+{
+    double *P = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!P)
+        return -2;
+    for (int k = 0; k < N; ++k) {
+        double sum = 0.0;
+        for (long q = 0;; ++q) {
+            double nu = ((double)k / (double)N + (double)q) * fs;
+            double term = oracle_gmw_spectrum(nu, F, beta, gamma);
+            sum += term;
+            if (nu > F && term == 0.0)
+                break;
+        }
+        P[k] = sum;
+    }
+    int rc = idft_real_spectrum(P, N, 1.0, p_re, p_im);
+    free(P);
+    return rc;
+}
+
+/* Continuous Fourier transform of the Morlet (kind 0) or Gabor (kind 1)
+ * wavelet of step 1 at nu Hz: int psi(tau) exp(-i 2 pi nu tau) dtau. */
+double oracle_morlet_spectrum(int kind, double nu, double F, double sigma)
+{
+    double a = sigma / (2.0 * ORACLE_PI * F);
+    double kappa = kind == 0 ? exp(-0.5 * sigma * sigma) : 0.0;
+    double u = nu / F;
+    double g = exp(-0.5 * sigma * sigma * (u - 1.0) * (u - 1.0)) -
+               kappa * exp(-0.5 * sigma * sigma * u * u);
+    return a * sqrt(2.0 * ORACLE_PI) * g;
+}
+
+/* Step 2 from the spectrum side for Morlet / Gabor (Poisson summation):
+ * p = fs * IDFT_N(P), P[k] = sum_q Psi((k/N + q) fs) over every q whose
+ * Gaussians are not exactly zero in double (both lie within 40 F / sigma of
+ * nu = F and nu = 0). */
+static int morlet_periodised_spectral(int kind, double F, double sigma, double fs, int N,
+                                      double *p_re, double *p_im)
+{
+    double *P = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!P)
+        return -2;
+    double reach = 40.0 * F / sigma;
+    for (int k = 0; k < N; ++k) {
+        double base = (double)k / (double)N;
+        double q_lo = ceil(-reach / fs - base), q_hi = floor((F + reach) / fs - base);
+        double sum = 0.0;
+        for (double q = q_lo; q <= q_hi; q += 1.0)
+            sum += oracle_morlet_spectrum(kind, (base + q) * fs, F, sigma);
+        P[k] = sum;
+    }
+    int rc = idft_real_spectrum(P, N, fs, p_re, p_im);
+    free(P);
+    return rc;
 }
 
 /* Step 2: p[m] = sum_r psi((m + r N) / fs).  kind 0 = Morlet, 1 = Gabor
@@ -165,6 +220,7 @@ int oracle_periodised_wavelet(int kind, double F, double sigma, double gamma, do
     }
     double a = sigma / (2.0 * ORACLE_PI * F);
     double reach = ORACLE_ENVELOPE_RADIUS * a * fs; /* in samples */
+    double e_raw = 0.0, e_per = 0.0; /* replicas' own energy, periodised energy */
     for (int m = 0; m < N; ++m) {
         double lo = ceil((-reach - (double)m) / (double)N);
         double hi = floor((reach - (double)m) / (double)N);
@@ -178,10 +234,16 @@ int oracle_periodised_wavelet(int kind, double F, double sigma, double gamma, do
                 gabor_psi(tau, F, sigma, &vre, &vim);
             sre += vre;
             sim += vim;
+            e_raw += vre * vre + vim * vim;
         }
         p_re[m] = sre;
         p_im[m] = sim;
+        e_per += sre * sre + sim * sim;
     }
+    /* unresolved wavelet: the replicas cancel to below 1e-6 of their energy,
+     * so the sum above has lost most of its digits; take the spectral side */
+    if (e_per < 1e-6 * e_raw)
+        return morlet_periodised_spectral(kind, F, sigma, fs, N, p_re, p_im);
     return 0;
 }
 

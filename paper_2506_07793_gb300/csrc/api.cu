@@ -233,6 +233,8 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         if (st != CWT_OK) return st;
     }
     if ((long long)channels * n_freqs > (1ll << 30)) return CWT_EUNSUPPORTED;
+    if (!cwtk::scales_on_grid(wavelet, freqs_hz, n_cycles, n_freqs, o.gmw_gamma, fs, N))
+        return CWT_EINVAL;
 
     cwt_plan_s *p = new (std::nothrow) cwt_plan_s();
     if (!p) return CWT_ENOMEM;
@@ -440,6 +442,17 @@ cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, 
         const cwt_epoch &e = epochs[i];
         if (e.samples < 1 || e.samples > p->n || e.in_offset < 0 || e.out_offset < 0) return CWT_EINVAL;
         if (e.samples + p->pad_extra > 8192) return CWT_EUNSUPPORTED;
+        // each epoch's own length N_e must represent every scale (checked once
+        // per length and remembered)
+        int Ne = 0;
+        cwt_fft_length(e.samples + p->pad_extra, CWT_PAD_POW2, &Ne);
+        const unsigned bit = 1u << ilog2c(Ne);
+        if (!(p->grid_ok_lengths & bit)) {
+            if (!cwtk::scales_on_grid(p->wavelet, p->freqs.data(), p->cycles.data(), p->S, p->gmw_gamma,
+                                      p->fs, Ne))
+                return CWT_EINVAL;
+            p->grid_ok_lengths |= bit;
+        }
     }
     if (n_epochs == 0) return CWT_OK;
     DeviceGuard g(p->device);

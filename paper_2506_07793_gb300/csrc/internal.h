@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 
 #include <string>
 #include <vector>
@@ -47,6 +49,8 @@ struct cwt_plan_s {
     int wavelet = 0;
     double gmw_gamma = 3.0;  // gamma of Eq. 5 (CWT_WAVELET_GMW only)
     int pad_extra = 0;       // linear edges: samples added before padding (R + 1)
+    unsigned grid_ok_lengths = 0;  // batch: bit log2(N_e) set once every scale passed
+                                   // the grid check at that epoch length
     unsigned outputs = 0;
     int io = CWT_DTYPE_F32;
     std::vector<double> freqs, cycles;
@@ -98,6 +102,55 @@ inline bool wavelet_params_ok(int wavelet, const double *n_cycles, int n, double
     if (!(gamma > 0.0) || !(gamma <= 64.0)) return false;
     for (int i = 0; i < n; ++i)
         if (!(n_cycles[i] <= 1000.0)) return false;
+    return true;
+}
+
+// Scales whose wavelet the N-point grid cannot represent are refused.  The
+// spectrum sampled on the bins, P[k] = sum_q G((k/N + q) fs), is normalised
+// to unit energy by sum_k P[k]^2; when every P[k] is below ~1e-154 that sum
+// underflows in FP64 and the scale would come out as zeros.  This happens
+// only when the carrier lies far below the first DFT bin (e.g. 1.5 Hz with
+// sigma = 7 in a 32-point window at 500 Hz, where the first bin sits at ten
+// times the carrier).  The library refuses (CWT_EINVAL) a scale whose largest
+// |P[k]| is below kMinSpectrumPeak; every other scale, resolved or not, is
+// the exact alias-summed closed form.
+constexpr double kMinSpectrumPeak = 1e-150;
+
+// Largest |P[k]| over the bins that can hold the maximum of a scale's
+// alias-summed spectrum (Eq. 3/4 for Morlet/Gabor with sig = sigma, Eq. 5 for
+// the GMW with sig = beta): the two bins around the carrier F and the bins
+// 0, 1 and N - 1 around DC, with the aliases q = -2..2.  Host-only.
+inline double spectrum_peak_on_grid(int wavelet, double F, double sig, double gamma, double fs,
+                                    int N) {
+    auto g = [&](double nu) -> double {
+        if (wavelet == CWT_WAVELET_GMW) {
+            if (!(nu > 0.0)) return 0.0;
+            const double wp = std::pow(sig / gamma, 1.0 / gamma);
+            const double w = wp * nu / F;
+            const double la = std::log(2.0) + (sig / gamma) * (1.0 + std::log(gamma) - std::log(sig));
+            return std::exp(la + sig * std::log(w) - std::pow(w, gamma));
+        }
+        const double kappa = wavelet == CWT_WAVELET_GABOR ? 0.0 : std::exp(-0.5 * sig * sig);
+        const double u = nu / F;
+        return std::exp(-0.5 * sig * sig * (u - 1.0) * (u - 1.0)) - kappa * std::exp(-0.5 * sig * sig * u * u);
+    };
+    const long long k0 = (long long)std::floor(F * (double)N / fs);
+    const long long ks[5] = {0, 1, N - 1, k0, k0 + 1};
+    double best = 0.0;
+    for (long long k : ks) {
+        const long long kk = ((k % N) + N) % N;
+        double sum = 0.0;
+        for (int q = -2; q <= 2; ++q) sum += g(((double)kk / (double)N + q) * fs);
+        best = std::max(best, std::fabs(sum));
+    }
+    return best;
+}
+
+// True when every scale passes the check above at length N.
+inline bool scales_on_grid(int wavelet, const double *F, const double *sig, int S, double gamma,
+                           double fs, int N) {
+    for (int s = 0; s < S; ++s)
+        if (!(spectrum_peak_on_grid(wavelet, F[s], sig[s], gamma, fs, N) >= kMinSpectrumPeak)) return false;
     return true;
 }
 

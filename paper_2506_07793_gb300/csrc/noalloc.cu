@@ -271,6 +271,7 @@ extern "C" cwt_status cwt_execute_noalloc(const float *d_signal, int channels, i
     int N = 0;
     cwt_status stt = cwt_fft_length(samples, CWT_PAD_POW2, &N);
     if (stt != CWT_OK) return stt;
+    if (!scales_on_grid(CWT_WAVELET_MORLET, freqs_hz, n_cycles, n_freqs, 3.0, fs, N)) return CWT_EINVAL;
     const int nblk = (N + kNaThreads - 1) / kNaThreads;
     const size_t off_par = align256(kTwBytes);
     const size_t off_part = off_par + align256(sizeof(double) * 2 * (size_t)n_freqs);

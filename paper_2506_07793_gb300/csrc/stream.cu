@@ -371,6 +371,8 @@ cwt_status cwt_stream_open(cwt_server s, int channels, double fs, int *stream_id
     if (!s || !stream_id || channels < 1 || !(fs > 0.0) || !std::isfinite(fs)) return CWT_EINVAL;
     for (double f : s->freqs)
         if (!(f < 0.5 * fs)) return CWT_EINVAL;
+    if (!scales_on_grid(s->wavelet, s->freqs.data(), s->cycles.data(), s->S, s->opt.gmw_gamma, fs, kSW))
+        return CWT_EINVAL;
     const int H = (int)std::ceil(fs * s->opt.hop_seconds - 1e-9);
     if (H < 1 || H > kSW / 2) return CWT_EINVAL;
     Guard g(s->device);

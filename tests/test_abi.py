@@ -60,7 +60,11 @@ def test_pow2_padding(lib, n, N):
                                  (10000, 10000), (14000, 14000), (14401, 15000), (15000, 15000),
                                  (15100, 15360), (16001, 16384), (16383, 16384)])
 def test_smooth_padding(lib, n, N):
-    """Section "Fast Fourier transform": smallest 2,3,5,7-smooth length >= n."""
+    """Section "Fast Fourier transform": the smallest 2,3,5,7-smooth length >= n
+    among those the mixed-radix kernels schedule.  14406 = 2 3 7^4 and
+    15120 = 2^4 3^3 5 7 are smooth but have no schedule of at most 32 values
+    per thread and 512 threads per row, so 14401 pads to 15000 and 15100 to
+    15360 (the 15 such lengths in [14175, 16200] are passed over)."""
     assert lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) == N
 
 
@@ -85,6 +89,13 @@ BAD = [
     dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
     dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]), dict(edge=2), dict(edge=-1),
     dict(edge=1, fft_length=128),  # linear edges need N >= n + R + 1 (here 100 + 363 + 1)
+    # a carrier far below the first DFT bin: 1.5 Hz with sigma 7 in a 32-point
+    # window at 500 Hz (first bin 15.6 Hz) has a spectrum below 1e-150 on every
+    # bin, so its unit-energy normalisation would underflow
+    dict(samples=32, freqs=[1.5, 20.0]),
+    # Gabor keeps a DC term exp(-sigma^2 / 2): below 1e-150 only for sigma > 26
+    dict(samples=32, freqs=[1.5, 20.0], wavelet=1, n_cycles=[30.0, 7.0]),
+    dict(samples=32, freqs=[1.5, 20.0], wavelet=2, n_cycles=[20.0, 20.0]),  # GMW
 ]
 
 
@@ -215,3 +226,22 @@ def test_smooth_schedules_on_the_host(lib):
     for N in (1024, 3001 * 7 + 1, 20000, 16):
         with pytest.raises(lib.CWTError):
             lib.cwt_smooth_schedule(N)
+
+
+def test_grid_check_boundary(lib):
+    """The refusal is the 1e-150 floor on the sampled spectrum, not a rule on
+    the carrier's bin: 6 Hz with sigma 5 in a 32-point window at 500 Hz (0.38
+    of the first bin, peak ~1e-14 on the grid) passes the host-side checks and
+    fails only for lack of a GPU here, while 2 Hz with sigma 12 is refused."""
+    import torch
+    o = lib.cwt_options_init()
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(1, 32, 500.0, [2.0], [12.0], 0, lib.CWT_OUT_POWER, o)
+    assert e.value.status == lib.CWT_EINVAL
+    if torch.cuda.is_available():
+        plan = lib.cwt_plan_create(1, 32, 500.0, [6.0], [5.0], 0, lib.CWT_OUT_POWER, o)
+        lib.cwt_plan_destroy(plan)
+    else:
+        with pytest.raises(lib.CWTError) as e:
+            lib.cwt_plan_create(1, 32, 500.0, [6.0], [5.0], 0, lib.CWT_OUT_POWER, o)
+        assert e.value.status != lib.CWT_EINVAL

@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 from eeg_synth import eeg, workload
-from tests.metrics import FP32_TOL, complex_err, phase_err, power_err
+from tests.metrics import FP32_TOL, complex_err, paper_style_error, phase_err, power_err
 
 pytestmark = pytest.mark.gpu
 
@@ -269,7 +269,7 @@ def test_paper_style_error_report(lib):
     x = eeg(400, 1, n, fs, np.float32)
     res, N = run_gpu(lib, x, fs, freqs, np.full(len(freqs), 7.0), ("complex",))
     ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, np.full(len(freqs), 7.0))
-    rep = oracle.paper_style_error(res["complex"].astype(np.complex128), ref)
+    rep = paper_style_error(res["complex"].astype(np.complex128), ref)
     assert rep["real"][2] == 0 and rep["imag"][2] == 0, rep
 
 

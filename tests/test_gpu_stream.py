@@ -219,3 +219,20 @@ def test_backpressure_and_errors(lib):
             lib.cwt_stream_push(srv, 31, np.zeros((2, 5), np.float32))  # not open
     finally:
         lib.cwt_server_destroy(srv)
+
+
+def test_stream_refused_when_the_window_cannot_hold_a_scale(lib):
+    """A 0.1 Hz scale with 7 cycles has a spectrum below 1e-150 on every bin
+    of the 2048-point window at 4 kHz (first bin 1.95 Hz): such a stream is
+    refused (CWT_EINVAL, not counted as an admission refusal), while the same
+    scales at 250 Hz (first bin 0.12 Hz) are admitted."""
+    o = lib.cwt_server_options_init()
+    srv = lib.cwt_server_create(np.array([0.1, 10.0]), np.array([7.0, 7.0]), lib.CWT_WAVELET_MORLET, o)
+    try:
+        with pytest.raises(lib.CWTError) as e:
+            lib.cwt_stream_open(srv, 2, 4000.0)
+        assert e.value.status == lib.CWT_EINVAL
+        sid = lib.cwt_stream_open(srv, 2, 250.0)
+        lib.cwt_stream_close(srv, sid)
+    finally:
+        lib.cwt_server_destroy(srv)

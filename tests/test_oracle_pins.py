@@ -263,3 +263,66 @@ def test_golden_fixture_regression():
     got = compute(**TINY)
     assert rows.shape == got.shape
     assert np.abs(rows - got).max() <= 1e-12 * np.abs(rows).max()
+
+
+# Unresolved wavelets: the carrier lies below the first DFT bins of N, so the
+# replicas of the periodised wavelet cancel almost completely (to 1e-11 .. 1e-20
+# of their amplitude here).  The oracle then takes the spectral side of Poisson
+# summation; the pin is the time-domain definition
+# p[m] = sum_r psi((m + r N) / fs) evaluated in 60-digit arithmetic.
+UNRESOLVED = [
+    # (kind, F, sigma, fs, N)
+    ("morlet", 7.8, 7.0, 500.0, 32),    # 0.5 bin: first bin at 2 F
+    ("morlet", 1.0, 7.0, 125.0, 64),    # 0.51 bin (the 1 Hz scale of a 2048-point window at 4 kHz)
+    ("gabor", 5.0, 7.0, 500.0, 32),     # Gabor, 0.32 bin: no zero-mean term, DC bin dominates
+    ("morlet", 3.0, 12.0, 250.0, 64),   # 0.77 bin, large sigma
+    ("morlet", 6.0, 5.0, 500.0, 32),    # 0.38 bin, smaller sigma
+]
+
+
+def _mp_periodised(kind, F, sigma, fs, N, dps=60):
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = dps
+    Fm, sg, fsm = mp.mpf(F), mp.mpf(sigma), mp.mpf(fs)
+    a = sg / (2 * mp.pi * Fm)
+    kappa = mp.e ** (-sg * sg / 2) if kind == "morlet" else mp.mpf(0)
+    reach = int(mpmath.ceil(40 * a * fsm))  # envelope below e^-800 beyond
+    out = np.zeros(N, np.complex128)
+    for m in range(N):
+        s = mp.mpc(0)
+        r_lo = -((reach + m) // N) - 1
+        r_hi = (reach - m) // N + 1
+        for r in range(r_lo, r_hi + 1):
+            tau = (m + r * N) / fsm
+            env = mp.e ** (-(tau * tau) / (2 * a * a))
+            s += env * (mp.expj(2 * mp.pi * Fm * tau) - kappa)
+        out[m] = complex(s)
+    return out
+
+
+@pytest.mark.parametrize("kind,F,sigma,fs,N", UNRESOLVED)
+def test_unresolved_wavelet_matches_high_precision_periodisation(kind, F, sigma, fs, N):
+    """The oracle's periodised wavelet equals the 60-digit time-domain sum to
+    1e-11 of its peak, and so does the unit-energy wavelet."""
+    ref = _mp_periodised(kind, F, sigma, fs, N)
+    p = oracle.periodised_wavelet(F, sigma, fs, N, wavelet=kind)
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(p - ref).max() <= 1e-11 * scale
+    w = oracle.wavelet(F, sigma, fs, N, wavelet=kind)
+    wref = ref / np.sqrt(np.sum(np.abs(ref) ** 2))
+    assert np.abs(w - wref).max() <= 1e-11
+
+
+def test_unresolved_route_is_taken_and_resolved_route_kept():
+    """Both sides of the switch: a wavelet half a bin below the first bin
+    (replicas cancel to ~1e-11 of their amplitude) and a resolved one agree with the
+    Poisson-summed closed form of Eq. 3 (the spectral side, computed here in
+    numpy) to 1e-11 of the peak."""
+    for F, sigma, fs, N in [(7.8, 7.0, 500.0, 32), (10.0, 7.0, 500.0, 512)]:
+        p = oracle.periodised_wavelet(F, sigma, fs, N)
+        a = sigma / (2 * PI * F)
+        expected = fs * a * np.sqrt(2 * PI) * morlet_closed_form(F, sigma, fs, N)
+        P = np.fft.fft(p)
+        assert np.abs(P - expected).max() <= 1e-11 * np.abs(expected).max()
