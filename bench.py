@@ -231,6 +231,45 @@ def plain_fp32_pipeline(cw, plan, x, fused_power, w, args, flush, stream):
             "max_row_power_diff_vs_fused": row_err, "speedup_of_fused": None}
 
 
+def plain_fp32_chunked(cw, plan, x, fused_power, fused_phase, w, args, flush, stream, chunk=8):
+    """The plain FP32 pipeline (cuFFT through torch.fft, as in
+    plain_fp32_pipeline) for the precision workload, whose [C][S][N] complex
+    intermediate (34 GB) is formed `chunk` channels at a time: one FFT of all
+    channels, then per chunk the broadcast product with the same FP32 bank, the
+    inverse FFT, the crop, |c|^2 and atan2 into the power and phase outputs.
+    The fused result is compared on the last step's outputs (per-row power
+    difference over the row's peak)."""
+    import torch
+    info = cw.cwt_plan_info(plan)
+    N = info.fft_length
+    bank, _, _ = cw.cwt_plan_bank(plan)
+    Wt = torch.from_numpy(bank * N).cuda()
+    xp = torch.zeros((w.channels, N), dtype=torch.float32, device="cuda")
+    ref_p = fused_power[:chunk].clone()
+    pw = torch.empty_like(fused_power)
+    ph = torch.empty_like(fused_phase)
+
+    def step():
+        xp[:, :w.samples] = x
+        X = torch.fft.fft(xp)
+        for c0 in range(0, w.channels, chunk):
+            c = torch.fft.ifft(X[c0:c0 + chunk, None, :] * Wt[None])[..., :w.samples]
+            pw[c0:c0 + chunk] = c.real * c.real + c.imag * c.imag
+            ph[c0:c0 + chunk] = torch.angle(c)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    steps = max(2, min(args.steps, 5))
+    ms = timed_steps(step, steps, flush, stream) / steps
+    row_err = ((pw[:chunk] - ref_p).abs().amax(dim=-1) / ref_p.amax(dim=-1)).max().item()
+    del pw, ph, xp, Wt
+    torch.cuda.empty_cache()
+    return {"value": w.coefficients / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "impl": f"torch.fft (cuFFT): fft -> per {chunk}-channel chunk: broadcast product -> ifft "
+                    "-> crop -> |c|^2, angle",
+            "max_row_power_diff_vs_fused": row_err, "speedup_of_fused": None}
+
+
 def other_padding(cw, w, kinds, pad, x, outs, flush, stream, args):
     """The same workload under the other padding policy (same outputs, same
     timing method), reported beside the main line for comparison."""
@@ -274,14 +313,7 @@ def run_batch(args):
     from eeg_synth import batch_signal, workload
     import oracle
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local, dist = rank_setup()
     w = workload("batch")
     if args.epochs:
         w.extra["epoch_lengths"] = w.extra["epoch_lengths"][:args.epochs]
@@ -350,6 +382,10 @@ def run_batch(args):
     loop = per_epoch_loop(cw, w, x_host, ep, lengths, stream) if world == 1 else None
     if loop is not None:
         loop["speedup_of_batch"] = value / loop["value"]
+    plain = (plain_fp32_batch(cw, w, x, out, ep, lengths, flush, stream)
+             if world == 1 and not getattr(args, "no_plain", False) else None)
+    if plain is not None:
+        plain["speedup_of_batch"] = plain["ms_per_step"] / ms_step
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -367,12 +403,14 @@ def run_batch(args):
         }
         if loop is not None:
             line["per_epoch_loop"] = loop
+        if plain is not None:
+            line["plain_fp32_gpu"] = plain
         if world == 1:
             # the oracle over the first epochs, one at a time until at least 10 s of work
             cores = len(os.sched_getaffinity(0))
             t0 = time.perf_counter()
             done = n_ep = 0
-            while n_ep < len(lengths) and (n_ep < 2 or time.perf_counter() - t0 < 10.0):
+            while n_ep < len(lengths) and (n_ep < 2 or time.perf_counter() - t0 < getattr(args, "cpu_seconds", 10.0)):
                 n = int(lengths[n_ep])
                 xe = x_host[ep[n_ep].in_offset:ep[n_ep].in_offset + C * n].reshape(C, n)
                 oracle.cwt(xe.astype(np.float64), padded_length(n, "pow2"), w.fs, w.freqs, w.n_cycles,
@@ -385,9 +423,67 @@ def run_batch(args):
                                     "sample": f"first {n_ep} of {len(lengths)} epochs x all {C} "
                                               f"channels x all {S} scales ({done} coefficients), "
                                               f"{dt:.2f} s wall"}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+        return line
+    return None
+
+
+def plain_fp32_batch(cw, w, x, batch_out, ep, lengths, flush, stream, chunk=8):
+    """The plain FP32 GPU pipeline for the batching workload (cuFFT through
+    torch.fft, the paper's own design): epochs grouped by their padded length
+    N_e, `chunk` epochs at a time zero-padded to N_e, FFT, broadcast product
+    with that length's FP32 bank, inverse FFT, crop, every d-th sample, |c|^2
+    written to the same packed output layout.  Timed like the batch (CUDA
+    events, L2 flushed), two steps after one warm-up; the largest per-row
+    power difference from the batch kernel's result is reported."""
+    import torch
+    C, S, d = w.channels, w.scales, w.decimation
+    groups = {}
+    for e_, n in enumerate(lengths):
+        groups.setdefault(padded_length(int(n), "pow2"), []).append(e_)
+    banks = {}
+    for Ne in groups:
+        o = cw.cwt_options_init()
+        p = cw.cwt_plan_create(1, Ne, w.fs, w.freqs, w.n_cycles, cw.CWT_WAVELET_MORLET,
+                               cw.CWT_OUT_POWER, o)
+        b, _, _ = cw.cwt_plan_bank(p)
+        cw.cwt_plan_destroy(p)
+        banks[Ne] = torch.from_numpy(b * Ne).cuda()  # the bank carries 1/N_e; ifft applies it
+    out = torch.empty_like(batch_out)
+
+    def step():
+        for Ne, eps in groups.items():
+            Wt = banks[Ne]
+            for i0 in range(0, len(eps), chunk):
+                sel = eps[i0:i0 + chunk]
+                xs = torch.zeros((len(sel) * C, Ne), dtype=torch.float32, device="cuda")
+                for j, e_ in enumerate(sel):
+                    n = int(lengths[e_])
+                    off = int(ep[e_].in_offset)
+                    xs[j * C:(j + 1) * C, :n] = x[off:off + C * n].view(C, n)
+                c = torch.fft.ifft(torch.fft.fft(xs)[:, None, :] * Wt[None])
+                p = c.real * c.real + c.imag * c.imag
+                for j, e_ in enumerate(sel):
+                    n = int(lengths[e_])
+                    no = -(-n // d)
+                    off = int(ep[e_].out_offset)
+                    out[off:off + C * S * no].view(C, S, no)[:] = p[j * C:(j + 1) * C, :, :n:d]
+    step()
+    torch.cuda.synchronize()
+    ms = timed_steps(step, 2, flush, stream) / 2
+    # compare the first epoch's rows
+    n0 = int(lengths[0])
+    no0 = -(-n0 // d)
+    off0 = int(ep[0].out_offset)
+    a = out[off0:off0 + C * S * no0].view(C * S, no0)
+    b = batch_out[off0:off0 + C * S * no0].view(C * S, no0)
+    diff = ((a - b).abs().amax(dim=-1) / b.amax(dim=-1).clamp_min(1e-30)).max().item()
+    del out, banks
+    torch.cuda.empty_cache()
+    coeffs = int(batch_out.numel())
+    return {"value": coeffs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 2,
+            "impl": f"torch.fft (cuFFT) per padded length, {chunk} epochs at a time: fft -> "
+                    "broadcast product -> ifft -> crop, decimate -> |c|^2",
+            "max_row_power_diff_vs_batch_first_epoch": diff}
 
 
 def per_epoch_loop(cw, w, x_host, ep, lengths, stream, n_ep=256):
@@ -541,11 +637,159 @@ def run_serving(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(steps, 1),
                 "d2h_bytes_per_step": d2h // max(steps, 1)},
         "gpu_launches": int(st.launches), "clocks": clk,
+        # a latency-bound path: the fraction of the hop interval (the deadline)
+        # that the 99th-percentile hop takes
+        "roofline": {"bound": "latency", "achieved": st.latency_p99_s * 1e3, "peak": hop_ms,
+                     "unit": "ms (p99 hop latency vs hop interval)",
+                     "frac": st.latency_p99_s * 1e3 / hop_ms, "traffic": None},
+        "cpu_baseline": serving_cpu_baseline(w, blocks, min_seconds=getattr(args, "cpu_seconds", 5.0)),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
-def main():
+def serving_cpu_baseline(w, blocks, min_seconds=5.0):
+    """The FP64 oracle on the serving definition: the cyclic CWT of one
+    2048-sample window per hop (8 channels at 1000 Hz, all 64 scales), of
+    which the H = 50 centred outputs are delivered; hops one after another
+    until min_seconds of work."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    fs, C, W, H = 1000.0, 8, 2048, 50
+    rec = blocks[fs]
+    rows = [(c, s) for c in range(C) for s in range(w.scales)]
+    t0 = time.perf_counter()
+    hops = 0
+    while hops < 1 or time.perf_counter() - t0 < min_seconds:
+        e = W + hops * H
+        win = rec[:C, (np.arange(e - W, e)) % rec.shape[1]].astype(np.float64)
+        oracle.cwt_rows(win, W, fs, w.freqs, w.n_cycles, rows, threads=cores)
+        hops += 1
+    dt = time.perf_counter() - t0
+    delivered = hops * C * w.scales * H
+    return {"value": delivered / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{hops} hops of 8 channels at 1000 Hz x all {w.scales} scales: the "
+                      f"2048-sample window's CWT, {H} outputs delivered per row, {dt:.2f} s wall"}
+
+
+def rank_setup():
+    """(world, rank, local_rank, torch.distributed or None) of this process.
+    One process per GPU: RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* come from
+    torchrun or from spawn_ranks.  The process group (NCCL on GPUs, gloo on a
+    CPU-only host) carries only the barrier and the max-over-ranks timing."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            if torch.cuda.is_available():
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group("gloo")
+    return world, rank, local, dist
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_entry(local_rank, argv, world, port):
+    os.environ.update({"RANK": str(local_rank), "LOCAL_RANK": str(local_rank),
+                       "WORLD_SIZE": str(world), "MASTER_ADDR": "127.0.0.1",
+                       "MASTER_PORT": str(port)})
+    main(argv)
+
+
+def spawn_ranks(argv, world):
+    """--gpus N with no WORLD_SIZE in the environment: start N local ranks, one
+    per GPU, each running this benchmark (rank 0 prints the line)."""
+    import torch.multiprocessing as mp
+    mp.spawn(_rank_entry, args=(argv, world, _free_port()), nprocs=world, join=True)
+
+
+def launcher_selftest(args):
+    """The multi-rank path without GPUs (gloo): each rank takes its block of a
+    64 x N-channel recording with the shard helper, reports a rank-dependent
+    time, and rank 0 prints the slowest rank's time and the blocks."""
+    from paper_2506_07793_gb300.partition import max_over_ranks, shard_channels
+    world, rank, local, dist = rank_setup()
+    c0, c1 = shard_channels(64 * world, world, rank)
+    ms = max_over_ranks(10.0 + rank, dist)
+    blocks = [None] * world
+    if dist:
+        dist.all_gather_object(blocks, (c0, c1))
+        dist.barrier()
+    else:
+        blocks = [(c0, c1)]
+    if rank == 0:
+        return {"metric": METRIC, "n_gpus": world, "ms_per_step": ms, "shards": blocks,
+                "scaling": "weak", "launcher": "spawn" if "SPAWNED_BY_BENCH" in os.environ else "env"}
+    return None
+
+
+def sub_args(args, **kw):
+    a = argparse.Namespace(**vars(args))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def precision_suite(args):
+    """The precision workload (256 ch x 122880 @2048 Hz, N = 131072, 128 scales,
+    power + phase) in its three inverse-FFT arithmetics -- FP32 on clusters,
+    tensor-core FP16 and BF16 hi/lo -- beside the plain FP32 cuFFT pipeline,
+    each timed like the headline (CUDA events, L2 flushed between steps)."""
+    out = {}
+    for prec in ("fp32", "tc_fp16", "tc_bf16"):
+        a = sub_args(args, workload="precision", precision=prec, pad="pow2", steps=5, warmup=3,
+                     no_e2e=prec != "fp32", no_plain=prec != "fp32", no_other=True,
+                     no_cpu=prec != "fp32", cpu_seconds=5.0, e2e_steps=1, channels=0)
+        line = run_plan_workload(a, "precision")
+        keep = {k: line[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "clocks",
+                                     "gpu_launches", "e2e", "cpu_baseline", "plain_fp32_gpu",
+                                     "steps", "warmup") if k in line}
+        out[prec] = keep
+        if prec == "fp32":
+            out["config"] = line["config"]
+    plain = out["fp32"].pop("plain_fp32_gpu", None)
+    if plain is not None:
+        out["plain_fp32_gpu"] = plain
+        for prec in ("fp32", "tc_fp16", "tc_bf16"):
+            out[prec]["speedup_over_plain_fp32_gpu"] = plain["ms_per_step"] / out[prec]["ms_per_step"]
+    for prec in ("tc_fp16", "tc_bf16"):
+        out[prec]["speedup_over_fp32_clusters"] = out["fp32"]["ms_per_step"] / out[prec]["ms_per_step"]
+    out["error_bar"] = "2e-3 of each row's peak power (tests/test_gpu_tc.py checks it per frequency)"
+    return out
+
+
+def run_default(args):
+    """The headline line (fused workload) and, on one GPU, the rest of the
+    metric as sub-objects: precision (FP32 / TC FP16 / TC BF16 / plain cuFFT),
+    batch and serving."""
+    line = run_plan_workload(args, "fused")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if line is None or world > 1 or args.headline_only:
+        return line
+    line["precision"] = precision_suite(args)
+    b = run_batch(sub_args(args, steps=5, warmup=3, e2e_steps=1, epochs=0, cpu_seconds=5.0))
+    line["batch"] = {k: v for k, v in b.items() if k not in ("metric", "n_gpus", "scaling",
+                                                             "higher_is_better", "vs_baseline",
+                                                             "data")}
+    s = run_serving(sub_args(args, serve_seconds=min(args.serve_seconds, 6.0)))
+    line["serving"] = {k: v for k, v in s.items() if k not in ("metric", "n_gpus", "scaling",
+                                                               "higher_is_better", "vs_baseline",
+                                                               "data")}
+    return line
+
+
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -555,6 +799,9 @@ def main():
     ap.add_argument("--cpu-channels", type=int, default=2)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=["fused", "batch", "serving", "precision", "sweep"])
+    ap.add_argument("--headline-only", action="store_true",
+                    help="fused workload only: leave out the precision, batch and serving "
+                         "sub-objects of the default line")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--pad", default=None, choices=["pow2", "smooth"],
                     help="padding policy: the paper's 2,3,5,7-smooth length (default for the fused "
@@ -562,22 +809,45 @@ def main():
                          "whose 122880 samples exceed the smooth lengths built)")
     ap.add_argument("--channels", type=int, default=0,
                     help="override the workload's channel count (small profiling captures)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_fp16", "tc_bf16"],
+                    help="inverse-FFT arithmetic of the precision workload: FP32, or the "
+                         "tensor-core DFT stages with FP16 / BF16 hi/lo operands")
     ap.add_argument("--epochs", type=int, default=0,
                     help="batch workload: use only the first N epochs (small profiling captures)")
-    args = ap.parse_args()
+    ap.add_argument("--launcher-selftest", action="store_true", help=argparse.SUPPRESS)
+    argv = sys.argv[1:] if argv is None else argv
+    args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.pad is None:
         args.pad = "pow2" if args.workload == "precision" else "smooth"
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        os.environ["SPAWNED_BY_BENCH"] = "1"
+        return spawn_ranks(argv, args.gpus)
+    if int(os.environ.get("WORLD_SIZE", "1")) != args.gpus:
+        ap.error(f"--gpus {args.gpus} but WORLD_SIZE={os.environ.get('WORLD_SIZE')}")
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    if args.workload == "serving":
-        return run_serving(args)
-    if args.workload == "sweep":
-        return run_sweep(args)
-    return run_plan_workload(args, args.workload)
+    if args.launcher_selftest:
+        line = launcher_selftest(args)
+    elif args.workload == "batch":
+        line = run_batch(args)
+    elif args.workload == "serving":
+        line = run_serving(args)
+    elif args.workload == "sweep":
+        line = run_sweep(args)
+    elif args.workload == "fused":
+        line = run_default(args)
+    else:
+        line = run_plan_workload(args, args.workload)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized():
+        tdist.barrier()
+        tdist.destroy_process_group()
 
 
 SWEEP_LENGTHS = sorted(set(range(100, 2501, 100)) | {101, 127, 499, 509, 1009, 1021, 1024, 1499,
@@ -681,20 +951,16 @@ def run_plan_workload(args, name):
     import paper_2506_07793_gb300 as cw
     from eeg_synth import workload
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    world, rank, local, dist = rank_setup()
 
     w = workload(name)
     if args.channels:
         w.channels = args.channels
-    # each rank transforms its own independent recording (weak scaling)
-    x_host = w.signal(first_channel=rank * w.channels)
+    # weak scaling: the job is a recording of channels x world channels; each
+    # rank transforms its contiguous block (the shard helper), no exchange
+    from paper_2506_07793_gb300.partition import shard_channels
+    c0, c1 = shard_channels(w.channels * world, world, rank)
+    x_host = w.signal(channels=c1 - c0, first_channel=c0)
     x = torch.from_numpy(x_host).cuda()
     bits = {"complex": cw.CWT_OUT_COMPLEX, "power": cw.CWT_OUT_POWER, "phase": cw.CWT_OUT_PHASE}
     kinds = 0
@@ -702,6 +968,8 @@ def run_plan_workload(args, name):
         kinds |= bits[o]
     popt = cw.cwt_options_init()
     popt.pad_policy = cw.CWT_PAD_SMOOTH if args.pad == "smooth" else cw.CWT_PAD_POW2
+    popt.precision = {"fp32": cw.CWT_PREC_FP32, "tc_fp16": cw.CWT_PREC_TC_FP16,
+                      "tc_bf16": cw.CWT_PREC_TC_BF16}[args.precision]
     plan = cw.cwt_plan_create(w.channels, w.samples, w.fs, w.freqs, w.n_cycles,
                               cw.CWT_WAVELET_MORLET, kinds, popt)
     info = cw.cwt_plan_info(plan)
@@ -772,6 +1040,10 @@ def run_plan_workload(args, name):
             kname = f"mr_scale_block_kernel<0, 0> (generic mixed radix; N = {N} = {rad})"
     elif N <= 16384:
         kname = f"scale_block_kernel<{N},float>"
+    elif args.precision != "fp32":
+        kname = (f"tc_scale_block_cluster_kernel<{N // 16384}, {args.precision[3:]}> (cluster of "
+                 f"{N // 16384} CTAs; radix-16 stages as mma.sync DFT products, hi/lo operands, "
+                 "FP32 accumulation)")
     else:
         kname = f"cl_scale_block_kernel<{N},float> (cluster of {N // 16384} CTAs)"
     roofline = {"kernel": kname, "bound": "hbm",
@@ -782,6 +1054,31 @@ def run_plan_workload(args, name):
                 "kernel_ms": sb_s * 1e3, "forward_fft_ms": ms_fw / max(n_fw, 1)}
 
     # end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if not getattr(args, "no_e2e", False):
+        e2e = end_to_end(cw, plan, x_host, shape, out_c, out_ph, stream, w, world, dist,
+                         args.e2e_steps if name == "fused" else 1, out_bytes_per_coef)
+    if getattr(args, "no_plain", False):
+        plain = None
+    elif name == "fused":
+        plain = plain_fp32_pipeline(cw, plan, x, out_p, w, args, flush, stream)
+    elif name == "precision" and world == 1:
+        plain = plain_fp32_chunked(cw, plan, x, out_p, out_ph, w, args, flush, stream)
+    else:
+        plain = None
+    cw.cwt_plan_destroy(plan)
+    other = (other_padding(cw, w, kinds, "pow2" if args.pad == "smooth" else "smooth", x,
+                           (out_c, out_p, out_ph), flush, stream, args)
+             if name == "fused" and world == 1 and not getattr(args, "no_other", False) else None)
+    return finish_plan_line(args, name, w, info, N, world, rank, value, ms_step, wall, clk, roofline,
+                            e2e, plain, other, coeffs_rank, x_host)
+
+
+def end_to_end(cw, plan, x_host, shape, out_c, out_ph, stream, w, world, dist, e2e_steps,
+               out_bytes_per_coef):
+    """The same metric through cwt_execute_host: pinned host input copied in and
+    the outputs written to pinned host memory, inside the timed region."""
+    import torch
     h_in = torch.from_numpy(x_host).pin_memory()
     h_c = torch.empty(shape, dtype=torch.complex64).pin_memory() if out_c is not None else None
     h_p = torch.empty(shape, dtype=torch.float32).pin_memory()
@@ -790,7 +1087,6 @@ def run_plan_workload(args, name):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e2e_steps = args.e2e_steps if name == "fused" else 1
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         cw.cwt_execute_host(plan, h_in, h_c, h_p, h_ph, stream)
@@ -799,26 +1095,27 @@ def run_plan_workload(args, name):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": coeffs_rank * world / e2e_s, "unit": UNIT,
+    e2e = {"value": w.coefficients * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(x_host.nbytes),
            "d2h_bytes_per_step": int(w.coefficients * out_bytes_per_coef),
            "ms_per_step": e2e_s * 1e3}
     del h_c, h_p, h_ph
-    plain = (plain_fp32_pipeline(cw, plan, x, out_p, w, args, flush, stream) if name == "fused"
-             else None)
-    cw.cwt_plan_destroy(plan)
-    other = (other_padding(cw, w, kinds, "pow2" if args.pad == "smooth" else "smooth", x,
-                           (out_c, out_p, out_ph), flush, stream, args)
-             if name == "fused" and world == 1 else None)
+    return e2e
 
+
+def finish_plan_line(args, name, w, info, N, world, rank, value, ms_step, wall, clk, roofline,
+                     e2e, plain, other, coeffs_rank, x_host):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tc_fp16": "f16 hi/lo, f32 accumulation",
+                      "tc_bf16": "bf16 hi/lo, f32 accumulation"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.notes, "channels": w.channels, "samples": w.samples,
                        "scales": w.scales, "fft_length": N, "padding": args.pad,
+                       "precision": args.precision,
                        "coefficients_per_step": coeffs_rank,
                        "l2": "256 MB buffer overwritten between timed steps (outside the events)",
                        "bank_ms": info.bank_ms, "wall_s_timed_region": wall,
@@ -826,21 +1123,24 @@ def run_plan_workload(args, name):
             "roofline": roofline,
             "e2e": e2e,
             "plain_fp32_gpu": plain,
-            "gpu_launches": 2 * args.steps,
+            # forward FFT + scale block per step (+ the spectrum bounds of the tensor-core path)
+            "gpu_launches": (3 if args.precision != "fp32" else 2) * args.steps,
             "clocks": clk,
         }
+        if e2e is None:
+            del line["e2e"]
         if other is not None:
             line["other_padding"] = other
-        if world == 1:
+        if world == 1 and not getattr(args, "no_cpu", False):
             line["cpu_baseline"] = cpu_baseline(w, x_host, args.cpu_channels if name == "fused" else 1, N,
-                                                n_scales=None if name == "fused" else 8)
+                                                n_scales=None if name == "fused" else 8,
+                                                min_seconds=getattr(args, "cpu_seconds", 10.0))
         if plain is not None:
             plain["speedup_of_fused"] = plain["ms_per_step"] / ms_step
         else:
             del line["plain_fp32_gpu"]
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+        return line
+    return None
 
 
 if __name__ == "__main__":

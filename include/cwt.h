@@ -99,6 +99,18 @@ typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
  * Gabor only (CWT_EUNSUPPORTED for GMW, whose support has no closed form). */
 typedef enum { CWT_EDGE_CYCLIC = 0, CWT_EDGE_LINEAR = 1 } cwt_edge_mode;
 
+/* Per-scale normalisation of the wavelet (Section "Precision" compares the
+ * coefficients with MNE-python's, Table 1).  UNIT_ENERGY: the periodised
+ * sampled wavelet has sum_m |w[m]|^2 = 1.  MNE: the convention MNE-python
+ * documents for its Morlet wavelets (each wavelet divided by sqrt(0.5) times
+ * its L2 norm), i.e. sum_m |w[m]|^2 = 2: every coefficient is sqrt(2) times
+ * the unit-energy one and every power twice.  MNE also truncates each
+ * wavelet at 5 sigma_t (an envelope below 4e-6 of its peak); the library
+ * keeps the untruncated wavelet, so coefficients differ from MNE's by that
+ * tail (a comparison with MNE itself is not made here: MNE is not part of
+ * this library's dependencies). */
+typedef enum { CWT_NORM_UNIT_ENERGY = 0, CWT_NORM_MNE = 1 } cwt_normalization;
+
 /* Kernel identifiers for the profiling counters. */
 typedef enum {
     CWT_KERNEL_BANK = 0,        /* wavelet-bank + band generation (plan creation) */
@@ -136,7 +148,13 @@ typedef struct {
 } cwt_batch_stats;
 
 typedef struct {
-    int precision;  /* cwt_precision; only CWT_PREC_FP32 is implemented */
+    int precision;  /* cwt_precision of the inverse FFTs (default FP32).  TC_FP16 and
+                       TC_BF16 run their radix-16 stages as DFT matrix products on
+                       the tensor cores with hi/lo split operands and FP32
+                       accumulation (the Cooley-Tukey factorisation of Section
+                       "Fast Fourier transform"; error within 2e-3 of the row's
+                       peak power): power-of-two N of 16384 ... 131072 only (else
+                       CWT_EUNSUPPORTED); not for cwt_execute_batch */
     int decimation; /* keep every d-th output sample, d >= 1 (default 1) */
     int pad_policy; /* cwt_pad_policy (default CWT_PAD_POW2) */
     int fft_length; /* 0: from pad_policy; else an explicit N >= samples that is a
@@ -147,7 +165,9 @@ typedef struct {
     int edge_mode;  /* cwt_edge_mode (default CWT_EDGE_CYCLIC) */
     double gmw_gamma; /* gamma of the generalized Morse wavelet (Eq. 5), > 0,
                          default 3; read only for CWT_WAVELET_GMW */
-    int reserved[8];
+    int normalization; /* cwt_normalization of each scale's wavelet (default
+                          CWT_NORM_UNIT_ENERGY) */
+    int reserved[7];
 } cwt_options;
 
 typedef struct {
@@ -170,14 +190,14 @@ typedef struct {
                                compiled for exactly this N and radix schedule (10000,
                                8000, 5000, 4000, 2500, 2000, 1000, 500),
                                else 0; the forward FFT stays on inlined_pair's kernel */
-    int reserved;
+    int precision;          /* cwt_precision of the inverse FFTs */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */
 const char *cwt_status_str(cwt_status s);
 
 /* Fill *opt with defaults: FP32, d = 1, CWT_PAD_POW2, N from the policy, F32
- * I/O, CWT_EDGE_CYCLIC, gmw_gamma 3. */
+ * I/O, CWT_EDGE_CYCLIC, gmw_gamma 3, CWT_NORM_UNIT_ENERGY. */
 cwt_status cwt_options_init(cwt_options *opt);
 
 /* Padded FFT length N for `samples` under `pad_policy` (Section "Fast Fourier
@@ -346,7 +366,10 @@ cwt_status cwt_server_destroy(cwt_server srv);
  * be < fs/2 and representable on the window's W-point grid at fs, as in
  * cwt_plan_create; else CWT_EINVAL).  CWT_EBUSY when no slot is free or its
  * device memory would exceed the budget (the refusal is counted).  Generates
- * the bank for a new fs. */
+ * the bank for a new fs and grows the server's batch buffers to hold
+ * kMaxPending (8) hops of every open stream, waiting for the batches in
+ * flight if it has to replace them.  Call cwt_stream_open, cwt_server_step
+ * and cwt_stream_close from one thread. */
 cwt_status cwt_stream_open(cwt_server srv, int channels, double fs, int *stream_id);
 
 /* Append k new samples per channel: samples is [channels][k] float32, host or
@@ -358,7 +381,10 @@ cwt_status cwt_stream_push(cwt_server srv, int stream_id, const float *samples, 
 
 /* Launch one batch with every ready hop of every open stream, asynchronously
  * on the server's own CUDA stream (two batches may be in flight; a third call
- * waits for the oldest).  *hops_launched (may be NULL) receives the count. */
+ * waits for the oldest).  *hops_launched (may be NULL) receives the count.
+ * Allocates nothing: the batch buffers were sized when the streams were
+ * admitted.  Pushes copy on a separate CUDA stream, and the batch waits only
+ * for the pushes issued before this call. */
 cwt_status cwt_server_step(cwt_server srv, int *hops_launched);
 
 /* Wait until every launched batch has completed. */
@@ -410,6 +436,20 @@ cwt_status cwt_fft(const void *d_in, void *d_out, int n, int batch, int directio
 cwt_status cwt_plan_set_profiling(cwt_plan plan, int enable);
 cwt_status cwt_plan_profile_read(cwt_plan plan, int kernel, int *launches, double *total_ms,
                                  int reset);
+
+/*
+ * cwt_measure_peak -- measured compute peak of the current GPU in TFLOP/s,
+ * the denominator of the benchmark's compute-side roofline fractions (the
+ * paper has no counterpart; a measurement aid).  what = 0: FP32 FMA
+ * throughput (8 independent fma.rn.f32 chains per thread, 8 CTAs of 256
+ * threads per SM, 2 flops per FMA); 1: mma.sync.m16n8k16 with FP16 operands
+ * and FP32 accumulation (4 independent accumulators per warp, 4096 flops per
+ * MMA), the instruction of the tensor-core inverse FFTs; 2: the same with
+ * BF16.  One warm-up and one timed launch of a few tens of milliseconds,
+ * CUDA events on the legacy default stream; synchronous.  CWT_EINVAL for an
+ * unknown `what` or NULL `tflops`.
+ */
+cwt_status cwt_measure_peak(int what, double *tflops);
 
 /*
  * cwt_execute_noalloc -- the Morlet transform of cwt_plan_create +

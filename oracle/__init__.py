@@ -39,7 +39,12 @@ def _load():
         lib.oracle_wavelet.restype = ctypes.c_int
         lib.oracle_cwt_rows.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                        ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, ctypes.c_int]
+                                        ctypes.c_int, ip, ip, ctypes.c_int, ctypes.c_double, dp, dp,
+                                        ctypes.c_int]
+        lib.oracle_wavelet_norm.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_double, dp, dp]
+        lib.oracle_wavelet_norm.restype = ctypes.c_int
         lib.oracle_cwt_rows.restype = ctypes.c_int
         lib.oracle_gmw_spectrum.argtypes = [ctypes.c_double] * 4
         lib.oracle_gmw_spectrum.restype = ctypes.c_double
@@ -79,20 +84,24 @@ def periodised_wavelet(freq, n_cycles, fs, N, wavelet="morlet", gamma=3.0):
     return re + 1j * im
 
 
-def wavelet(freq, n_cycles, fs, N, wavelet="morlet", gamma=3.0):
-    """Unit-energy N-periodised sampled wavelet of one scale (complex128)."""
+NORMS = {"unit": 1.0, "mne": 2.0}
+
+
+def wavelet(freq, n_cycles, fs, N, wavelet="morlet", gamma=3.0, normalization="unit"):
+    """N-periodised sampled wavelet of one scale (complex128) with unit energy,
+    or sum |w|^2 = 2 for normalization="mne" (MNE-python's convention)."""
     lib = _load()
     re = np.zeros(N)
     im = np.zeros(N)
-    rc = lib.oracle_wavelet(WAVELETS[wavelet], float(freq), float(n_cycles), float(gamma),
-                            float(fs), int(N), _dp(re), _dp(im))
+    rc = lib.oracle_wavelet_norm(WAVELETS[wavelet], float(freq), float(n_cycles), float(gamma),
+                                 float(fs), int(N), NORMS[normalization], _dp(re), _dp(im))
     if rc != 0:
         raise ValueError("oracle_wavelet: bad argument")
     return re + 1j * im
 
 
 def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", threads=None,
-             gamma=3.0):
+             gamma=3.0, normalization="unit"):
     """Complex CWT coefficients of the (channel, scale) pairs in `rows`.
 
     x: [C][n] real signal.  Returns complex128 [len(rows)][ceil(n/d)].
@@ -117,14 +126,15 @@ def cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation=1, wavelet="morlet", th
         threads = os.cpu_count() or 1
     rc = lib.oracle_cwt_rows(_dp(x), C, n, int(N), float(fs), _dp(freqs), _dp(n_cycles),
                              len(freqs), WAVELETS[wavelet], float(gamma), d, _ip(rc_), _ip(rs_),
-                             len(rows),
+                             len(rows), NORMS[normalization],
                              _dp(out_re), _dp(out_im), int(threads))
     if rc != 0:
         raise ValueError(f"oracle_cwt_rows failed ({rc})")
     return out_re + 1j * out_im
 
 
-def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None, gamma=3.0):
+def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None, gamma=3.0,
+        normalization="unit"):
     """Complex CWT of every row: complex128 [C][S][ceil(n/d)]."""
     x = np.asarray(x, dtype=np.float64)
     if x.ndim == 1:
@@ -132,7 +142,8 @@ def cwt(x, N, fs, freqs, n_cycles, decimation=1, wavelet="morlet", threads=None,
     C = x.shape[0]
     S = len(np.atleast_1d(freqs))
     rows = [(c, s) for c in range(C) for s in range(S)]
-    out = cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation, wavelet, threads, gamma)
+    out = cwt_rows(x, N, fs, freqs, n_cycles, rows, decimation, wavelet, threads, gamma,
+                   normalization)
     return out.reshape(C, S, -1)
 
 

@@ -52,7 +52,9 @@
  *     by the O(N^2) definition of the inverse DFT (no FFT).
  *
  *  3. Each scale is normalised to unit discrete energy,
- *         pn[m] = p[m] / sqrt(sum_m |p[m]|^2).
+ *         pn[m] = p[m] / sqrt(sum_m |p[m]|^2),
+ *     or, under MNE-python's convention (its Morlet wavelets are divided by
+ *     sqrt(0.5) times their L2 norm), to sum_m |pn[m]|^2 = 2.
  *
  *  4. The signal x[0..n) is zero-padded to N and convolved cyclically:
  *         c[t] = sum_{m=0}^{n-1} x[m] * pn[(t - m) mod N],
@@ -247,9 +249,10 @@ int oracle_periodised_wavelet(int kind, double F, double sigma, double gamma, do
     return 0;
 }
 
-/* Steps 2 + 3: the unit-energy periodised wavelet of one scale. */
-int oracle_wavelet(int kind, double F, double sigma, double gamma, double fs, int N, double *w_re,
-                   double *w_im)
+/* Steps 2 + 3: the periodised wavelet of one scale with sum_m |w[m]|^2 = norm2
+ * (1: unit energy; 2: MNE-python's convention). */
+int oracle_wavelet_norm(int kind, double F, double sigma, double gamma, double fs, int N,
+                        double norm2, double *w_re, double *w_im)
 {
     int rc = oracle_periodised_wavelet(kind, F, sigma, gamma, fs, N, w_re, w_im);
     if (rc != 0)
@@ -257,14 +260,21 @@ int oracle_wavelet(int kind, double F, double sigma, double gamma, double fs, in
     double e = 0.0;
     for (int m = 0; m < N; ++m)
         e += w_re[m] * w_re[m] + w_im[m] * w_im[m];
-    if (!(e > 0.0))
+    if (!(e > 0.0) || !(norm2 > 0.0))
         return -1;
-    double inv = 1.0 / sqrt(e);
+    double inv = sqrt(norm2 / e);
     for (int m = 0; m < N; ++m) {
         w_re[m] *= inv;
         w_im[m] *= inv;
     }
     return 0;
+}
+
+/* Steps 2 + 3 with unit energy. */
+int oracle_wavelet(int kind, double F, double sigma, double gamma, double fs, int N, double *w_re,
+                   double *w_im)
+{
+    return oracle_wavelet_norm(kind, F, sigma, gamma, fs, N, 1.0, w_re, w_im);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -327,13 +337,15 @@ static void *conv_worker(void *arg)
  *   kind     0 = Morlet, 1 = Gabor, 2 = GMW (with gamma)
  *   d        decimation (>= 1); n_out = ceil(n / d)
  *   row_c, row_s [n_rows]: channel and scale index of each requested row
+ *   norm2    sum_m |w[m]|^2 of every scale's wavelet (1 or 2, step 3)
  *   out_re, out_im [n_rows][n_out]
  *   n_threads worker threads (>= 1)
  * Returns 0 on success, -1 on a bad argument, -2 on allocation failure.
  */
 int oracle_cwt_rows(const double *x, int C, int n, int N, double fs, const double *freqs,
                     const double *n_cycles, int S, int kind, double gamma, int d, const int *row_c,
-                    const int *row_s, int n_rows, double *out_re, double *out_im, int n_threads)
+                    const int *row_s, int n_rows, double norm2, double *out_re, double *out_im,
+                    int n_threads)
 {
     if (C <= 0 || n <= 0 || N < n || S <= 0 || d < 1 || n_rows < 0 || !(fs > 0.0))
         return -1;
@@ -351,8 +363,8 @@ int oracle_cwt_rows(const double *x, int C, int n, int N, double fs, const doubl
     }
     int rc = 0;
     for (int s = 0; s < S && rc == 0; ++s)
-        rc = oracle_wavelet(kind, freqs[s], n_cycles[s], gamma, fs, N, wre + (size_t)s * N,
-                            wim + (size_t)s * N);
+        rc = oracle_wavelet_norm(kind, freqs[s], n_cycles[s], gamma, fs, N, norm2,
+                                 wre + (size_t)s * N, wim + (size_t)s * N);
     if (rc == 0) {
         conv_job J;
         J.x = x;

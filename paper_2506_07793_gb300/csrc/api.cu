@@ -85,9 +85,12 @@ cwt_status run_execute(cwt_plan_s *p, const void *sig, void *oc, void *op, void 
     cwtk::ProfEvent ev{};
     cudaError_t e = prof_begin(p, CWT_KERNEL_FORWARD_FFT, st, &ev);
     if (e == cudaSuccess) e = cwtk::launch_forward(p, sig, st);
+    const bool tc = p->precision != CWT_PREC_FP32;
+    if (e == cudaSuccess && tc) e = cwtk::launch_tc_row_bounds(p, st);
     if (e == cudaSuccess) e = prof_end(p, st, &ev);
     if (e == cudaSuccess) e = prof_begin(p, CWT_KERNEL_SCALE_BLOCK, st, &ev);
-    if (e == cudaSuccess) e = cwtk::launch_scale_block(p, oc, op, oph, st);
+    if (e == cudaSuccess)
+        e = tc ? cwtk::launch_scale_block_tc(p, oc, op, oph, st) : cwtk::launch_scale_block(p, oc, op, oph, st);
     if (e == cudaSuccess) e = prof_end(p, st, &ev);
     return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
 }
@@ -98,6 +101,8 @@ void free_plan_memory(cwt_plan_s *p) {
     cudaFree(p->bank);
     cudaFree(p->band);
     cudaFree(p->spec);
+    cudaFree(p->tc_chmax);
+    cudaFree(p->tc_wl1);
     cudaFree(p->twN);
     cudaFree(p->stage_in);
     cudaFree(p->stage_c);
@@ -135,7 +140,9 @@ const char *cwt_status_str(cwt_status s) {
 }
 
 // the Python binding mirrors this layout
-static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24, "cwt_options layout");
+static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24 &&
+                  offsetof(cwt_options, normalization) == 32,
+              "cwt_options layout");
 static_assert(sizeof(cwt_plan_info_t) == 112 && offsetof(cwt_plan_info_t, radices) == 64 &&
                   offsetof(cwt_plan_info_t, fixed_kernel) == 104,
               "cwt_plan_info_t layout");
@@ -198,11 +205,10 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     if (!cwtk::wavelet_params_ok(wavelet, n_cycles, n_freqs, o.gmw_gamma)) return CWT_EINVAL;
     if (o.decimation < 1) return CWT_EINVAL;
     if (o.io_dtype != CWT_DTYPE_F32 && o.io_dtype != CWT_DTYPE_F64) return CWT_EINVAL;
-    if (o.precision != CWT_PREC_FP32) {
-        if (o.precision == CWT_PREC_TC_FP16 || o.precision == CWT_PREC_TC_BF16) return CWT_EUNSUPPORTED;
-        return CWT_EINVAL;
-    }
+    const bool tc = o.precision == CWT_PREC_TC_FP16 || o.precision == CWT_PREC_TC_BF16;
+    if (o.precision != CWT_PREC_FP32 && !tc) return CWT_EINVAL;
     if (o.edge_mode != CWT_EDGE_CYCLIC && o.edge_mode != CWT_EDGE_LINEAR) return CWT_EINVAL;
+    if (o.normalization != CWT_NORM_UNIT_ENERGY && o.normalization != CWT_NORM_MNE) return CWT_EINVAL;
     // linear edges: pad by the widest wavelet's support radius R (Gaussian
     // envelope below 1e-9 of its peak beyond R samples) so that nothing wraps
     int pad_extra = 0;
@@ -233,6 +239,8 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         if (st != CWT_OK) return st;
     }
     if ((long long)channels * n_freqs > (1ll << 30)) return CWT_EUNSUPPORTED;
+    // tensor-core inverse FFTs: power-of-two rows of 16384 .. 131072 points
+    if (tc && (!is_pow2(N) || N < cwtk::kMaxFft || N > cwtk::kMaxClusterFft)) return CWT_EUNSUPPORTED;
     if (!cwtk::scales_on_grid(wavelet, freqs_hz, n_cycles, n_freqs, o.gmw_gamma, fs, N))
         return CWT_EINVAL;
 
@@ -245,8 +253,9 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->d = o.decimation;
     p->mr = !is_pow2(N);
     if (p->mr) cwtk::mr_schedule(N, &p->sch);
-    int f = 1;
-    while (!p->mr && (p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
+    p->precision = o.precision;
+    int f = 1;  // no spectral fold on the cluster and tensor-core paths
+    while (!p->mr && !tc && (p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
     p->fold = f;
     p->M = N / f;
     p->sub = p->d / f;
@@ -255,6 +264,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->wavelet = wavelet;
     p->gmw_gamma = o.gmw_gamma;
     p->pad_extra = pad_extra;
+    p->norm2 = o.normalization == CWT_NORM_MNE ? 2.0 : 1.0;
     p->outputs = output_kinds;
     p->io = o.io_dtype;
     p->freqs.assign(freqs_hz, freqs_hz + n_freqs);
@@ -278,6 +288,13 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         p->bytes += sizeof(float2) * (size_t)N;
     }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
+    if (e == cudaSuccess && tc) {
+        e = cudaMalloc(&p->tc_chmax, sizeof(float) * (size_t)channels);
+        if (e == cudaSuccess) e = cudaMalloc(&p->tc_wl1, sizeof(float) * (size_t)n_freqs);
+        p->bytes += sizeof(float) * ((size_t)channels + n_freqs);
+        if (e == cudaSuccess) e = cwtk::launch_tc_wl1(p, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) {
         cwt_status s = fail_cuda(p, e);
@@ -331,6 +348,7 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->output_kinds = p->outputs;
     info->workspace_bytes = p->bytes + p->stage_bytes;
     info->bank_ms = p->bank_ms;
+    info->precision = p->precision;
     if (p->mr) describe_schedule(p->sch, info->radices, info->inlined_pair, &info->fixed_kernel);
     return CWT_OK;
 }
@@ -437,7 +455,8 @@ cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, 
                wph = p->outputs & CWT_OUT_PHASE;
     if (wc != (d_complex != nullptr) || wp != (d_power != nullptr) || wph != (d_phase != nullptr))
         return CWT_EINVAL;
-    if (p->io != CWT_DTYPE_F32 || p->mr) return CWT_EUNSUPPORTED;  // batches pad each epoch to pow2
+    // batches pad each epoch to pow2 and run FP32 inverse FFTs
+    if (p->io != CWT_DTYPE_F32 || p->mr || p->precision != CWT_PREC_FP32) return CWT_EUNSUPPORTED;
     for (int i = 0; i < n_epochs; ++i) {
         const cwt_epoch &e = epochs[i];
         if (e.samples < 1 || e.samples > p->n || e.in_offset < 0 || e.out_offset < 0) return CWT_EINVAL;

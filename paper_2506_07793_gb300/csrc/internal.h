@@ -48,6 +48,7 @@ struct cwt_plan_s {
     double fs = 0;
     int wavelet = 0;
     double gmw_gamma = 3.0;  // gamma of Eq. 5 (CWT_WAVELET_GMW only)
+    double norm2 = 1.0;      // sum_m |w[m]|^2 of each scale (1: unit energy, 2: MNE's convention)
     int pad_extra = 0;       // linear edges: samples added before padding (R + 1)
     unsigned grid_ok_lengths = 0;  // batch: bit log2(N_e) set once every scale passed
                                    // the grid check at that epoch length
@@ -61,6 +62,9 @@ struct cwt_plan_s {
     float *bank = nullptr;    // [S][N] W_s[k] / N (real)
     int *band = nullptr;      // [S][2]: start, length
     float2 *spec = nullptr;   // [C][N] forward spectra (workspace)
+    int precision = CWT_PREC_FP32;  // cwt_precision of the inverse FFTs
+    float *tc_chmax = nullptr;  // tensor-core plans: [C] max |Re|, |Im| of each spectrum
+    float *tc_wl1 = nullptr;    // tensor-core plans: [S] sum of |W_s| over the band
     const float2 *tw = nullptr;
     size_t bytes = 0;
     double bank_ms = 0;
@@ -165,6 +169,12 @@ cudaError_t launch_scale_block(const cwt_plan_s *p, void *out_c, void *out_p, vo
                                cudaStream_t st);
 cudaError_t launch_fft(const float2 *in, float2 *out, int log2n, int batch, int sign,
                        const float2 *tw, cudaStream_t st);
+// Tensor-core inverse FFTs (tc_scale_block.cu): per-channel spectrum bounds
+// after the forward FFT, per-scale band sums at plan creation, the scale block.
+cudaError_t launch_tc_row_bounds(const cwt_plan_s *p, cudaStream_t st);
+cudaError_t launch_tc_wl1(const cwt_plan_s *p, cudaStream_t st);
+cudaError_t launch_scale_block_tc(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
+                                  cudaStream_t st);
 // Rows of 2^15..2^17 points on thread-block clusters (cluster.cu).
 cudaError_t launch_forward_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 cudaError_t launch_scale_block_cluster(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,

@@ -22,7 +22,14 @@
 //    memory.
 //  * Admission: a stream is refused (CWT_EBUSY) when no slot is free or its
 //    device memory (ring + its share of the batch buffers) would exceed the
-//    server's budget.
+//    server's budget.  The batch buffers of both in-flight slots are grown at
+//    admission to the bound of every open stream (kMaxPending hops each), so
+//    cwt_server_step never allocates.
+//  * Pushes copy into the rings on a copy stream of their own; each batch
+//    waits for an event recorded there, so a push never queues behind a batch
+//    in flight.  A push cannot overwrite ring samples that a batch in flight
+//    still reads: with at most kMaxPending hops pending, the oldest window in
+//    flight starts after the last sample the push overwrites.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -176,7 +183,10 @@ struct cwt_server_s {
     long long coeffs_done = 0;
     double first_ready = -1, last_done = -1;
     const float2 *tw = nullptr;
-    cudaStream_t st = nullptr;  // the server's own CUDA stream
+    cudaStream_t st = nullptr;   // the server's own CUDA stream (batches)
+    cudaStream_t cst = nullptr;  // pushes into the rings
+    cudaEvent_t pushed = nullptr;  // recorded on cst before each batch
+    size_t bound_items = 0, bound_out = 0;  // batch-buffer bound of the open streams
     std::string last_error;
 };
 
@@ -257,6 +267,39 @@ cudaError_t bank_for(cwt_server_s *srv, double fs, int *idx) {
     return cudaSuccess;
 }
 
+// Grow both slots' batch buffers to hold `items` work items and `outf`
+// output floats (waiting for a slot's batch in flight before replacing its
+// buffers).  Called at admission, never by cwt_server_step.
+cudaError_t grow_slots(cwt_server_s *srv, size_t items, size_t outf) {
+    for (Slot &sl : srv->slots) {
+        if (sl.items_cap >= items && sl.out_cap >= outf) continue;
+        if (sl.busy) {
+            cudaError_t e = cudaEventSynchronize(sl.done);
+            if (e != cudaSuccess) return e;
+        }
+        if (sl.items_cap < items) {
+            cudaFree(sl.d_items);
+            if (sl.h_items) cudaFreeHost(sl.h_items);
+            sl.d_items = nullptr;
+            sl.h_items = nullptr;
+            sl.items_cap = 0;
+            cudaError_t e = cudaMalloc(&sl.d_items, sizeof(StreamItem) * items);
+            if (e == cudaSuccess) e = cudaMallocHost(&sl.h_items, sizeof(StreamItem) * items);
+            if (e != cudaSuccess) return e;
+            sl.items_cap = items;
+        }
+        if (sl.out_cap < outf) {
+            cudaFree(sl.d_out);
+            sl.d_out = nullptr;
+            sl.out_cap = 0;
+            cudaError_t e = cudaMalloc(&sl.d_out, sizeof(float) * outf);
+            if (e != cudaSuccess) return e;
+            sl.out_cap = outf;
+        }
+    }
+    return cudaSuccess;
+}
+
 size_t stream_dev_bytes(const cwt_server_s *srv, int C, int H) {
     const size_t ring = sizeof(float) * (size_t)C * (kSW + (size_t)kMaxPending * H);
     const size_t outs = sizeof(float) * (size_t)C * srv->S * H * kMaxPending * kSlots;
@@ -329,12 +372,18 @@ cwt_status cwt_server_create(cwt_server *out, const double *freqs_hz, const doub
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = device_twiddles(&s->tw);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->pushed, cudaEventDisableTiming);
     static std::atomic<unsigned> attr{0};
     if (e == cudaSuccess) e = ensure_smem_attr(stream_kernel, kStreamSmem, &attr);
     for (int i = 0; i < kSlots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cwt_status r = cuda_fail(s, e);
         if (s->st) cudaStreamDestroy(s->st);
+        if (s->cst) cudaStreamDestroy(s->cst);
+        if (s->pushed) cudaEventDestroy(s->pushed);
+        for (auto &sl : s->slots)
+            if (sl.done) cudaEventDestroy(sl.done);
         delete s;
         return r;
     }
@@ -346,6 +395,7 @@ cwt_status cwt_server_destroy(cwt_server s) {
     if (!s) return CWT_OK;
     {
         Guard g(s->device);
+        cudaStreamSynchronize(s->cst);
         cudaStreamSynchronize(s->st);
         for (auto &st : s->streams) {
             cudaFree(st.d_ring);
@@ -362,6 +412,8 @@ cwt_status cwt_server_destroy(cwt_server s) {
             if (sl.done) cudaEventDestroy(sl.done);
         }
         cudaStreamDestroy(s->st);
+        cudaStreamDestroy(s->cst);
+        cudaEventDestroy(s->pushed);
     }
     delete s;
     return CWT_OK;
@@ -407,9 +459,13 @@ cwt_status cwt_stream_open(cwt_server s, int channels, double fs, int *stream_id
     st.queue_slots = kMaxPending * 2;
     const size_t ring_b = sizeof(float) * (size_t)channels * st.cap;
     const size_t q_b = sizeof(float) * (size_t)channels * s->S * H * st.queue_slots;
+    // zeroed on the copy stream, so that the stream's pushes land after it
     if (e == cudaSuccess) e = cudaMalloc(&st.d_ring, ring_b);
-    if (e == cudaSuccess) e = cudaMemsetAsync(st.d_ring, 0, ring_b, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st.d_ring, 0, ring_b, s->cst);
     if (e == cudaSuccess) e = cudaMallocHost(&st.h_queue, q_b);
+    const size_t items = s->bound_items + (size_t)channels * kMaxPending;
+    const size_t outf = s->bound_out + (size_t)channels * s->S * H * kMaxPending;
+    if (e == cudaSuccess) e = grow_slots(s, items, outf);
     if (e != cudaSuccess) {
         cudaFree(st.d_ring);
         if (st.h_queue) cudaFreeHost(st.h_queue);
@@ -418,6 +474,8 @@ cwt_status cwt_stream_open(cwt_server s, int channels, double fs, int *stream_id
         s->dev_bytes -= need;
         return cuda_fail(s, e);
     }
+    s->bound_items = items;
+    s->bound_out = outf;
     std::lock_guard<std::mutex> lk(s->mu);
     for (int i = st.queue_slots - 1; i >= 0; --i) st.free_slots.push_back(i);
     st.dev_bytes = need;
@@ -450,10 +508,10 @@ cwt_status cwt_stream_push(cwt_server s, int id, const float *samples, int k) {
     const int first = std::min(k, st.cap - pos);
     cudaError_t e = cudaMemcpy2DAsync(st.d_ring + pos, sizeof(float) * st.cap, samples,
                                       sizeof(float) * k, sizeof(float) * first, st.C,
-                                      cudaMemcpyDefault, s->st);
+                                      cudaMemcpyDefault, s->cst);
     if (e == cudaSuccess && first < k)
         e = cudaMemcpy2DAsync(st.d_ring, sizeof(float) * st.cap, samples + first, sizeof(float) * k,
-                              sizeof(float) * (k - first), st.C, cudaMemcpyDefault, s->st);
+                              sizeof(float) * (k - first), st.C, cudaMemcpyDefault, s->cst);
     if (e != cudaSuccess) return cuda_fail(s, e);
     std::lock_guard<std::mutex> lk(s->mu);
     st.pushed = end;
@@ -520,24 +578,16 @@ cwt_status cwt_server_step(cwt_server s, int *hops_launched) {
     }
     if (hops_launched) *hops_launched = (int)hops.size();
     if (items.empty()) return CWT_OK;
-    cudaError_t e = cudaSuccess;
-    if (items.size() > sl.items_cap) {
-        cudaFree(sl.d_items);
-        if (sl.h_items) cudaFreeHost(sl.h_items);
-        sl.d_items = nullptr;
-        sl.h_items = nullptr;
-        e = cudaMalloc(&sl.d_items, sizeof(StreamItem) * items.size());
-        if (e == cudaSuccess) e = cudaMallocHost(&sl.h_items, sizeof(StreamItem) * items.size());
-        if (e != cudaSuccess) return cuda_fail(s, e);
-        sl.items_cap = items.size();
+    // the slot buffers were sized at admission for kMaxPending hops of every
+    // open stream, which bounds any batch: nothing is allocated here
+    if (items.size() > sl.items_cap || out_floats > sl.out_cap) {
+        s->last_error = "batch exceeds the buffers sized at admission";
+        return CWT_ECUDA;
     }
-    if (out_floats > sl.out_cap) {
-        cudaFree(sl.d_out);
-        sl.d_out = nullptr;
-        e = cudaMalloc(&sl.d_out, sizeof(float) * out_floats);
-        if (e != cudaSuccess) return cuda_fail(s, e);
-        sl.out_cap = out_floats;
-    }
+    // the batch reads samples pushed on the copy stream
+    cudaError_t e = cudaEventRecord(s->pushed, s->cst);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->st, s->pushed, 0);
+    if (e != cudaSuccess) return cuda_fail(s, e);
     // per-channel output blocks: hop block base + c * S * H
     {
         size_t i = 0;
@@ -609,8 +659,10 @@ cwt_status cwt_stream_close(cwt_server s, int id) {
     Guard g(s->device);
     if (!g.ok) return CWT_ECUDA;
     if (!s->streams[id].open) return CWT_EINVAL;
-    // let its launched hops finish (they write its host queue), then free it
-    cudaError_t e = cudaStreamSynchronize(s->st);
+    // let its pushes and launched hops finish (they write its ring and host
+    // queue), then free it
+    cudaError_t e = cudaStreamSynchronize(s->cst);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda_fail(s, e);
     float *ring = nullptr, *queue = nullptr;
     {
@@ -619,6 +671,8 @@ cwt_status cwt_stream_close(cwt_server s, int id) {
         ring = st.d_ring;
         queue = st.h_queue;
         s->dev_bytes -= st.dev_bytes;
+        s->bound_items -= (size_t)st.C * kMaxPending;
+        s->bound_out -= (size_t)st.C * s->S * st.H * kMaxPending;
         st = Stream();
     }
     cudaFree(ring);

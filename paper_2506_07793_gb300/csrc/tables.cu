@@ -15,7 +15,8 @@
 //     P[k] = sum_q G((k/N + q) fs).
 // Each scale is normalised to unit discrete energy through Parseval,
 // sum_m |w[m]|^2 = (1/N) sum_k |P[k]|^2, and the 1/N of the inverse FFT is
-// folded in:  bank[k] = P[k] / sqrt(N * sum_k P[k]^2).
+// folded in:  bank[k] = P[k] / sqrt(N * sum_k P[k]^2) (times sqrt(2) under
+// MNE-python's convention, sum_m |w[m]|^2 = 2).
 // The constant prefactors of Eq. 3 (c_sigma, pi^(-1/4)) cancel in the
 // normalisation.  The spectrum is real because psi(-t) = conj(psi(t)).
 //
@@ -115,7 +116,7 @@ bank_raw_kernel(int N, double fs, const double *__restrict__ F, const double *__
 
 // One CTA per scale: normalise, round to FP32, find the band.
 __global__ void __launch_bounds__(kBankThreads)
-bank_finish_kernel(int N, int nblk, const double *__restrict__ raw,
+bank_finish_kernel(int N, int nblk, double norm2, const double *__restrict__ raw,
                    const double *__restrict__ partial, float *__restrict__ bank,
                    int *__restrict__ band) {
     __shared__ double sd[kBankThreads];
@@ -131,7 +132,8 @@ bank_finish_kernel(int N, int nblk, const double *__restrict__ raw,
     }
     __syncthreads();
     const double energy = sd[0];
-    const double scale = energy > 0.0 ? 1.0 / sqrt((double)N * energy) : 0.0;
+    // sum_m |w[m]|^2 = norm2: Parseval over the N bins, 1/N of the inverse FFT folded in
+    const double scale = energy > 0.0 ? sqrt(norm2 / ((double)N * energy)) : 0.0;
     __syncthreads();
     double mx = 0.0;
     for (int k = threadIdx.x; k < N; k += kBankThreads) {
@@ -237,7 +239,7 @@ cudaError_t launch_bank_n(const cwt_plan_s *p, int N, float *bank, int *band, cu
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        bank_finish_kernel<<<S, kBankThreads, 0, st>>>(N, nblk, raw, partial, bank, band);
+        bank_finish_kernel<<<S, kBankThreads, 0, st>>>(N, nblk, p->norm2, raw, partial, bank, band);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(t1, st);

@@ -29,6 +29,7 @@ CWT_OUT_COMPLEX, CWT_OUT_POWER, CWT_OUT_PHASE = 1, 2, 4
 CWT_PREC_FP32, CWT_PREC_TC_FP16, CWT_PREC_TC_BF16 = 0, 1, 2
 CWT_DTYPE_F32, CWT_DTYPE_F64 = 0, 1
 CWT_PAD_POW2, CWT_PAD_SMOOTH = 0, 1
+CWT_NORM_UNIT_ENERGY, CWT_NORM_MNE = 0, 1
 CWT_KERNEL_BANK, CWT_KERNEL_FORWARD_FFT, CWT_KERNEL_SCALE_BLOCK, CWT_KERNEL_BATCH = 0, 1, 2, 3
 
 
@@ -36,7 +37,8 @@ class cwt_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("decimation", ctypes.c_int),
                 ("pad_policy", ctypes.c_int), ("fft_length", ctypes.c_int),
                 ("io_dtype", ctypes.c_int), ("edge_mode", ctypes.c_int),
-                ("gmw_gamma", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+                ("gmw_gamma", ctypes.c_double), ("normalization", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class cwt_plan_info_t(ctypes.Structure):
@@ -46,7 +48,7 @@ class cwt_plan_info_t(ctypes.Structure):
                 ("io_dtype", ctypes.c_int), ("output_kinds", ctypes.c_uint),
                 ("workspace_bytes", ctypes.c_size_t), ("bank_ms", ctypes.c_double),
                 ("radices", ctypes.c_int * 8), ("inlined_pair", ctypes.c_int * 2),
-                ("fixed_kernel", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("fixed_kernel", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class cwt_epoch(ctypes.Structure):
@@ -106,6 +108,7 @@ _sig("cwt_execute", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("cwt_execute_host", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp])
 _sig("cwt_plan_bank", ctypes.c_int, [_vp, _fp, _ip, _ip])
 _sig("cwt_fft", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp])
+_sig("cwt_measure_peak", ctypes.c_int, [ctypes.c_int, _dp])
 _sig("cwt_execute_noalloc", ctypes.c_int,
      [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp])
 _sig("cwt_execute_batch", ctypes.c_int,
@@ -249,6 +252,13 @@ def cwt_fft(d_in, d_out, n, batch, direction, stream=None):
                         _stream(stream)), "cwt_fft")
 
 
+def cwt_measure_peak(what):
+    """Measured TFLOP/s of the current GPU: 0 FP32 FMA, 1 mma.sync FP16, 2 mma.sync BF16."""
+    v = ctypes.c_double()
+    _check(_lib.cwt_measure_peak(int(what), ctypes.byref(v)), "cwt_measure_peak")
+    return v.value
+
+
 def cwt_execute_noalloc(signal, channels, samples, fs, freqs_hz, n_cycles, complex_out=None,
                         power_out=None, phase_out=None, stream=None):
     """The transform without any GPU allocation (for callers that may not
@@ -317,8 +327,11 @@ class CWT:
 
     def __init__(self, channels, samples, fs, freqs, n_cycles, outputs=("power",),
                  wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2",
-                 gmw_gamma=3.0, edge="cyclic"):
+                 gmw_gamma=3.0, edge="cyclic", precision="fp32", normalization="unit"):
         opt = cwt_options_init()
+        opt.normalization = {"unit": CWT_NORM_UNIT_ENERGY, "mne": CWT_NORM_MNE}[normalization]
+        opt.precision = {"fp32": CWT_PREC_FP32, "tc_fp16": CWT_PREC_TC_FP16,
+                         "tc_bf16": CWT_PREC_TC_BF16}[precision]
         opt.decimation = int(decimation)
         opt.pad_policy = {"pow2": CWT_PAD_POW2, "smooth": CWT_PAD_SMOOTH}[pad]
         opt.gmw_gamma = float(gmw_gamma)

@@ -89,6 +89,7 @@ BAD = [
     dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
     dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]), dict(edge=2), dict(edge=-1),
     dict(edge=1, fft_length=128),  # linear edges need N >= n + R + 1 (here 100 + 363 + 1)
+    dict(norm=2), dict(norm=-1),
     # a carrier far below the first DFT bin: 1.5 Hz with sigma 7 in a 32-point
     # window at 500 Hz (first bin 15.6 Hz) has a spectrum below 1e-150 on every
     # bin, so its unit-energy normalisation would underflow
@@ -102,12 +103,14 @@ BAD = [
 @pytest.mark.parametrize("bad", BAD)
 def test_invalid_arguments_rejected_before_cuda(lib, bad):
     a = dict(channels=2, samples=100, fs=500.0, freqs=[10.0, 20.0], n_cycles=[7.0, 7.0],
-             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0, edge=0)
+             wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0, edge=0,
+             norm=0)
     a.update(bad)
     o = lib.cwt_options_init()
     o.decimation, o.io_dtype, o.precision, o.fft_length = a["decimation"], a["io"], a["precision"], a["fft_length"]
     o.gmw_gamma = a["gamma"]
     o.edge_mode = a["edge"]
+    o.normalization = a["norm"]
     f = np.asarray(a["freqs"], dtype=np.float64)
     c = np.asarray(a["n_cycles"], dtype=np.float64)
     if len(c) != len(f):
@@ -124,6 +127,7 @@ def test_option_struct_layout(lib):
     assert ctypes.sizeof(o) == 64 and type(o).gmw_gamma.offset == 24
     assert o.gmw_gamma == 3.0 and o.decimation == 1
     assert type(o).edge_mode.offset == 20 and o.edge_mode == lib.CWT_EDGE_CYCLIC
+    assert type(o).normalization.offset == 32 and o.normalization == lib.CWT_NORM_UNIT_ENERGY
     assert ctypes.sizeof(lib.cwt_plan_info_t) == 112 and lib.cwt_plan_info_t.radices.offset == 64
     assert lib.cwt_plan_info_t.fixed_kernel.offset == 104
     so = lib.cwt_server_options_init()
@@ -145,6 +149,8 @@ def test_linear_edges_unsupported_for_gmw_and_too_long(lib):
 
 @pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long"])
 def test_unsupported_requests(lib, what):
+    """The tensor-core inverse FFTs cover power-of-two N of 16384 .. 131072
+    only (here N = 128); 140000 samples exceed the longest padding."""
     o = lib.cwt_options_init()
     wavelet, samples = 0, 100
     if what == "tc_fp16":

@@ -31,11 +31,12 @@ def lib():
 
 
 def run_gpu(lib, x, fs, freqs, cycles, outputs, dtype="f32", decimation=1, wavelet="morlet",
-            fft_length=0, pad="pow2", gmw_gamma=3.0, edge="cyclic"):
+            fft_length=0, pad="pow2", gmw_gamma=3.0, edge="cyclic", normalization="unit"):
     import torch
     C, n = x.shape
     t = lib.CWT(C, n, fs, freqs, cycles, outputs=outputs, dtype=dtype, decimation=decimation,
-                wavelet=wavelet, fft_length=fft_length, pad=pad, gmw_gamma=gmw_gamma, edge=edge)
+                wavelet=wavelet, fft_length=fft_length, pad=pad, gmw_gamma=gmw_gamma, edge=edge,
+                normalization=normalization)
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = t(xt)
     torch.cuda.synchronize()
@@ -538,3 +539,16 @@ def test_explicit_smooth_fft_length(lib, N):
     res, got_N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power", "phase"), fft_length=N)
     assert got_N == N
     check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
+
+
+@pytest.mark.parametrize("pad,edge", [("pow2", "cyclic"), ("smooth", "cyclic"), ("pow2", "linear")])
+def test_mne_normalisation(lib, pad, edge):
+    """MNE-python's wavelet normalisation (sum |w|^2 = 2) on every row, against
+    the oracle under the same convention, including linear edges (MNE's own
+    "same"-mode convolution)."""
+    fs, n = 1000.0, 3000
+    freqs, cycles = np.array([4.0, 12.0, 40.0, 90.0]), np.array([5.0, 7.0, 7.0, 9.0])
+    x = eeg(1300, 2, n, fs, np.float32)
+    res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), pad=pad, edge=edge,
+                     normalization="mne")
+    check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, normalization="mne"))

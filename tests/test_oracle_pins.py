@@ -326,3 +326,26 @@ def test_unresolved_route_is_taken_and_resolved_route_kept():
         expected = fs * a * np.sqrt(2 * PI) * morlet_closed_form(F, sigma, fs, N)
         P = np.fft.fft(p)
         assert np.abs(P - expected).max() <= 1e-11 * np.abs(expected).max()
+
+
+@pytest.mark.parametrize("F,sigma,fs,N", [(10.0, 7.0, 500.0, 4096), (3.0, 3.0, 250.0, 2048),
+                                          (40.0, 10.0, 1000.0, 4096)])
+def test_mne_normalisation_closed_form(F, sigma, fs, N):
+    """MNE-python's convention (sum |w|^2 = 2) against the closed-form energy of
+    a well-sampled Gaussian-windowed complex sinusoid with the zero-mean term:
+    sum_m |psi(m / fs)|^2 = fs * a sqrt(pi) (1 + kappa^2 - 2 kappa exp(-sigma^2 / 4))
+    (Riemann sum of the integral; aliasing and truncation are below 1e-12 for
+    these cases), so w_mne = p * sqrt(2 / that)."""
+    a = sigma / (2 * PI * F)
+    kappa = np.exp(-0.5 * sigma**2)
+    energy = fs * a * np.sqrt(PI) * (1 + kappa**2 - 2 * kappa * np.exp(-sigma**2 / 4))
+    p = oracle.periodised_wavelet(F, sigma, fs, N)
+    w = oracle.wavelet(F, sigma, fs, N, normalization="mne")
+    assert np.abs(w - p * np.sqrt(2.0 / energy)).max() <= 1e-10 * np.abs(w).max()
+    wu = oracle.wavelet(F, sigma, fs, N)
+    assert np.abs(w - np.sqrt(2.0) * wu).max() <= 1e-13
+    # and the coefficients scale by sqrt(2), power by 2
+    x = np.random.default_rng(5).standard_normal((1, 300))
+    cu = oracle.cwt(x, N, fs, [F], [sigma])
+    cm = oracle.cwt(x, N, fs, [F], [sigma], normalization="mne")
+    assert np.abs(cm - np.sqrt(2.0) * cu).max() <= 1e-12 * np.abs(cm).max()
