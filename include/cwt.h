@@ -470,18 +470,24 @@ cwt_status cwt_measure_peak(int what, double *tflops);
  *   d_complex  device [channels][n_freqs][samples] complex64, or NULL
  *   d_power, d_phase  device [channels][n_freqs][samples] float32, or NULL
  *              (at least one output non-NULL; all 16-byte aligned)
- * Size limit: with N = cwt_fft_length(samples), the request must satisfy
- *   1 MiB + 256-byte-rounded(16*S + 8*S*ceil(N/256) + 8*S + 4*S*N) + 8*C*N
- *       <= CWT_NOALLOC_SCRATCH_BYTES   (S = n_freqs, C = channels),
- * e.g. 64 channels x 10000 samples x 100 scales fits; larger requests return
- * CWT_EINVAL before any device work.
+ * Size limit: with N = cwt_fft_length(samples), S = n_freqs, C = channels
+ * and r(x) = x rounded up to a multiple of 256 bytes, the request must satisfy
+ *   1 MiB + r(16 S) + r(8 S ceil(N/256)) + r(8 S) + r(4 S N) + 8 C N
+ *       <= CWT_NOALLOC_SCRATCH_BYTES
+ * (each region of the array starts on a 256-byte boundary), e.g. 64 channels
+ * x 10000 samples x 100 scales fits; larger requests return CWT_EINVAL
+ * before any device work.
  * The first call on a device (the current device) resolves the array's device
  * address and writes its twiddle table, then waits for that on `stream`; make
- * that first call before any stream capture.  Every call reuses the same array
- * and overwrites everything it reads, so nothing needs clearing between
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: do not call this entry point again on a device after
+ * cudaDeviceReset.  Every call copies freqs_hz and n_cycles into the array
+ * (so the caller may reuse them as soon as the call returns), reuses the same
+ * array and overwrites everything it reads, so nothing needs clearing between
  * calls; calls that overlap on the GPU (unordered streams, other host
- * threads) race on it and must be serialised by the caller.  Asynchronous on
- * `stream` after the first call.
+ * threads) race on it and must be serialised by the caller.  Its kernels run
+ * on `stream`; the call returns without waiting for them (except the first
+ * call's set-up).
  */
 #define CWT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 cwt_status cwt_execute_noalloc(const float *d_signal, int channels, int samples, double fs,

@@ -276,21 +276,21 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     const size_t bank_b = sizeof(float) * (size_t)n_freqs * N;
     const size_t band_b = sizeof(int) * 2 * (size_t)n_freqs;
     const size_t spec_b = sizeof(float2) * (size_t)channels * N;
-    if (e == cudaSuccess) e = cudaMalloc(&p->bank, bank_b);
-    if (e == cudaSuccess) e = cudaMalloc(&p->band, band_b);
-    if (e == cudaSuccess) e = cudaMalloc(&p->spec, spec_b);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&p->bank, bank_b);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&p->band, band_b);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&p->spec, spec_b);
     p->bytes = bank_b + band_b + spec_b;
     cudaStream_t st = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess && p->mr) {
-        e = cudaMalloc(&p->twN, sizeof(float2) * (size_t)N);
+        e = cwtk::dmalloc(&p->twN, sizeof(float2) * (size_t)N);
         if (e == cudaSuccess) e = cwtk::make_twiddles_n(N, p->twN, st);
         p->bytes += sizeof(float2) * (size_t)N;
     }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
     if (e == cudaSuccess && tc) {
-        e = cudaMalloc(&p->tc_chmax, sizeof(float) * (size_t)channels);
-        if (e == cudaSuccess) e = cudaMalloc(&p->tc_wl1, sizeof(float) * (size_t)n_freqs);
+        e = cwtk::dmalloc(&p->tc_chmax, sizeof(float) * (size_t)channels);
+        if (e == cudaSuccess) e = cwtk::dmalloc(&p->tc_wl1, sizeof(float) * (size_t)n_freqs);
         p->bytes += sizeof(float) * ((size_t)channels + n_freqs);
         if (e == cudaSuccess) e = cwtk::launch_tc_wl1(p, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -413,10 +413,10 @@ cwt_status cwt_execute_host(cwt_plan p, const void *h_signal, void *h_complex, v
     const size_t out_b = eb * (size_t)p->C * p->S * p->n_out;
     cudaError_t e = cudaSuccess;
     if (!p->stage_in) {
-        e = cudaMalloc(&p->stage_in, in_b);
-        if (e == cudaSuccess && wc) e = cudaMalloc(&p->stage_c, 2 * out_b);
-        if (e == cudaSuccess && wp) e = cudaMalloc(&p->stage_p, out_b);
-        if (e == cudaSuccess && wph) e = cudaMalloc(&p->stage_ph, out_b);
+        e = cwtk::dmalloc(&p->stage_in, in_b);
+        if (e == cudaSuccess && wc) e = cwtk::dmalloc(&p->stage_c, 2 * out_b);
+        if (e == cudaSuccess && wp) e = cwtk::dmalloc(&p->stage_p, out_b);
+        if (e == cudaSuccess && wph) e = cwtk::dmalloc(&p->stage_ph, out_b);
         if (e != cudaSuccess) {
             cudaFree(p->stage_in);
             cudaFree(p->stage_c);

@@ -142,7 +142,7 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
     BatchState *b = p->batch;
     cudaError_t e = cudaSuccess;
     if (!b->d_counter) {
-        e = cudaMalloc(&b->d_counter, sizeof(int));
+        e = cwtk::dmalloc(&b->d_counter, sizeof(int));
         if (e != cudaSuccess) return e;
     }
     // banks for every padded length in the batch (generated once per length)
@@ -154,8 +154,8 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         while (N < ep.samples + p->pad_extra) N <<= 1;
         const int L = ilog2c(N);
         if (!b->bank[L]) {
-            e = cudaMalloc(&b->bank[L], sizeof(float) * (size_t)S * N);
-            if (e == cudaSuccess) e = cudaMalloc(&b->band[L], sizeof(int) * 2 * (size_t)S);
+            e = cwtk::dmalloc(&b->bank[L], sizeof(float) * (size_t)S * N);
+            if (e == cudaSuccess) e = cwtk::dmalloc(&b->band[L], sizeof(int) * 2 * (size_t)S);
             if (e == cudaSuccess) e = launch_bank_n(p, N, b->bank[L], b->band[L], st, nullptr);
             if (e != cudaSuccess) return e;
             b->bytes += sizeof(float) * (size_t)S * N + sizeof(int) * 2 * (size_t)S;
@@ -192,7 +192,7 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         if (items.size() > b->items_cap) {
             cudaFree(b->d_items);
             b->d_items = nullptr;
-            e = cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size());
+            e = cwtk::dmalloc(&b->d_items, sizeof(BatchItem) * items.size());
             if (e != cudaSuccess) return e;
             b->items_cap = items.size();
         }

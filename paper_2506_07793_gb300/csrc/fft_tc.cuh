@@ -145,80 +145,84 @@ __device__ __forceinline__ void tc_dft16_afrag(uint32_t (&ahi)[2][2][4], uint32_
 // cores: bh/bl are this lane's B fragments (points t, t+4, t+8, t+12 of
 // butterfly g, twiddled and split), acc receives outputs g and g+8 of
 // butterflies 2t and 2t+1 (acc[0][*] real parts, acc[1][*] imaginary parts;
-// index r: 0/1 output g of butterfly 2t/2t+1, 2/3 output g+8).
+// index r: 0/1 output g of butterfly 2t/2t+1, 2/3 output g+8).  The small
+// products (A_hi B_lo, A_lo B_hi) and A_hi B_hi run as two independent
+// accumulation chains per m-tile, summed at the end.
 template <class T>
 __device__ __forceinline__ void tc_dft16_mma(float (&acc)[2][4], const uint32_t (&ahi)[2][2][4],
                                              const uint32_t (&alo)[2][2][4], const uint32_t (&bh)[4],
                                              const uint32_t (&bl)[4]) {
     __syncwarp();  // the operands may come from divergent paths; mma.sync needs the whole warp
+    float lo[2][4];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[mt][r] = 0.f;
+        for (int r = 0; r < 4; ++r) acc[mt][r] = lo[mt][r] = 0.f;
 #pragma unroll
-        for (int kt = 0; kt < 2; ++kt) {
-            // small terms first, the hi x hi product last
-            T::mma(acc[mt], ahi[mt][kt], bl[2 * kt], bl[2 * kt + 1]);
-            T::mma(acc[mt], alo[mt][kt], bh[2 * kt], bh[2 * kt + 1]);
+    for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            T::mma(lo[mt], ahi[mt][kt], bl[2 * kt], bl[2 * kt + 1]);
             T::mma(acc[mt], ahi[mt][kt], bh[2 * kt], bh[2 * kt + 1]);
+            T::mma(lo[mt], alo[mt][kt], bh[2 * kt], bh[2 * kt + 1]);
         }
-    }
-}
-
-// Loads of one butterfly column: point m = t + 4h of butterfly jj (k = jj mod
-// Ns) is val(m) times w^m, w = exp(SIGN 2 pi i k / (16 Ns)), split hi/lo.
-template <class T, int SIGN, typename Val>
-__device__ __forceinline__ void tc_column(const float2 *__restrict__ tw, int Ns, int k, int t,
-                                          uint32_t (&bh)[4], uint32_t (&bl)[4], Val &val) {
-    const int tws = kTwN / (16 * Ns);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int m = t + 4 * h;
-        float2 w = __ldg(&tw[(k * m) * tws]);  // k m < 16 Ns: inside the table
-        if (SIGN < 0) w.y = -w.y;
-        tc_split<T>(cmul(val(m), w), bh[h], bl[h]);
-    }
-}
-
-// Stores of a pass's outputs: output q of butterfly jj (k = jj mod Ns) goes
-// to (jj - k) 16 + k + q Ns; this lane holds q = g, g+8 of columns 2t, 2t+1,
-// whose butterflies are jj_of(2t), jj_of(2t+1).
-template <typename JJ>
-__device__ __forceinline__ void tc_store(float2 *__restrict__ sm, int Ns, int g, int t,
-                                         const float (&acc)[2][4], JJ &jj_of) {
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int jj = jj_of(2 * t + e);
-        const int k = jj & (Ns - 1);
-        const int base = (jj - k) * 16 + k;
-        sm[tc_pad(base + g * Ns)] = make_float2(acc[0][e], acc[1][e]);
-        sm[tc_pad(base + (g + 8) * Ns)] = make_float2(acc[0][2 + e], acc[1][2 + e]);
-    }
+        for (int r = 0; r < 4; ++r) acc[mt][r] += lo[mt][r];
 }
 
-// x * exp(SIGN 2 pi i n / 4): the radix-4 roots are +-1 and +-i.
-template <int SIGN>
+// x * exp(2 pi i n / 4) for any integer n, without branches (the radix-4
+// roots are +-1 and +-i).
 __device__ __forceinline__ float2 rot4(float2 x, int n) {
-    n = (SIGN > 0 ? n : -n) & 3;
-    if (n == 0) return x;
-    if (n == 1) return make_float2(-x.y, x.x);
-    if (n == 2) return make_float2(-x.x, -x.y);
-    return make_float2(x.y, -x.x);
+    const float2 y = (n & 1) ? make_float2(-x.y, x.x) : x;
+    return (n & 2) ? make_float2(-y.x, -y.y) : y;
 }
+
+// Twiddles of the three passes in shared memory, after the row (float2):
+//   [0, 64)       pass A: w^m = exp(SIGN 2 pi i k m / 64),    entry 16 k + m (k < 4)
+//   [64, 1088)    pass B: w^m = exp(SIGN 2 pi i k m / 1024),  entry 16 k + m (k < 64)
+//   [1088, 1216)  exp(SIGN 2 pi i 128 a / 16384), a < 128
+//   [1216, 1344)  exp(SIGN 2 pi i b / 16384), b < 128
+// so pass C's exp(SIGN 2 pi i x / 16384) is the product of entries x >> 7 and
+// x & 127 of the last two.  All come from the FP64-generated FP32 table tw.
+constexpr int kTcTabA = 0, kTcTabB = 64, kTcTab1 = 1088, kTcTab2 = 1216, kTcTabF2 = 1344;
+
+template <int SIGN>
+__device__ __forceinline__ void tc_fill_twiddles(float2 *__restrict__ tab, const float2 *__restrict__ tw) {
+    for (int i = threadIdx.x; i < kTcTabF2; i += kTcThreads) {
+        int idx;
+        if (i < kTcTabB) idx = (((i >> 4) * (i & 15)) & 63) * (kTwN / 64);
+        else if (i < kTcTab1) idx = ((((i - kTcTabB) >> 4) * ((i - kTcTabB) & 15)) & 1023) * (kTwN / 1024);
+        else if (i < kTcTab2) idx = (i - kTcTab1) * 128 * (kTwN / kTcNL);
+        else idx = (i - kTcTab2) * (kTwN / kTcNL);
+        float2 w = __ldg(&tw[idx]);
+        if (SIGN < 0) w.y = -w.y;
+        tab[i] = w;
+    }
+}
+
+// tc_pad's XOR term for bits 10-12 of an index: the nibble table.
+__device__ __forceinline__ int tc_lut(int b) { return (int)((0x9C14D850u >> (b * 4)) & 15u); }
 
 // The whole 16384-point FFT of the CTA's row (all 512 threads call it):
 // X[t] = sum_m x[m] exp(SIGN 2 pi i m t / 16384).  Pass 0 (radix 4) reads its
 // inputs through the caller: dense, load(m) for any m < 16384; sparse (every
 // radix-4 butterfly {j + 4096 r} holds at most one nonzero input),
 // first(j, r, x) returns whether butterfly j has one, with its position r and
-// value x.  On return sm holds X[t] at tc_pad(t), natural order.
+// value x.  `tab` holds the twiddle tables (tc_fill_twiddles, before the
+// call, with a barrier).  On return sm holds X[t] at tc_pad(t), natural order.
+// The shared-memory indices of passes B and C are tc_pad's, with the XOR
+// terms that stay fixed for a lane (bits 6-7 and 10-12 of each access
+// pattern) computed once.
 template <class T, int SIGN, typename Load, typename First>
-__device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float2 *__restrict__ tw,
+__device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float2 *__restrict__ tab,
                                             bool sparse, Load &load, First &first) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     uint32_t ahi[2][2][4], alo[2][2][4];
     tc_dft16_afrag<T, SIGN>(ahi, alo, lane);
     constexpr int Q0 = kTcNL / 4;
+    const int sgn = SIGN > 0 ? 1 : -1;
 
     // ---- pass A: pass 0 on the fly + radix 16 with Ns = 4 ----
     // input point m of butterfly jj is pass-0 output p = jj + 1024 m, i.e.
@@ -229,63 +233,103 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
             int r = 0;
             float2 x;
             if (!first(j, r, x)) return make_float2(0.f, 0.f);
-            return rot4<SIGN>(x, r * m0);
+            return rot4(x, sgn * r * m0);
         }
         float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) s = cadd(s, rot4<SIGN>(load(j + Q0 * r), r * m0));
+        for (int r = 0; r < 4; ++r) s = cadd(s, rot4(load(j + Q0 * r), sgn * r * m0));
         return s;
     };
 #pragma unroll 1
     for (int i = 0; i < 8; ++i) {
         const int jj0 = (warp + 16 * i) * 8;
-        const int jj = jj0 + g;
-        auto val = [&](int m) -> float2 { return pass0_out(jj + kTcNB * m); };
+        const int jj = jj0 + g, k = jj & 3;
         uint32_t bh[4], bl[4];
-        tc_column<T, SIGN>(tw, 4, jj & 3, t, bh, bl, val);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int m = t + 4 * h;
+            tc_split<T>(cmul(pass0_out(jj + kTcNB * m), tab[kTcTabA + 16 * k + m]), bh[h], bl[h]);
+        }
         float acc[2][4];
         tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
-        auto jj_of = [&](int n) { return jj0 + n; };
-        tc_store(sm, 4, g, t, acc, jj_of);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int jn = jj0 + 2 * t + e, kn = jn & 3;
+            const int base = (jn - kn) * 16 + kn;
+            sm[tc_pad(base + 4 * g)] = make_float2(acc[0][e], acc[1][e]);
+            sm[tc_pad(base + 4 * (g + 8))] = make_float2(acc[0][2 + e], acc[1][2 + e]);
+        }
     }
     __syncthreads();
 
     // ---- pass B: radix 16, Ns = 64; warp w owns residue classes 4w .. 4w+3 ----
+    // loads k + 64 (8 rho + g) + 1024 m: bits 6-7 = g & 3, bits 10-12 = m & 7;
+    // stores 1024 (8 rho + 2t + e) + k + 64 q: bits 6-7 = g & 3, bits 10-12 = 2t + e
+    {
+        int xl[4], xs[2];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) xl[h] = (g & 3) ^ tc_lut((t + 4 * h) & 7);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) xs[e] = (g & 3) ^ tc_lut(2 * t + e);
 #pragma unroll 1
-    for (int kk = 0; kk < 4; ++kk) {
-        const int k = 4 * warp + kk;
-        float acc[2][2][4];
+        for (int kk = 0; kk < 4; ++kk) {
+            const int k = 4 * warp + kk;
+            float acc[2][2][4];
 #pragma unroll
-        for (int rho = 0; rho < 2; ++rho) {
-            const int jj = k + 64 * (8 * rho + g);
-            auto val = [&](int m) -> float2 { return sm[tc_pad(jj + kTcNB * m)]; };
-            uint32_t bh[4], bl[4];
-            tc_column<T, SIGN>(tw, 64, k, t, bh, bl, val);
-            tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);
-        }
-        __syncwarp();  // the class's 32 inputs are read before any of its outputs lands
+            for (int rho = 0; rho < 2; ++rho) {
+                const int jj = k + 64 * (8 * rho + g);
+                uint32_t bh[4], bl[4];
 #pragma unroll
-        for (int rho = 0; rho < 2; ++rho) {
-            auto jj_of = [&](int n) { return k + 64 * (8 * rho + n); };
-            tc_store(sm, 64, g, t, acc[rho], jj_of);
+                for (int h = 0; h < 4; ++h) {
+                    const int m = t + 4 * h;
+                    tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ xl[h]], tab[kTcTabB + 16 * k + m]), bh[h], bl[h]);
+                }
+                tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);
+            }
+            __syncwarp();  // the class's 32 inputs are read before any of its outputs lands
+#pragma unroll
+            for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int base = 1024 * (8 * rho + 2 * t + e) + k;
+                    sm[(base + 64 * g) ^ xs[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
+                    sm[(base + 64 * (g + 8)) ^ xs[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
+                }
         }
     }
     __syncthreads();
 
     // ---- pass C: radix 16, Ns = 1024; in place per butterfly ----
+    // loads jj0 + g + 1024 m and stores jj0 + 2t + e + 1024 q: bits 6-7 from
+    // jj0 (one value per round), bits 10-12 = m & 7 and q & 7 = g
+    {
+        int xl[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) xl[h] = tc_lut((t + 4 * h) & 7);
+        const int xs = tc_lut(g);
 #pragma unroll 1
-    for (int i = 0; i < 8; ++i) {
-        const int jj0 = (warp + 16 * i) * 8;
-        const int jj = jj0 + g;
-        auto val = [&](int m) -> float2 { return sm[tc_pad(jj + kTcNB * m)]; };
-        uint32_t bh[4], bl[4];
-        tc_column<T, SIGN>(tw, 1024, jj, t, bh, bl, val);
-        float acc[2][4];
-        tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
-        __syncwarp();  // the eight butterflies' inputs are read before their outputs land
-        auto jj_of = [&](int n) { return jj0 + n; };
-        tc_store(sm, 1024, g, t, acc, jj_of);
-        __syncwarp();
+        for (int i = 0; i < 8; ++i) {
+            const int jj0 = (warp + 16 * i) * 8;
+            const int jj = jj0 + g, b6 = (jj0 >> 6) & 3;
+            uint32_t bh[4], bl[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int m = t + 4 * h;
+                const int x = (jj * m) & (kTcNL - 1);
+                const float2 w = cmul(tab[kTcTab1 + (x >> 7)], tab[kTcTab2 + (x & 127)]);
+                tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ b6 ^ xl[h]], w), bh[h], bl[h]);
+            }
+            float acc[2][4];
+            tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
+            __syncwarp();  // the eight butterflies' inputs are read before their outputs land
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int base = jj0 + 2 * t + e;
+                sm[(base + 1024 * g) ^ b6 ^ xs] = make_float2(acc[0][e], acc[1][e]);
+                sm[(base + 1024 * (g + 8)) ^ b6 ^ xs] = make_float2(acc[0][2 + e], acc[1][2 + e]);
+            }
+            __syncwarp();
+        }
     }
     __syncthreads();
 }

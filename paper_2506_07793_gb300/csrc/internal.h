@@ -23,6 +23,19 @@ constexpr int kMaxClusterFftLog2 = 17;  // up to 131072 on a cluster of 8 CTAs
 constexpr int kMaxClusterFft = 1 << kMaxClusterFftLog2;
 constexpr double kBandRelThreshold = 1e-10;  // bins below this fraction of a scale's peak are skipped
 
+// Device (cudaMalloc) and pinned host (cudaMallocHost) allocations of the
+// library, with host-side failure injection (alloc.cu).
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t host_alloc(void **p, size_t bytes);
+template <class T>
+cudaError_t dmalloc(T **p, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+template <class T>
+cudaError_t hmalloc(T **p, size_t bytes) {
+    return host_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // Per-device FP32 twiddle table exp(2 pi i m / 2^17), built in FP64 on first use.
 cudaError_t device_twiddles(const float2 **out);
 

@@ -238,8 +238,8 @@ cudaError_t bank_for(cwt_server_s *srv, double fs, int *idx) {
     }
     Bank b;
     b.fs = fs;
-    cudaError_t e = cudaMalloc(&b.bank, sizeof(float) * (size_t)srv->S * kSW);
-    if (e == cudaSuccess) e = cudaMalloc(&b.band, sizeof(int) * 2 * (size_t)srv->S);
+    cudaError_t e = cwtk::dmalloc(&b.bank, sizeof(float) * (size_t)srv->S * kSW);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&b.band, sizeof(int) * 2 * (size_t)srv->S);
     if (e == cudaSuccess) {
         // reuse the plan generator through a temporary plan description, on a
         // private stream so that in-flight batches are not waited for
@@ -283,8 +283,8 @@ cudaError_t grow_slots(cwt_server_s *srv, size_t items, size_t outf) {
             sl.d_items = nullptr;
             sl.h_items = nullptr;
             sl.items_cap = 0;
-            cudaError_t e = cudaMalloc(&sl.d_items, sizeof(StreamItem) * items);
-            if (e == cudaSuccess) e = cudaMallocHost(&sl.h_items, sizeof(StreamItem) * items);
+            cudaError_t e = cwtk::dmalloc(&sl.d_items, sizeof(StreamItem) * items);
+            if (e == cudaSuccess) e = cwtk::hmalloc(&sl.h_items, sizeof(StreamItem) * items);
             if (e != cudaSuccess) return e;
             sl.items_cap = items;
         }
@@ -292,7 +292,7 @@ cudaError_t grow_slots(cwt_server_s *srv, size_t items, size_t outf) {
             cudaFree(sl.d_out);
             sl.d_out = nullptr;
             sl.out_cap = 0;
-            cudaError_t e = cudaMalloc(&sl.d_out, sizeof(float) * outf);
+            cudaError_t e = cwtk::dmalloc(&sl.d_out, sizeof(float) * outf);
             if (e != cudaSuccess) return e;
             sl.out_cap = outf;
         }
@@ -460,9 +460,9 @@ cwt_status cwt_stream_open(cwt_server s, int channels, double fs, int *stream_id
     const size_t ring_b = sizeof(float) * (size_t)channels * st.cap;
     const size_t q_b = sizeof(float) * (size_t)channels * s->S * H * st.queue_slots;
     // zeroed on the copy stream, so that the stream's pushes land after it
-    if (e == cudaSuccess) e = cudaMalloc(&st.d_ring, ring_b);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&st.d_ring, ring_b);
     if (e == cudaSuccess) e = cudaMemsetAsync(st.d_ring, 0, ring_b, s->cst);
-    if (e == cudaSuccess) e = cudaMallocHost(&st.h_queue, q_b);
+    if (e == cudaSuccess) e = cwtk::hmalloc(&st.h_queue, q_b);
     const size_t items = s->bound_items + (size_t)channels * kMaxPending;
     const size_t outf = s->bound_out + (size_t)channels * s->S * H * kMaxPending;
     if (e == cudaSuccess) e = grow_slots(s, items, outf);

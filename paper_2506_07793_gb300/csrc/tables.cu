@@ -190,7 +190,7 @@ cudaError_t device_twiddles(const float2 **out) {
     std::lock_guard<std::mutex> lk(g_tw_mutex);
     if (!g_tw[dev]) {
         float2 *tw = nullptr;
-        e = cudaMalloc(&tw, sizeof(float2) * kTwN);
+        e = cwtk::dmalloc(&tw, sizeof(float2) * kTwN);
         if (e != cudaSuccess) return e;
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -221,10 +221,10 @@ cudaError_t launch_bank_n(const cwt_plan_s *p, int N, float *bank, int *band, cu
     const int S = p->S;
     const int nblk = (N + kBankThreads - 1) / kBankThreads;
     double *raw = nullptr, *partial = nullptr, *dF = nullptr, *dsig = nullptr;
-    cudaError_t e = cudaMalloc(&raw, sizeof(double) * (size_t)S * N);
-    if (e == cudaSuccess) e = cudaMalloc(&partial, sizeof(double) * (size_t)S * nblk);
-    if (e == cudaSuccess) e = cudaMalloc(&dF, sizeof(double) * S);
-    if (e == cudaSuccess) e = cudaMalloc(&dsig, sizeof(double) * S);
+    cudaError_t e = cwtk::dmalloc(&raw, sizeof(double) * (size_t)S * N);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&partial, sizeof(double) * (size_t)S * nblk);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&dF, sizeof(double) * S);
+    if (e == cudaSuccess) e = cwtk::dmalloc(&dsig, sizeof(double) * S);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dF, p->freqs.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)

@@ -89,7 +89,10 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
         x = make_float2(xv.x * w, xv.y * w);
         return true;
     };
-    tc_fft16384<T, +1>(sm, a.tw, Bm <= Q, load, first);
+    float2 *tab = sm + kTcNL;
+    tc_fill_twiddles<+1>(tab, a.tw);
+    __syncthreads();
+    tc_fft16384<T, +1>(sm, tab, Bm <= Q, load, first);
 
     const size_t obase = (size_t)row * (size_t)a.n_out;
     V2 *oc = (V2 *)a.out_c;
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scale_block_kernel(const TcA
     tc_row<1, T, IO>(a, tcsm, blockIdx.x, 0);
 }
 
-constexpr int kTcSmemBytes = kTcNL * (int)sizeof(float2);  // 128 KB
+constexpr int kTcSmemBytes = (kTcNL + kTcTabF2) * (int)sizeof(float2);  // the row + twiddles, 138.5 KB
 
 // chmax[c] = max_k max(|Re X_c[k]|, |Im X_c[k]|): one CTA per channel.
 __global__ void __launch_bounds__(512) tc_chmax_kernel(const float2 *__restrict__ spec, int N,

@@ -262,3 +262,36 @@ def test_swizzle_is_a_permutation_and_conflict_free():
                         assert ok((jj - k) * 16 + k + 64 * (g + qh))         # pass B stores
     for base in range(0, NL, 32):
         assert ok(base + lanes)                                              # natural order
+
+
+def test_hoisted_swizzle_terms_equal_tc_pad():
+    """Passes B and C XOR fixed per-lane terms instead of evaluating tc_pad on
+    every access; those terms equal tc_pad's on every index they touch."""
+    lut = lambda b: (0x9C14D850 >> (b * 4)) & 15  # noqa: E731
+    lanes = np.arange(32)
+    g, t = lanes >> 2, lanes & 3
+    for w in range(16):
+        for kk in range(4):                                   # pass B
+            k = 4 * w + kk
+            for rho in range(2):
+                for h in range(4):
+                    i = k + 64 * (8 * rho + g) + NB * (t + 4 * h)
+                    assert np.array_equal(i ^ ((g & 3) ^ lut_v(lut, (t + 4 * h) & 7)), tc_pad(i))
+                for e in range(2):
+                    for qh in (0, 8):
+                        i = 1024 * (8 * rho + 2 * t + e) + k + 64 * (g + qh)
+                        assert np.array_equal(i ^ ((g & 3) ^ lut_v(lut, 2 * t + e)), tc_pad(i))
+        for i_ in range(8):                                   # pass C
+            jj0 = (w + 16 * i_) * 8
+            b6 = (jj0 >> 6) & 3
+            for h in range(4):
+                i = jj0 + g + NB * (t + 4 * h)
+                assert np.array_equal(i ^ b6 ^ lut_v(lut, (t + 4 * h) & 7), tc_pad(i))
+            for e in range(2):
+                for qh in (0, 8):
+                    i = jj0 + 2 * t + e + 1024 * (g + qh)
+                    assert np.array_equal(i ^ b6 ^ lut_v(lut, g), tc_pad(i))
+
+
+def lut_v(lut, b):
+    return np.vectorize(lut)(np.asarray(b))
