@@ -154,10 +154,20 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         while (N < ep.samples + p->pad_extra) N <<= 1;
         const int L = ilog2c(N);
         if (!b->bank[L]) {
-            e = cwtk::dmalloc(&b->bank[L], sizeof(float) * (size_t)S * N);
-            if (e == cudaSuccess) e = cwtk::dmalloc(&b->band[L], sizeof(int) * 2 * (size_t)S);
-            if (e == cudaSuccess) e = launch_bank_n(p, N, b->bank[L], b->band[L], st, nullptr);
-            if (e != cudaSuccess) return e;
+            // a length's bank is published only once it is generated, so a
+            // failure here leaves nothing half-built for the next call
+            float *bank = nullptr;
+            int *band = nullptr;
+            e = cwtk::dmalloc(&bank, sizeof(float) * (size_t)S * N);
+            if (e == cudaSuccess) e = cwtk::dmalloc(&band, sizeof(int) * 2 * (size_t)S);
+            if (e == cudaSuccess) e = launch_bank_n(p, N, bank, band, st, nullptr);
+            if (e != cudaSuccess) {
+                cudaFree(bank);
+                cudaFree(band);
+                return e;
+            }
+            b->bank[L] = bank;
+            b->band[L] = band;
             b->bytes += sizeof(float) * (size_t)S * N + sizeof(int) * 2 * (size_t)S;
         }
         const int G = std::max(1, std::min(C, kTile / N));
@@ -186,16 +196,18 @@ cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, 
         items.size() != b->h_items_natural.size() ||
         std::memcmp(items.data(), b->h_items_natural.data(), items.size() * sizeof(BatchItem)) != 0;
     if (shape_changed) {
+        if (items.size() > b->items_cap) {
+            BatchItem *d = nullptr;
+            e = cwtk::dmalloc(&d, sizeof(BatchItem) * items.size());
+            if (e != cudaSuccess) return e;  // the previous shape stays intact
+            cudaFree(b->d_items);
+            b->d_items = d;
+            b->items_cap = items.size();
+            b->uploaded.clear();
+        }
         b->h_items_natural = items;
         b->h_items_sorted = sorted;
         b->tuned = false;
-        if (items.size() > b->items_cap) {
-            cudaFree(b->d_items);
-            b->d_items = nullptr;
-            e = cwtk::dmalloc(&b->d_items, sizeof(BatchItem) * items.size());
-            if (e != cudaSuccess) return e;
-            b->items_cap = items.size();
-        }
     }
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));  // padding too: the graph compares argument bytes

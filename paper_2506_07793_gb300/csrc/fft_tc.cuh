@@ -120,25 +120,23 @@ __device__ __forceinline__ void tc_split(float2 v, uint32_t &hi, uint32_t &lo) {
 
 // This lane's A fragments of the real 32 x 32 form of F16, split hi/lo:
 // a[mt][kt][r] for m-tile mt (0: Re y rows, 1: Im y rows), k-tile kt.
-template <class T, int SIGN>
+// root16[e] = exp(SIGN 2 pi i e / 16), e < 16 (entries 8e of the twiddle
+// table tc_fill_twiddles builds).
+template <class T>
 __device__ __forceinline__ void tc_dft16_afrag(uint32_t (&ahi)[2][2][4], uint32_t (&alo)[2][2][4],
-                                               int lane) {
+                                               int lane, const float2 *__restrict__ root16, int stride) {
     const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+    for (int kt = 0; kt < 2; ++kt)
 #pragma unroll
-        for (int kt = 0; kt < 2; ++kt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int q = g + 8 * (r & 1);
-                const int m = 8 * kt + t + 4 * (r >> 1);
-                const int e = (q * m) & 15;          // F16[q][m] = exp(SIGN 2 pi i e / 16)
-                const float c = cos32(2 * e);
-                const float s = SIGN > 0 ? sin32(2 * e) : -sin32(2 * e);
-                const float a0 = mt == 0 ? c : s;    // coefficient of Re x_m
-                const float a1 = mt == 0 ? -s : c;   // coefficient of Im x_m
-                tc_split<T>(make_float2(a0, a1), ahi[mt][kt][r], alo[mt][kt][r]);
-            }
+        for (int r = 0; r < 4; ++r) {
+            const int q = g + 8 * (r & 1);
+            const int m = 8 * kt + t + 4 * (r >> 1);
+            const float2 w = root16[((q * m) & 15) * stride];  // F16[q][m] = c + i s
+            // m-tile 0 (Re y_q): (c, -s) on (Re x_m, Im x_m); m-tile 1 (Im y_q): (s, c)
+            tc_split<T>(make_float2(w.x, -w.y), ahi[0][kt][r], alo[0][kt][r]);
+            tc_split<T>(make_float2(w.y, w.x), ahi[1][kt][r], alo[1][kt][r]);
+        }
 }
 
 // The 16-point DFTs of eight butterflies (the MMA's columns) on the tensor
@@ -209,8 +207,8 @@ __device__ __forceinline__ int tc_lut(int b) { return (int)((0x9C14D850u >> (b *
 // X[t] = sum_m x[m] exp(SIGN 2 pi i m t / 16384).  Pass 0 (radix 4) reads its
 // inputs through the caller: dense, load(m) for any m < 16384; sparse (every
 // radix-4 butterfly {j + 4096 r} holds at most one nonzero input),
-// first(j, r, x) returns whether butterfly j has one, with its position r and
-// value x.  `tab` holds the twiddle tables (tc_fill_twiddles, before the
+// first(j, r, x) gives butterfly j's nonzero input x and its position r, or
+// x = 0 when it has none.  `tab` holds the twiddle tables (tc_fill_twiddles, before the
 // call, with a barrier).  On return sm holds X[t] at tc_pad(t), natural order.
 // The shared-memory indices of passes B and C are tc_pad's, with the XOR
 // terms that stay fixed for a lane (bits 6-7 and 10-12 of each access
@@ -220,7 +218,7 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
                                             bool sparse, Load &load, First &first) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     uint32_t ahi[2][2][4], alo[2][2][4];
-    tc_dft16_afrag<T, SIGN>(ahi, alo, lane);
+    tc_dft16_afrag<T>(ahi, alo, lane, tab + kTcTab1, 8);  // exp(SIGN 2 pi i 8e / 128)
     constexpr int Q0 = kTcNL / 4;
     const int sgn = SIGN > 0 ? 1 : -1;
 
@@ -229,10 +227,10 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
     // output p & 3 of radix-4 butterfly p >> 2
     auto pass0_out = [&](int p) -> float2 {
         const int j = p >> 2, m0 = p & 3;
-        if (sparse) {
+        if (sparse) {  // first() sets x = 0 when the butterfly has no nonzero input
             int r = 0;
             float2 x;
-            if (!first(j, r, x)) return make_float2(0.f, 0.f);
+            first(j, r, x);
             return rot4(x, sgn * r * m0);
         }
         float2 s = make_float2(0.f, 0.f);

@@ -268,32 +268,37 @@ cudaError_t bank_for(cwt_server_s *srv, double fs, int *idx) {
 }
 
 // Grow both slots' batch buffers to hold `items` work items and `outf`
-// output floats (waiting for a slot's batch in flight before replacing its
-// buffers).  Called at admission, never by cwt_server_step.
+// output floats.  The new buffers are allocated first, so a failure leaves
+// every slot as it was; a slot's batch in flight is waited for before its
+// buffers are replaced.  Called at admission, never by cwt_server_step.
 cudaError_t grow_slots(cwt_server_s *srv, size_t items, size_t outf) {
     for (Slot &sl : srv->slots) {
         if (sl.items_cap >= items && sl.out_cap >= outf) continue;
-        if (sl.busy) {
-            cudaError_t e = cudaEventSynchronize(sl.done);
-            if (e != cudaSuccess) return e;
-        }
+        StreamItem *d_items = nullptr, *h_items = nullptr;
+        float *d_out = nullptr;
+        cudaError_t e = cudaSuccess;
         if (sl.items_cap < items) {
+            e = cwtk::dmalloc(&d_items, sizeof(StreamItem) * items);
+            if (e == cudaSuccess) e = cwtk::hmalloc(&h_items, sizeof(StreamItem) * items);
+        }
+        if (e == cudaSuccess && sl.out_cap < outf) e = cwtk::dmalloc(&d_out, sizeof(float) * outf);
+        if (e == cudaSuccess && sl.busy) e = cudaEventSynchronize(sl.done);
+        if (e != cudaSuccess) {
+            cudaFree(d_items);
+            if (h_items) cudaFreeHost(h_items);
+            cudaFree(d_out);
+            return e;
+        }
+        if (d_items) {
             cudaFree(sl.d_items);
             if (sl.h_items) cudaFreeHost(sl.h_items);
-            sl.d_items = nullptr;
-            sl.h_items = nullptr;
-            sl.items_cap = 0;
-            cudaError_t e = cwtk::dmalloc(&sl.d_items, sizeof(StreamItem) * items);
-            if (e == cudaSuccess) e = cwtk::hmalloc(&sl.h_items, sizeof(StreamItem) * items);
-            if (e != cudaSuccess) return e;
+            sl.d_items = d_items;
+            sl.h_items = h_items;
             sl.items_cap = items;
         }
-        if (sl.out_cap < outf) {
+        if (d_out) {
             cudaFree(sl.d_out);
-            sl.d_out = nullptr;
-            sl.out_cap = 0;
-            cudaError_t e = cwtk::dmalloc(&sl.d_out, sizeof(float) * outf);
-            if (e != cudaSuccess) return e;
+            sl.d_out = d_out;
             sl.out_cap = outf;
         }
     }

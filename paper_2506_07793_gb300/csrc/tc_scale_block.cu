@@ -78,16 +78,17 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
     const int delta = (rank - b0) & (CL - 1);
     const int Bm = delta < B ? (B - delta + CL - 1) / CL : 0;
     const int m_first = ((((b0 + delta) & (N - 1)) - rank) / CL) & (kTcNL - 1);
-    auto first = [&](int j, int &r, float2 &x) -> bool {
+    // Branch-free: a butterfly with no in-band input reads bin `rank` (in
+    // bounds, the same address for every such lane) and returns x = 0.
+    auto first = [&](int j, int &r, float2 &x) {
         const int d0 = (j - m_first) & (Q - 1);
-        if (d0 >= Bm) return false;
+        const bool in = d0 < Bm;
         const int m = (m_first + d0) & (kTcNL - 1);
-        r = (m - j) / Q;
-        const int k = rank + CL * m;
+        r = (m - j) >> 12;  // m = j + r Q when in band (Q = 4096)
+        const int k = in ? rank + CL * m : rank;
         const float2 xv = X[k];
-        const float w = W[k] * sc;
+        const float w = in ? W[k] * sc : 0.f;
         x = make_float2(xv.x * w, xv.y * w);
-        return true;
     };
     float2 *tab = sm + kTcNL;
     tc_fill_twiddles<+1>(tab, a.tw);
