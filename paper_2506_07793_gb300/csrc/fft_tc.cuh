@@ -41,17 +41,20 @@
 //           whole residue classes k (two MMAs of 8 butterflies each) only
 //           has to wait for its own lanes (__syncwarp) between reading and
 //           writing;
-//   pass C  radix 16, Ns = 1024: each butterfly reads and writes the same 16
-//           positions, so again one __syncwarp per 8 butterflies.
+//   pass C  radix 16, Ns = 1024: butterfly jj reads and writes the positions
+//           jj + 1024 m, so the butterflies k + 64 q (q < 16) of pass C touch
+//           exactly the class k of pass B: the warp that owns class k runs
+//           its pass C right after its pass B, with __syncwarp only (no
+//           barrier of the whole CTA between the two passes).
 // So no pass holds more than two MMAs' outputs in registers and the row
 // stays in place in one 128 KB buffer.
 //
 // Shared-memory layout (tc_pad): element i of the row sits at i with its
-// bits 0-3 XORed by a GF(2)-linear function of bits 6, 7, 10, 11 and 12.  It is
-// chosen so that every access of the three passes (lanes at strides 1 and
-// 1024, 2 and 1024, 64 and 1024, and the Ns = 4 output pattern) and the
-// natural-order reads that follow touch 16 distinct 8-byte bank pairs per
-// half-warp: no bank conflicts.
+// bits 0-3 XORed by a GF(2)-linear function of bits 6, 7, 8, 10, 11 and 12.
+// It is chosen so that every access of the passes (lanes at strides 64 and
+// 1024, 128 and 1024, and the Ns = 4 output pattern) and the natural-order
+// reads that follow touch 16 distinct 8-byte bank pairs per half-warp: no
+// bank conflicts.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -66,11 +69,12 @@ constexpr int kTcNL = 16384;      // points per CTA row
 constexpr int kTcThreads = 512;   // 16 warps
 constexpr int kTcNB = kTcNL / 16; // butterflies per radix-16 pass
 
-__device__ __forceinline__ int tc_pad(int i) {
-    // bits 10, 11, 12 -> XOR masks 5, 8, 4 (a nibble table); bits 6, 7 -> 1, 2
-    const int hi = (int)((0x9C14D850u >> (((i >> 10) & 7) * 4)) & 15u);
-    return i ^ ((i >> 6) & 3) ^ hi;
-}
+// XOR terms of tc_pad: bits 6, 7, 8 of the index -> masks 1, 2, 1 and bits
+// 10, 11, 12 -> masks 5, 8, 4, each group as a table of eight nibbles.
+__device__ __forceinline__ int tc_lut_lo(int b) { return (int)((0x23013210u >> (b * 4)) & 15u); }
+__device__ __forceinline__ int tc_lut(int b) { return (int)((0x9C14D850u >> (b * 4)) & 15u); }
+
+__device__ __forceinline__ int tc_pad(int i) { return i ^ tc_lut_lo((i >> 6) & 7) ^ tc_lut((i >> 10) & 7); }
 
 // The two 16-bit operand types of mma.sync kind f16 (A and B of one MMA
 // always share the type).
@@ -200,9 +204,6 @@ __device__ __forceinline__ void tc_fill_twiddles(float2 *__restrict__ tab, const
     }
 }
 
-// tc_pad's XOR term for bits 10-12 of an index: the nibble table.
-__device__ __forceinline__ int tc_lut(int b) { return (int)((0x9C14D850u >> (b * 4)) & 15u); }
-
 // The whole 16384-point FFT of the CTA's row (all 512 threads call it):
 // X[t] = sum_m x[m] exp(SIGN 2 pi i m t / 16384).  Pass 0 (radix 4) reads its
 // inputs through the caller: dense, load(m) for any m < 16384; sparse (every
@@ -260,19 +261,27 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
     }
     __syncthreads();
 
-    // ---- pass B: radix 16, Ns = 64; warp w owns residue classes 4w .. 4w+3 ----
-    // loads k + 64 (8 rho + g) + 1024 m: bits 6-7 = g & 3, bits 10-12 = m & 7;
-    // stores 1024 (8 rho + 2t + e) + k + 64 q: bits 6-7 = g & 3, bits 10-12 = 2t + e
+    // ---- passes B (radix 16, Ns = 64) and C (radix 16, Ns = 1024) ----
+    // Warp w owns the residue classes k = 4w .. 4w+3 (mod 64) of both.
+    //   pass B: butterflies k + 64 (8 rho + n), loads k + 64 (8 rho + g) + 1024 m
+    //           (bits 6-8 = g, 10-12 = m & 7), stores 1024 (8 rho + 2t + e) + k + 64 q
+    //           (bits 6-8 = g, 10-12 = 2t + e);
+    //   pass C: butterflies k + 64 (8 rho + n), the same loads, stores
+    //           k + 64 (8 rho + 2t + e) + 1024 q (bits 6-8 = 2t + e, 10-12 = g).
     {
-        int xl[4], xs[2];
+        int xl[4], xsb[2], xsc[2];
 #pragma unroll
-        for (int h = 0; h < 4; ++h) xl[h] = (g & 3) ^ tc_lut((t + 4 * h) & 7);
+        for (int h = 0; h < 4; ++h) xl[h] = tc_lut_lo(g) ^ tc_lut((t + 4 * h) & 7);
 #pragma unroll
-        for (int e = 0; e < 2; ++e) xs[e] = (g & 3) ^ tc_lut(2 * t + e);
+        for (int e = 0; e < 2; ++e) {
+            xsb[e] = tc_lut_lo(g) ^ tc_lut(2 * t + e);
+            xsc[e] = tc_lut_lo(2 * t + e) ^ tc_lut(g);
+        }
 #pragma unroll 1
         for (int kk = 0; kk < 4; ++kk) {
             const int k = 4 * warp + kk;
             float acc[2][2][4];
+            // pass B
 #pragma unroll
             for (int rho = 0; rho < 2; ++rho) {
                 const int jj = k + 64 * (8 * rho + g);
@@ -290,43 +299,33 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int base = 1024 * (8 * rho + 2 * t + e) + k;
-                    sm[(base + 64 * g) ^ xs[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
-                    sm[(base + 64 * (g + 8)) ^ xs[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
+                    sm[(base + 64 * g) ^ xsb[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
+                    sm[(base + 64 * (g + 8)) ^ xsb[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
                 }
-        }
-    }
-    __syncthreads();
-
-    // ---- pass C: radix 16, Ns = 1024; in place per butterfly ----
-    // loads jj0 + g + 1024 m and stores jj0 + 2t + e + 1024 q: bits 6-7 from
-    // jj0 (one value per round), bits 10-12 = m & 7 and q & 7 = g
-    {
-        int xl[4];
+            __syncwarp();  // pass B's outputs of the class are visible to the warp
+            // pass C: twiddle exp(SIGN 2 pi i jj m / 16384) = table entries x >> 7 and x & 127
 #pragma unroll
-        for (int h = 0; h < 4; ++h) xl[h] = tc_lut((t + 4 * h) & 7);
-        const int xs = tc_lut(g);
-#pragma unroll 1
-        for (int i = 0; i < 8; ++i) {
-            const int jj0 = (warp + 16 * i) * 8;
-            const int jj = jj0 + g, b6 = (jj0 >> 6) & 3;
-            uint32_t bh[4], bl[4];
+            for (int rho = 0; rho < 2; ++rho) {
+                const int jj = k + 64 * (8 * rho + g);
+                uint32_t bh[4], bl[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int m = t + 4 * h;
-                const int x = (jj * m) & (kTcNL - 1);
-                const float2 w = cmul(tab[kTcTab1 + (x >> 7)], tab[kTcTab2 + (x & 127)]);
-                tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ b6 ^ xl[h]], w), bh[h], bl[h]);
-            }
-            float acc[2][4];
-            tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
-            __syncwarp();  // the eight butterflies' inputs are read before their outputs land
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int base = jj0 + 2 * t + e;
-                sm[(base + 1024 * g) ^ b6 ^ xs] = make_float2(acc[0][e], acc[1][e]);
-                sm[(base + 1024 * (g + 8)) ^ b6 ^ xs] = make_float2(acc[0][2 + e], acc[1][2 + e]);
+                for (int h = 0; h < 4; ++h) {
+                    const int m = t + 4 * h;
+                    const int x = (jj * m) & (kTcNL - 1);
+                    const float2 w = cmul(tab[kTcTab1 + (x >> 7)], tab[kTcTab2 + (x & 127)]);
+                    tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ xl[h]], w), bh[h], bl[h]);
+                }
+                tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);
             }
             __syncwarp();
+#pragma unroll
+            for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int base = k + 64 * (8 * rho + 2 * t + e);
+                    sm[(base + 1024 * g) ^ xsc[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
+                    sm[(base + 1024 * (g + 8)) ^ xsc[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
+                }
         }
     }
     __syncthreads();

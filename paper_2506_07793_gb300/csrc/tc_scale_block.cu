@@ -132,8 +132,25 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
 #pragma unroll
             for (int cc = 1; cc < CL; ++cc) v[cc] = cmul(v[cc], __ldg(&a.tw[(cc * t1) * (kTwN / N)]));
             dft<CL, +1>(v);
+            if (sub == 1) {  // no decimation: output o = t, one crop test per output
 #pragma unroll
-            for (int t2 = 0; t2 < CL; ++t2) store(t1 + kTcNL * t2, v[t2]);
+                for (int t2 = 0; t2 < CL; ++t2) {
+                    const int o = t1 + kTcNL * t2;
+                    if (o < n_out) {
+                        if (op) op[obase + o] = (IO)(fmaf(v[t2].x, v[t2].x, v[t2].y * v[t2].y) * inv2);
+                        if (oph) oph[obase + o] = (IO)phase_atan2(v[t2].y, v[t2].x);
+                        if (oc) {
+                            V2 z;
+                            z.x = (IO)(v[t2].x * inv);
+                            z.y = (IO)(v[t2].y * inv);
+                            oc[obase + o] = z;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t2 = 0; t2 < CL; ++t2) store(t1 + kTcNL * t2, v[t2]);
+            }
         }
         cl.sync();  // no CTA still reads this CTA's buffer
     } else {

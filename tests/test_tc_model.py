@@ -4,7 +4,7 @@ The model replays the kernel's index arithmetic lane by lane in numpy: the
 A/B/D fragment layouts of mma.sync.m16n8k16 (PTX ISA, "Matrix Fragments for
 mma.m16n8k16"), the hi/lo split of both operands into FP16 or BF16, the
 Stockham passes (pass 0 of radix 4 computed on the fly, radix 16 with
-Ns = 4, 64 and 1024, the residue-class ownership of pass B), the XOR-swizzled
+Ns = 4, 64 and 1024, the residue-class ownership of passes B and C), the XOR-swizzled
 shared-memory layout, the sparse pass-0 inputs of a banded row, and the
 cross-CTA radix-CL stage of a row split over CL residue classes.  Its result
 must equal the inverse DFT of the row (numpy's FFT) to the split's precision,
@@ -19,8 +19,9 @@ NL, NB, Q0 = 16384, 1024, 4096
 
 def tc_pad(i):
     i = np.asarray(i)
+    lo = (0x23013210 >> (((i >> 6) & 7) * 4)) & 15
     hi = (0x9C14D850 >> (((i >> 10) & 7) * 4)) & 15
-    return i ^ ((i >> 6) & 3) ^ hi
+    return i ^ lo ^ hi
 
 
 def round16(x, kind):
@@ -160,7 +161,9 @@ def model_fft16384(x_local, kind, sparse_first=None):
     for Ns, groups in (
         (64, [[(lambda n, k=4 * w + kk, rho=rho: k + 64 * (8 * rho + n)) for rho in range(2)]
               for w in range(16) for kk in range(4)]),
-        (1024, [[(lambda n, jj0=(w + 16 * i) * 8: jj0 + n)] for w in range(16) for i in range(8)]),
+        # pass C on the same classes: butterflies k + 64 (8 rho + n)
+        (1024, [[(lambda n, k=4 * w + kk, rho=rho: k + 64 * (8 * rho + n)) for rho in range(2)]
+                for w in range(16) for kk in range(4)]),
     ):
         # every unit reads exactly the slots it writes (in-place closure)
         for unit in groups:
@@ -243,23 +246,21 @@ def test_swizzle_is_a_permutation_and_conflict_free():
     for w in range(16):
         for i in range(8):
             jj0 = (w + 16 * i) * 8
-            for h in range(4):
-                assert ok(jj0 + g + NB * (t + 4 * h))                       # pass C loads
             for e in range(2):
                 jj = jj0 + 2 * t + e
                 for qh in (0, 8):
-                    assert ok(jj + 1024 * (g + qh))                          # pass C stores
                     k = jj & 3
                     assert ok((jj - k) * 16 + k + 4 * (g + qh))              # pass A stores
         for kk in range(4):
             k = 4 * w + kk
             for rho in range(2):
                 for h in range(4):
-                    assert ok(k + 64 * (8 * rho + g) + NB * (t + 4 * h))     # pass B loads
+                    assert ok(k + 64 * (8 * rho + g) + NB * (t + 4 * h))     # pass B, C loads
                 for e in range(2):
-                    jj = k + 64 * (8 * rho + 2 * t + e)
                     for qh in (0, 8):
+                        jj = k + 64 * (8 * rho + 2 * t + e)
                         assert ok((jj - k) * 16 + k + 64 * (g + qh))         # pass B stores
+                        assert ok(jj + 1024 * (g + qh))                      # pass C stores
     for base in range(0, NL, 32):
         assert ok(base + lanes)                                              # natural order
 
@@ -268,29 +269,22 @@ def test_hoisted_swizzle_terms_equal_tc_pad():
     """Passes B and C XOR fixed per-lane terms instead of evaluating tc_pad on
     every access; those terms equal tc_pad's on every index they touch."""
     lut = lambda b: (0x9C14D850 >> (b * 4)) & 15  # noqa: E731
+    lut_lo = lambda b: (0x23013210 >> (b * 4)) & 15  # noqa: E731
     lanes = np.arange(32)
     g, t = lanes >> 2, lanes & 3
     for w in range(16):
-        for kk in range(4):                                   # pass B
+        for kk in range(4):
             k = 4 * w + kk
             for rho in range(2):
                 for h in range(4):
                     i = k + 64 * (8 * rho + g) + NB * (t + 4 * h)
-                    assert np.array_equal(i ^ ((g & 3) ^ lut_v(lut, (t + 4 * h) & 7)), tc_pad(i))
+                    assert np.array_equal(i ^ (lut_v(lut_lo, g) ^ lut_v(lut, (t + 4 * h) & 7)), tc_pad(i))
                 for e in range(2):
                     for qh in (0, 8):
                         i = 1024 * (8 * rho + 2 * t + e) + k + 64 * (g + qh)
-                        assert np.array_equal(i ^ ((g & 3) ^ lut_v(lut, 2 * t + e)), tc_pad(i))
-        for i_ in range(8):                                   # pass C
-            jj0 = (w + 16 * i_) * 8
-            b6 = (jj0 >> 6) & 3
-            for h in range(4):
-                i = jj0 + g + NB * (t + 4 * h)
-                assert np.array_equal(i ^ b6 ^ lut_v(lut, (t + 4 * h) & 7), tc_pad(i))
-            for e in range(2):
-                for qh in (0, 8):
-                    i = jj0 + 2 * t + e + 1024 * (g + qh)
-                    assert np.array_equal(i ^ b6 ^ lut_v(lut, g), tc_pad(i))
+                        assert np.array_equal(i ^ (lut_v(lut_lo, g) ^ lut_v(lut, 2 * t + e)), tc_pad(i))
+                        i = k + 64 * (8 * rho + 2 * t + e) + 1024 * (g + qh)
+                        assert np.array_equal(i ^ (lut_v(lut_lo, 2 * t + e) ^ lut_v(lut, g)), tc_pad(i))
 
 
 def lut_v(lut, b):
