@@ -57,8 +57,10 @@ typedef enum {
     CWT_ECUDA = 4,         /* a CUDA runtime call failed (see cwt_plan_last_error) */
     CWT_EAGAIN = 5,        /* not enough data yet / nothing ready */
     CWT_EBUSY = 6,         /* admission refused: no slot or memory budget */
-    CWT_ETIMEDOUT = 7,     /* a bounded device wait gave up */
-    CWT_EDEVICE = 8        /* the device reported an error status */
+    /* 7 is not used: no kernel of this library waits on the device */
+    CWT_EDEVICE = 8        /* a kernel reported an error: in the bounds-checked build
+                              (-DCWT_BOUNDS_CHECK), an out-of-range shared-memory
+                              access or index, named by cwt_plan_last_error */
 } cwt_status;
 
 typedef enum {

@@ -39,12 +39,12 @@ def _headers():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def _compile(src, extra, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, verbose, bdir=BUILD, defs=()):
+    obj = os.path.join(bdir, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
         return obj, ""
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(defs) + list(extra) + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -52,32 +52,42 @@ def _compile(src, extra, verbose):
     return obj, (r.stdout + r.stderr) if verbose else ""
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+CHECK_LIB = os.path.join(LIBDIR, "libcwt_gb300_check.so")
+
+
+def build(force=False, verbose=False, extra_flags=(), check=False):
+    """Compile and link; returns the library path.
+
+    check=True builds the bounds-checked variant (-DCWT_BOUNDS_CHECK, see
+    csrc/check.cuh) into _lib/libcwt_gb300_check.so, objects in _build_check/;
+    load it by setting CWT_GB300_LIB to its path before importing the package."""
+    bdir = BUILD + "_check" if check else BUILD
+    lib = CHECK_LIB if check else LIB
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if force:
-        for o in glob.glob(os.path.join(BUILD, "*.o")):
+        for o in glob.glob(os.path.join(bdir, "*.o")):
             os.remove(o)
     extra = list(extra_flags) + (["-Xptxas", "-v"] if verbose else [])
+    defs = ["-DCWT_BOUNDS_CHECK"] if check else []
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, verbose, bdir, defs), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 print(log)
-    if (not os.path.exists(LIB) or force or extra
-            or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(LIB)):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if (not os.path.exists(lib) or force or extra
+            or max(os.path.getmtime(o) for o in objs) > os.path.getmtime(lib)):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -56,6 +57,50 @@ cudaError_t host_alloc(void **p, size_t bytes) {
         return cudaErrorMemoryAllocation;
     }
     return cudaMallocHost(p, bytes);
+}
+
+}  // namespace cwtk
+
+// ---- bounds-check builds (check.cuh): the translation units' violation words ----
+
+namespace cwtk {
+
+namespace {
+
+struct CheckUnit {
+    cudaError_t (*take)(unsigned long long *);
+    const char *unit;
+};
+
+std::mutex &check_mu() {
+    static std::mutex m;
+    return m;
+}
+std::vector<CheckUnit> &check_units() {
+    static std::vector<CheckUnit> v;
+    return v;
+}
+
+}  // namespace
+
+void check_register(cudaError_t (*take)(unsigned long long *), const char *unit) {
+    std::lock_guard<std::mutex> lk(check_mu());
+    check_units().push_back({take, unit});
+}
+
+bool check_collect(std::string *where) {
+    std::lock_guard<std::mutex> lk(check_mu());
+    bool hit = false;
+    for (const CheckUnit &u : check_units()) {
+        unsigned long long v = 0;
+        if (u.take(&v) != cudaSuccess || !v) continue;
+        if (!hit && where) {
+            *where = std::string("bounds check: ") + u.unit + " line " + std::to_string(v >> 32) +
+                     ", offset/index " + std::to_string(v & 0xffffffffu);
+        }
+        hit = true;
+    }
+    return hit;
 }
 
 }  // namespace cwtk

@@ -12,6 +12,7 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "fft_core.cuh"
 #include "internal.h"
@@ -80,6 +81,24 @@ cudaError_t prof_end(cwt_plan_s *p, cudaStream_t st, cwtk::ProfEvent *ev) {
 
 size_t out_elem_bytes(const cwt_plan_s *p) { return p->io == CWT_DTYPE_F64 ? 8 : 4; }
 
+// Bounds-check builds: wait for the launches on `st` and report a recorded
+// out-of-range access as CWT_EDEVICE.  Ordinary builds: nothing.
+cwt_status check_after(cwt_plan_s *p, cudaStream_t st) {
+#ifdef CWT_BOUNDS_CHECK
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(p, e);
+    std::string where;
+    if (cwtk::check_collect(&where)) {
+        if (p) p->last_error = where;
+        return CWT_EDEVICE;
+    }
+#else
+    (void)p;
+    (void)st;
+#endif
+    return CWT_OK;
+}
+
 cwt_status run_execute(cwt_plan_s *p, const void *sig, void *oc, void *op, void *oph,
                        cudaStream_t st) {
     cwtk::ProfEvent ev{};
@@ -92,7 +111,8 @@ cwt_status run_execute(cwt_plan_s *p, const void *sig, void *oc, void *op, void 
     if (e == cudaSuccess)
         e = tc ? cwtk::launch_scale_block_tc(p, oc, op, oph, st) : cwtk::launch_scale_block(p, oc, op, oph, st);
     if (e == cudaSuccess) e = prof_end(p, st, &ev);
-    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+    if (e != cudaSuccess) return fail_cuda(p, e);
+    return check_after(p, st);
 }
 
 void free_plan_memory(cwt_plan_s *p) {
@@ -133,7 +153,6 @@ const char *cwt_status_str(cwt_status s) {
         case CWT_ECUDA: return "CWT_ECUDA: CUDA runtime error";
         case CWT_EAGAIN: return "CWT_EAGAIN: not ready";
         case CWT_EBUSY: return "CWT_EBUSY: admission refused";
-        case CWT_ETIMEDOUT: return "CWT_ETIMEDOUT: device wait timed out";
         case CWT_EDEVICE: return "CWT_EDEVICE: device reported an error";
     }
     return "CWT_UNKNOWN_STATUS";
@@ -490,7 +509,8 @@ cwt_status cwt_execute_batch(cwt_plan p, const cwt_epoch *epochs, int n_epochs, 
         e = cwtk::batch_execute(p, epochs, n_epochs, (const float *)d_in, (float2 *)d_complex,
                                 (float *)d_power, (float *)d_phase, st, false);
     if (e == cudaSuccess) e = prof_end(p, st, &ev);
-    return e == cudaSuccess ? CWT_OK : fail_cuda(p, e);
+    if (e != cudaSuccess) return fail_cuda(p, e);
+    return check_after(p, st);
 }
 
 cwt_status cwt_plan_batch_stats(cwt_plan p, cwt_batch_stats *stats) {
@@ -534,7 +554,8 @@ cwt_status cwt_fft(const void *d_in, void *d_out, int n, int batch, int directio
         e = cwtk::launch_fft((const float2 *)d_in, (float2 *)d_out, ilog2c(n), batch, direction, tw,
                              (cudaStream_t)stream);
     if (e == cudaErrorMemoryAllocation) return CWT_ENOMEM;
-    return e == cudaSuccess ? CWT_OK : CWT_ECUDA;
+    if (e != cudaSuccess) return CWT_ECUDA;
+    return check_after(nullptr, (cudaStream_t)stream);
 }
 
 cwt_status cwt_plan_set_profiling(cwt_plan p, int enable) {

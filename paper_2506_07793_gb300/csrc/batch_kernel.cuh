@@ -85,14 +85,14 @@ __device__ __noinline__ void batch_forward(const BatchArgs &a, const BatchItem &
     float2 *st = spec + g * FftShape<N, R>::SMEM_F2;
     float2 *sp = spec + g * N;
     auto load = [&](int i) -> float2 { return make_float2((act && i < n) ? x[i] : 0.f, 0.f); };
-    auto store = [&](int t, float2 v) { sp[t] = v; };  // NP = 1: no staging to overwrite
+    auto store = [&](int t, float2 v) { *CWT_SMEM(&sp[t]) = v; };  // NP = 1: no staging to overwrite
     float2 v[R];
     fft_pass0_dense<N, R, -1>(v, j, load);
     fft_finish<N, R, -1, decltype(store), true>(v, st, tw, j, store);
     if constexpr (FftShape<N, R>::NP > 1) {
         __syncthreads();  // every staging read is done before the spectra overwrite it
 #pragma unroll
-        for (int r = 0; r < R; ++r) sp[j + r * (N / R)] = v[r];
+        for (int r = 0; r < R; ++r) *CWT_SMEM(&sp[j + r * (N / R)]) = v[r];
     }
 }
 
@@ -140,7 +140,7 @@ __device__ __noinline__ void batch_inverse(const BatchArgs &a, const BatchItem &
                 const int delta = (jj - b0) & (M - 1);
                 if (delta < B) {
                     const int k = (b0 + delta) & nmask;
-                    const float2 xv = sp[k];
+                    const float2 xv = *CWT_SMEM(&sp[k]);
                     const float w = __ldg(&W[k]);
                     acc = make_float2(xv.x * w, xv.y * w);
                 }
@@ -149,7 +149,7 @@ __device__ __noinline__ void batch_inverse(const BatchArgs &a, const BatchItem &
             for (int q = 0; q < fold; ++q) {
                 const int k = jj + q * M;
                 if (((k - b0) & nmask) < B) {
-                    const float2 xv = sp[k];
+                    const float2 xv = *CWT_SMEM(&sp[k]);
                     const float w = __ldg(&W[k]);
                     acc.x = fmaf(xv.x, w, acc.x);
                     acc.y = fmaf(xv.y, w, acc.y);

@@ -72,7 +72,7 @@ __device__ __forceinline__ void fft_cluster_row(float2 *__restrict__ sm, const f
     fft_finish<NL, kClR, SIGN, decltype(nostore), true>(v, sm, tw, tid, nostore);
     __syncthreads();  // every thread has read its last-pass inputs
 #pragma unroll
-    for (int r = 0; r < kClR; ++r) sm[spad2(tid + r * TL)] = v[r];  // A_rank[t1], natural order
+    for (int r = 0; r < kClR; ++r) *CWT_SMEM(&sm[spad2(tid + r * TL)]) = v[r];  // A_rank[t1], natural order
     cl.sync();
     // 2. cross-CTA radix-CL stage over this CTA's t1 range
 #pragma unroll 1
@@ -80,7 +80,7 @@ __device__ __forceinline__ void fft_cluster_row(float2 *__restrict__ sm, const f
         const int t1 = rank * (NL / CL) + q * TL + tid;
         float2 a[CL];
 #pragma unroll
-        for (int c = 0; c < CL; ++c) a[c] = ld_cluster(&sm[spad2(t1)], (unsigned)c);
+        for (int c = 0; c < CL; ++c) a[c] = ld_cluster(CWT_SMEM(&sm[spad2(t1)]), (unsigned)c);
 #pragma unroll
         for (int c = 1; c < CL; ++c) {
             float2 w = __ldg(&tw[(c * t1) * (kTwN / N)]);  // c * t1 < N

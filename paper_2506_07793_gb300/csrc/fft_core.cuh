@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
+
 namespace cwtk {
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
@@ -247,7 +249,7 @@ __device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ 
 #pragma unroll
         for (int g = 0; g < G0; ++g)
 #pragma unroll
-            for (int r = 0; r < R0; ++r) sm[spad2((j + g * T) * R0 + r)] = v[g * R0 + r];
+            for (int r = 0; r < R0; ++r) *CWT_SMEM(&sm[spad2((j + g * T) * R0 + r)]) = v[g * R0 + r];
     }
     // ---- passes 1..NP-1: radix R, Ns = R0 * R^(p-1).  (Per-element padded
     // indices measured faster on GB300 than base-plus-stride addressing.)
@@ -256,7 +258,7 @@ __device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ 
     for (int p = 1; p < S::NP; ++p) {
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm[spad2(j + r * T)];
+        for (int r = 0; r < R; ++r) v[r] = *CWT_SMEM(&sm[spad2(j + r * T)]);
         const int k = j & (Ns - 1);
         float2 w1 = __ldg(&tw[k * (kTwN / (Ns * R))]);
         if (SIGN < 0) w1.y = -w1.y;
@@ -271,7 +273,7 @@ __device__ __forceinline__ void fft_finish(float2 (&v)[R], float2 *__restrict__ 
             __syncthreads();
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[spad2(base + r * Ns)] = v[r];
+            for (int r = 0; r < R; ++r) *CWT_SMEM(&sm[spad2(base + r * Ns)]) = v[r];
         }
         Ns *= R;
     }

@@ -61,6 +61,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "fft_core.cuh"
 
 namespace cwtk {
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tc_dft16_afrag(uint32_t (&ahi)[2][2][4], uint32_
         for (int r = 0; r < 4; ++r) {
             const int q = g + 8 * (r & 1);
             const int m = 8 * kt + t + 4 * (r >> 1);
-            const float2 w = root16[((q * m) & 15) * stride];  // F16[q][m] = c + i s
+            const float2 w = *CWT_SMEM(&root16[((q * m) & 15) * stride]);  // F16[q][m] = c + i s
             // m-tile 0 (Re y_q): (c, -s) on (Re x_m, Im x_m); m-tile 1 (Im y_q): (s, c)
             tc_split<T>(make_float2(w.x, -w.y), ahi[0][kt][r], alo[0][kt][r]);
             tc_split<T>(make_float2(w.y, w.x), ahi[1][kt][r], alo[1][kt][r]);
@@ -200,7 +201,7 @@ __device__ __forceinline__ void tc_fill_twiddles(float2 *__restrict__ tab, const
         else idx = (i - kTcTab2) * (kTwN / kTcNL);
         float2 w = __ldg(&tw[idx]);
         if (SIGN < 0) w.y = -w.y;
-        tab[i] = w;
+        *CWT_SMEM(&tab[i]) = w;
     }
 }
 
@@ -247,7 +248,7 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int m = t + 4 * h;
-            tc_split<T>(cmul(pass0_out(jj + kTcNB * m), tab[kTcTabA + 16 * k + m]), bh[h], bl[h]);
+            tc_split<T>(cmul(pass0_out(jj + kTcNB * m), *CWT_SMEM(&tab[kTcTabA + 16 * k + m])), bh[h], bl[h]);
         }
         float acc[2][4];
         tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
@@ -255,8 +256,8 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
         for (int e = 0; e < 2; ++e) {
             const int jn = jj0 + 2 * t + e, kn = jn & 3;
             const int base = (jn - kn) * 16 + kn;
-            sm[tc_pad(base + 4 * g)] = make_float2(acc[0][e], acc[1][e]);
-            sm[tc_pad(base + 4 * (g + 8))] = make_float2(acc[0][2 + e], acc[1][2 + e]);
+            *CWT_SMEM(&sm[tc_pad(base + 4 * g)]) = make_float2(acc[0][e], acc[1][e]);
+            *CWT_SMEM(&sm[tc_pad(base + 4 * (g + 8))]) = make_float2(acc[0][2 + e], acc[1][2 + e]);
         }
     }
     __syncthreads();
@@ -289,7 +290,7 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const int m = t + 4 * h;
-                    tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ xl[h]], tab[kTcTabB + 16 * k + m]), bh[h], bl[h]);
+                    tc_split<T>(cmul(*CWT_SMEM(&sm[(jj + kTcNB * m) ^ xl[h]]), *CWT_SMEM(&tab[kTcTabB + 16 * k + m])), bh[h], bl[h]);
                 }
                 tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);
             }
@@ -299,8 +300,8 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int base = 1024 * (8 * rho + 2 * t + e) + k;
-                    sm[(base + 64 * g) ^ xsb[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
-                    sm[(base + 64 * (g + 8)) ^ xsb[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
+                    *CWT_SMEM(&sm[(base + 64 * g) ^ xsb[e]]) = make_float2(acc[rho][0][e], acc[rho][1][e]);
+                    *CWT_SMEM(&sm[(base + 64 * (g + 8)) ^ xsb[e]]) = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
                 }
             __syncwarp();  // pass B's outputs of the class are visible to the warp
             // pass C: twiddle exp(SIGN 2 pi i jj m / 16384) = table entries x >> 7 and x & 127
@@ -312,8 +313,8 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
                 for (int h = 0; h < 4; ++h) {
                     const int m = t + 4 * h;
                     const int x = (jj * m) & (kTcNL - 1);
-                    const float2 w = cmul(tab[kTcTab1 + (x >> 7)], tab[kTcTab2 + (x & 127)]);
-                    tc_split<T>(cmul(sm[(jj + kTcNB * m) ^ xl[h]], w), bh[h], bl[h]);
+                    const float2 w = cmul(*CWT_SMEM(&tab[kTcTab1 + (x >> 7)]), *CWT_SMEM(&tab[kTcTab2 + (x & 127)]));
+                    tc_split<T>(cmul(*CWT_SMEM(&sm[(jj + kTcNB * m) ^ xl[h]]), w), bh[h], bl[h]);
                 }
                 tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);
             }
@@ -323,8 +324,8 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int base = k + 64 * (8 * rho + 2 * t + e);
-                    sm[(base + 1024 * g) ^ xsc[e]] = make_float2(acc[rho][0][e], acc[rho][1][e]);
-                    sm[(base + 1024 * (g + 8)) ^ xsc[e]] = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
+                    *CWT_SMEM(&sm[(base + 1024 * g) ^ xsc[e]]) = make_float2(acc[rho][0][e], acc[rho][1][e]);
+                    *CWT_SMEM(&sm[(base + 1024 * (g + 8)) ^ xsc[e]]) = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
                 }
         }
     }

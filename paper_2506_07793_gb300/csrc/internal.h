@@ -36,6 +36,12 @@ cudaError_t hmalloc(T **p, size_t bytes) {
     return host_alloc(reinterpret_cast<void **>(p), bytes);
 }
 
+// Bounds-check builds (-DCWT_BOUNDS_CHECK, check.cuh): true when a kernel
+// recorded an out-of-range shared-memory access or index since the last call
+// (the words are cleared); *where names the first one.  Always false in an
+// ordinary build.
+bool check_collect(std::string *where);
+
 // Per-device FP32 twiddle table exp(2 pi i m / 2^17), built in FP64 on first use.
 cudaError_t device_twiddles(const float2 **out);
 

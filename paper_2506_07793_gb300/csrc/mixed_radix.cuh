@@ -295,10 +295,10 @@ __device__ __forceinline__ void mr_first_body(const MrPass &ps, float2 *__restri
             if constexpr (LIN && R % 16 == 0) {
                 float2 *dst = sm + spad2(b * R);
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst[spad2(r)] = v[r];
+                for (int r = 0; r < R; ++r) *CWT_SMEM(&dst[spad2(r)]) = v[r];
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[spad2(b * R + r)] = v[r];
+                for (int r = 0; r < R; ++r) *CWT_SMEM(&sm[spad2(b * R + r)]) = v[r];
             }
         }
     }
@@ -330,10 +330,10 @@ __device__ __forceinline__ void mr_first_sparse_body(const MrPass &ps, float2 *_
             if constexpr (LIN && R % 16 == 0) {
                 float2 *dst = sm + spad2(b * R);
 #pragma unroll
-                for (int t = 0; t < R; ++t) dst[spad2(t)] = v[t];
+                for (int t = 0; t < R; ++t) *CWT_SMEM(&dst[spad2(t)]) = v[t];
             } else {
 #pragma unroll
-                for (int t = 0; t < R; ++t) sm[spad2(b * R + t)] = v[t];
+                for (int t = 0; t < R; ++t) *CWT_SMEM(&sm[spad2(b * R + t)]) = v[t];
             }
         }
     }
@@ -355,10 +355,10 @@ __device__ __forceinline__ void mr_mid_body(const MrPass &ps, float2 *__restrict
             if (lin_in) {
                 const float2 *src = sm + spad2(b);
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[g][r] = src[r * nbp];
+                for (int r = 0; r < R; ++r) v[g][r] = *CWT_SMEM(&src[r * nbp]);
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[g][r] = sm[spad2(b + r * nb)];
+                for (int r = 0; r < R; ++r) v[g][r] = *CWT_SMEM(&sm[spad2(b + r * nb)]);
             }
         }
     }
@@ -373,10 +373,10 @@ __device__ __forceinline__ void mr_mid_body(const MrPass &ps, float2 *__restrict
             if (lin_out) {
                 float2 *dst = sm + spad2(base);
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst[r * nsp] = v[g][r];
+                for (int r = 0; r < R; ++r) *CWT_SMEM(&dst[r * nsp]) = v[g][r];
             } else {
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[spad2(base + r * ps.Ns)] = v[g][r];
+                for (int r = 0; r < R; ++r) *CWT_SMEM(&sm[spad2(base + r * ps.Ns)]) = v[g][r];
             }
         }
     }

@@ -312,5 +312,9 @@ extern "C" cwt_status cwt_execute_noalloc(const float *d_signal, int channels, i
         }
     }
     if (e == cudaErrorMemoryAllocation) return CWT_ENOMEM;
+#ifdef CWT_BOUNDS_CHECK
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && check_collect(nullptr)) return CWT_EDEVICE;
+#endif
     return e == cudaSuccess ? CWT_OK : CWT_ECUDA;
 }

@@ -83,7 +83,7 @@ __device__ __forceinline__ void mr_sb_row(const MrArgs &a, int N, int T, int R0,
         double *op = (double *)a.out_p + obase, *oph = (double *)a.out_ph + obase;
 #pragma unroll 1
         for (int o = rs.j; o < n_out; o += T) {
-            const float2 v = sm[spad2(o * sub)];
+            const float2 v = *CWT_SMEM(&sm[spad2(o * sub)]);
             if (a.out_c) oc[o] = make_double2(v.x, v.y);
             if (a.out_p) op[o] = (double)fmaf(v.x, v.x, v.y * v.y);
             if (a.out_ph) mr_phase_d(oph + o, v);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void mr_sb_row(const MrArgs &a, int N, int T, int R0,
             const int step = spad2(T * sub);
 #pragma unroll 2
             for (int o = rs.j; o < n_out; o += T, src += step) {
-                const float2 v = *src;
+                const float2 v = *CWT_SMEM(src);
                 if (a.out_c) oc[o] = v;
                 if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
                 if (a.out_ph) mr_phase_f(oph + o, v);
@@ -105,7 +105,7 @@ __device__ __forceinline__ void mr_sb_row(const MrArgs &a, int N, int T, int R0,
         } else {
 #pragma unroll 2
             for (int o = rs.j; o < n_out; o += T) {
-                const float2 v = sm[spad2(o * sub)];
+                const float2 v = *CWT_SMEM(&sm[spad2(o * sub)]);
                 if (a.out_c) oc[o] = v;
                 if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
                 if (a.out_ph) mr_phase_f(oph + o, v);
@@ -182,7 +182,7 @@ mr_forward_kernel(const void *__restrict__ x, int f64, int n, float2 *__restrict
         mr_row_pair<-1, RA, RB>(sch, sm, twN, rs.j, rs.active, false, load, none);
     if (rs.active) {
 #pragma unroll 4
-        for (int t = rs.j; t < N; t += sch.T) out[t] = sm[spad2(t)];
+        for (int t = rs.j; t < N; t += sch.T) out[t] = *CWT_SMEM(&sm[spad2(t)]);
     }
 }
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kSThreads) stream_kernel(const StreamItem *__r
             return make_float2(v, 0.f);
         };
         auto store = [&](int t, float2 v) {
-            if (act) spec[t] = v;
+            if (act) spec[CWT_IDX(t, kSW)] = v;
         };
         fft_row<kSW, kSR, -1>(st, tw, j, load, store);
     }
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kSThreads) stream_kernel(const StreamItem *__r
         const int b0 = it.band[2 * (act ? s : 0)], B = act ? it.band[2 * s + 1] : 0;
         auto load = [&](int k) -> float2 {
             if (((k - b0) & (kSW - 1)) < B) {
-                const float2 x = spec[k];
+                const float2 x = spec[CWT_IDX(k, kSW)];
                 const float w = __ldg(&W[k]);
                 return make_float2(x.x * w, x.y * w);
             }
@@ -630,7 +630,15 @@ cwt_status cwt_server_sync(cwt_server s) {
     Guard g(s->device);
     if (!g.ok) return CWT_ECUDA;
     cudaError_t e = cudaStreamSynchronize(s->st);
-    return e == cudaSuccess ? CWT_OK : cuda_fail(s, e);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+#ifdef CWT_BOUNDS_CHECK
+    std::string where;
+    if (check_collect(&where)) {
+        s->last_error = where;
+        return CWT_EDEVICE;
+    }
+#endif
+    return CWT_OK;
 }
 
 cwt_status cwt_stream_pull(cwt_server s, int id, float *out, int max_hops, int *n_hops,

@@ -85,7 +85,7 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
         const bool in = d0 < Bm;
         const int m = (m_first + d0) & (kTcNL - 1);
         r = (m - j) >> 12;  // m = j + r Q when in band (Q = 4096)
-        const int k = in ? rank + CL * m : rank;
+        const int k = CWT_IDX(in ? rank + CL * m : rank, N);
         const float2 xv = X[k];
         const float w = in ? W[k] * sc : 0.f;
         x = make_float2(xv.x * w, xv.y * w);
@@ -128,7 +128,7 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
             const int t1 = rank * (kTcNL / CL) + q * kTcThreads + (int)threadIdx.x;
             float2 v[CL];
 #pragma unroll
-            for (int cc = 0; cc < CL; ++cc) v[cc] = ld_cluster(&sm[tc_pad(t1)], (unsigned)cc);
+            for (int cc = 0; cc < CL; ++cc) v[cc] = ld_cluster(CWT_SMEM(&sm[tc_pad(t1)]), (unsigned)cc);
 #pragma unroll
             for (int cc = 1; cc < CL; ++cc) v[cc] = cmul(v[cc], __ldg(&a.tw[(cc * t1) * (kTwN / N)]));
             dft<CL, +1>(v);
@@ -157,7 +157,7 @@ __device__ __forceinline__ void tc_row(const TcArgs &a, float2 *sm, int row, int
 #pragma unroll 4
         for (int q = 0; q < kTcNL / kTcThreads; ++q) {
             const int t1 = q * kTcThreads + (int)threadIdx.x;
-            store(t1, sm[tc_pad(t1)]);
+            store(t1, *CWT_SMEM(&sm[tc_pad(t1)]));
         }
     }
 }

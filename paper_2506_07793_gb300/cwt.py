@@ -11,7 +11,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libcwt_gb300.so")
+# CWT_GB300_LIB selects another build of the library (the bounds-checked
+# variant, _lib/libcwt_gb300_check.so); default the ordinary one.
+LIB_PATH = os.environ.get("CWT_GB300_LIB") or os.path.join(_HERE, "_lib", "libcwt_gb300.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -22,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # ---- constants (mirror include/cwt.h) ----
 CWT_OK, CWT_EINVAL, CWT_ENOMEM, CWT_EUNSUPPORTED, CWT_ECUDA = 0, 1, 2, 3, 4
-CWT_EAGAIN, CWT_EBUSY, CWT_ETIMEDOUT, CWT_EDEVICE = 5, 6, 7, 8
+CWT_EAGAIN, CWT_EBUSY, CWT_EDEVICE = 5, 6, 8
 CWT_WAVELET_MORLET, CWT_WAVELET_GABOR, CWT_WAVELET_GMW = 0, 1, 2
 CWT_EDGE_CYCLIC, CWT_EDGE_LINEAR = 0, 1
 CWT_OUT_COMPLEX, CWT_OUT_POWER, CWT_OUT_PHASE = 1, 2, 4

@@ -40,9 +40,23 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(9):
-        assert lib.cwt_status_str(s).startswith("CWT_")
+    for s in (0, 1, 2, 3, 4, 5, 6, 8):
+        assert lib.cwt_status_str(s).startswith("CWT_") and "UNKNOWN" not in lib.cwt_status_str(s)
+    assert "UNKNOWN" in lib.cwt_status_str(7)  # no status 7: nothing waits on the device
     assert "UNKNOWN" in lib.cwt_status_str(99)
+
+
+def test_bounds_check_build_compiles_and_exports(lib):
+    """The bounds-checked variant (-DCWT_BOUNDS_CHECK) builds and exports the
+    same symbols (its kernels run in tests/test_gpu_bounds_check.py)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_cwt_build", os.path.join(ROOT, "paper_2506_07793_gb300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    so = ctypes.CDLL(b.build(check=True))
+    for name in declared_functions():
+        assert hasattr(so, name), name
 
 
 def test_options_defaults(lib):
