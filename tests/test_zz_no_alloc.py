@@ -5,12 +5,14 @@ real-time EEG / BCI loop whose deadline a blocking cudaMalloc could break, or a
 plug-in whose host owns the GPU memory).  This file checks, through the C ABI,
 that two calls in a row (different sizes, so the second reuses scratch the
 first one filled) give the plan path's results (cwt_plan_create +
-cwt_execute) within the FP32 tolerance, and that oversized requests are refused.
+cwt_execute) within the FP32 tolerance, and the FP64 oracle's on sampled rows,
+and that oversized requests are refused.
 It is named to be collected last; it also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
 
+import oracle
 from eeg_synth import eeg
 from tests.metrics import FP32_TOL, complex_err, phase_err, power_err
 
@@ -58,6 +60,12 @@ def test_two_calls_in_a_row_match_plan_path(lib):
         assert power_err(p.cpu().numpy(), rc).max() <= FP32_TOL
         assert phase_err(ph.cpu().numpy(), rc).max() <= FP32_TOL
         assert np.abs(p.cpu().numpy() - ref["power"]).max() <= FP32_TOL * ref["power"].max()
+        # and directly against the FP64 oracle on a few rows (every row of the small case)
+        rows = [(0, 0), (C - 1, S - 1), (C // 2, S // 2)] if C > 8 else [(a, b) for a in range(C) for b in range(S)]
+        xo = x.cpu().numpy().astype(np.float64)
+        orc = oracle.cwt_rows(xo, lib.cwt_fft_length(n), fs, freqs, cycles, rows)
+        got = c.cpu().numpy()
+        assert complex_err(np.stack([got[a, b] for a, b in rows]), orc).max() <= FP32_TOL
 
 
 def test_oversized_request_is_refused(lib):
