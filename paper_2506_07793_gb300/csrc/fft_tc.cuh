@@ -182,24 +182,29 @@ __device__ __forceinline__ float2 rot4(float2 x, int n) {
     return (n & 2) ? make_float2(-y.x, -y.y) : y;
 }
 
-// Twiddles of the three passes in shared memory, after the row (float2):
-//   [0, 64)       pass A: w^m = exp(SIGN 2 pi i k m / 64),    entry 16 k + m (k < 4)
-//   [64, 1088)    pass B: w^m = exp(SIGN 2 pi i k m / 1024),  entry 16 k + m (k < 64)
-//   [1088, 1216)  exp(SIGN 2 pi i 128 a / 16384), a < 128
-//   [1216, 1344)  exp(SIGN 2 pi i b / 16384), b < 128
-// so pass C's exp(SIGN 2 pi i x / 16384) is the product of entries x >> 7 and
-// x & 127 of the last two.  All come from the FP64-generated FP32 table tw.
-constexpr int kTcTabA = 0, kTcTabB = 64, kTcTab1 = 1088, kTcTab2 = 1216, kTcTabF2 = 1344;
+// Twiddles of the three passes in shared memory, after the row (float2),
+// laid out so that a warp's reads hit distinct bank pairs or one address:
+//   [0, 80)       pass A: exp(SIGN 2 pi i k m / 64),     entry 20 k + m (k < 4)
+//   [80, 1104)    pass B: exp(SIGN 2 pi i k m / 1024),   entry 16 k + m (k < 64)
+//   [1104, 2128)  pass C: exp(SIGN 2 pi i k m / 16384),  entry 16 k + m (k < 64)
+//   [2128, 2448)  pass C: exp(SIGN 2 pi i a m / 256),    entry 20 a + m (a < 16)
+//   [2448, 2464)  exp(SIGN 2 pi i e / 16), the DFT matrix's entries
+// Pass C's butterfly jj = k + 64 a (k < 64, a < 16) needs exp(SIGN 2 pi i jj m /
+// 16384), the product of its two tables' entries.  All come from the
+// FP64-generated FP32 table tw of the 2^17-th roots of unity.
+constexpr int kTcTabA = 0, kTcTabB = 80, kTcTabC1 = 1104, kTcTabC2 = 2128, kTcTabR = 2448,
+              kTcTabF2 = 2464;
 
 template <int SIGN>
 __device__ __forceinline__ void tc_fill_twiddles(float2 *__restrict__ tab, const float2 *__restrict__ tw) {
     for (int i = threadIdx.x; i < kTcTabF2; i += kTcThreads) {
-        int idx;
-        if (i < kTcTabB) idx = (((i >> 4) * (i & 15)) & 63) * (kTwN / 64);
-        else if (i < kTcTab1) idx = ((((i - kTcTabB) >> 4) * ((i - kTcTabB) & 15)) & 1023) * (kTwN / 1024);
-        else if (i < kTcTab2) idx = (i - kTcTab1) * 128 * (kTwN / kTcNL);
-        else idx = (i - kTcTab2) * (kTwN / kTcNL);
-        float2 w = __ldg(&tw[idx]);
+        int x;  // exponent in units of 2 pi / 2^17
+        if (i < kTcTabB) x = (((i / 20) * (i % 20)) & 63) * (kTwN / 64);
+        else if (i < kTcTabC1) x = ((((i - kTcTabB) >> 4) * ((i - kTcTabB) & 15)) & 1023) * (kTwN / 1024);
+        else if (i < kTcTabC2) x = (((i - kTcTabC1) >> 4) * ((i - kTcTabC1) & 15)) * (kTwN / kTcNL);
+        else if (i < kTcTabR) x = ((((i - kTcTabC2) / 20) * ((i - kTcTabC2) % 20)) & 255) * (kTwN / 256);
+        else x = (i - kTcTabR) * (kTwN / 16);
+        float2 w = __ldg(&tw[x]);
         if (SIGN < 0) w.y = -w.y;
         *CWT_SMEM(&tab[i]) = w;
     }
@@ -220,7 +225,7 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
                                             bool sparse, Load &load, First &first) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     uint32_t ahi[2][2][4], alo[2][2][4];
-    tc_dft16_afrag<T>(ahi, alo, lane, tab + kTcTab1, 8);  // exp(SIGN 2 pi i 8e / 128)
+    tc_dft16_afrag<T>(ahi, alo, lane, tab + kTcTabR, 1);
     constexpr int Q0 = kTcNL / 4;
     const int sgn = SIGN > 0 ? 1 : -1;
 
@@ -248,7 +253,7 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int m = t + 4 * h;
-            tc_split<T>(cmul(pass0_out(jj + kTcNB * m), *CWT_SMEM(&tab[kTcTabA + 16 * k + m])), bh[h], bl[h]);
+            tc_split<T>(cmul(pass0_out(jj + kTcNB * m), *CWT_SMEM(&tab[kTcTabA + 20 * k + m])), bh[h], bl[h]);
         }
         float acc[2][4];
         tc_dft16_mma<T>(acc, ahi, alo, bh, bl);
@@ -304,16 +309,17 @@ __device__ __forceinline__ void tc_fft16384(float2 *__restrict__ sm, const float
                     *CWT_SMEM(&sm[(base + 64 * (g + 8)) ^ xsb[e]]) = make_float2(acc[rho][0][2 + e], acc[rho][1][2 + e]);
                 }
             __syncwarp();  // pass B's outputs of the class are visible to the warp
-            // pass C: twiddle exp(SIGN 2 pi i jj m / 16384) = table entries x >> 7 and x & 127
+            // pass C: twiddle exp(SIGN 2 pi i jj m / 16384), jj = k + 64 a, from the
+            // tables of exp(SIGN 2 pi i k m / 16384) and exp(SIGN 2 pi i a m / 256)
 #pragma unroll
             for (int rho = 0; rho < 2; ++rho) {
-                const int jj = k + 64 * (8 * rho + g);
+                const int a = 8 * rho + g, jj = k + 64 * a;
                 uint32_t bh[4], bl[4];
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     const int m = t + 4 * h;
-                    const int x = (jj * m) & (kTcNL - 1);
-                    const float2 w = cmul(*CWT_SMEM(&tab[kTcTab1 + (x >> 7)]), *CWT_SMEM(&tab[kTcTab2 + (x & 127)]));
+                    const float2 w = cmul(*CWT_SMEM(&tab[kTcTabC1 + 16 * k + m]),
+                                          *CWT_SMEM(&tab[kTcTabC2 + 20 * a + m]));
                     tc_split<T>(cmul(*CWT_SMEM(&sm[(jj + kTcNB * m) ^ xl[h]]), w), bh[h], bl[h]);
                 }
                 tc_dft16_mma<T>(acc[rho], ahi, alo, bh, bl);

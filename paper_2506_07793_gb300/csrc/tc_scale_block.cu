@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scale_block_kernel(const TcA
     tc_row<1, T, IO>(a, tcsm, blockIdx.x, 0);
 }
 
-constexpr int kTcSmemBytes = (kTcNL + kTcTabF2) * (int)sizeof(float2);  // the row + twiddles, 138.5 KB
+constexpr int kTcSmemBytes = (kTcNL + kTcTabF2) * (int)sizeof(float2);  // the row + twiddles, 147.3 KB
 
 // chmax[c] = max_k max(|Re X_c[k]|, |Im X_c[k]|): one CTA per channel.
 __global__ void __launch_bounds__(512) tc_chmax_kernel(const float2 *__restrict__ spec, int N,
