@@ -61,7 +61,9 @@ struct ClArgs {
     int S, n_out, sub;
 };
 
-template <int N, typename IO>
+// PLAIN: no decimation (output o = t), so each output needs only the crop
+// test; the general form also keeps t = 0 (mod sub).
+template <int N, typename IO, bool PLAIN>
 __global__ void __cluster_dims__(N / kClPoints, 1, 1) __launch_bounds__(kClThreads, 1)
 cl_scale_block_kernel(const ClArgs a) {
     using V2 = typename IO2c<IO>::type;
@@ -87,7 +89,7 @@ cl_scale_block_kernel(const ClArgs a) {
     const int sub = a.sub, n_out = a.n_out;
     auto store = [&](int t, float2 v) {
         int o = t;
-        if (sub != 1) {
+        if constexpr (!PLAIN) {
             if (t % sub) return;
             o = t / sub;
         }
@@ -144,13 +146,19 @@ cudaError_t cl_forward_n(const void *x, int C, int n, float2 *spec, const float2
     return cudaGetLastError();
 }
 
+template <int N, typename IO, bool PLAIN>
+cudaError_t cl_sb_nk(const ClArgs &a, int rows, cudaStream_t st) {
+    static std::atomic<unsigned> done{0};
+    cudaError_t e = cl_attr(cl_scale_block_kernel<N, IO, PLAIN>, ClusterShape<N>::SMEM_BYTES, &done);
+    if (e != cudaSuccess) return e;
+    cl_scale_block_kernel<N, IO, PLAIN>
+        <<<rows * ClusterShape<N>::CL, kClThreads, ClusterShape<N>::SMEM_BYTES, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int N, typename IO>
 cudaError_t cl_sb_n(const ClArgs &a, int rows, cudaStream_t st) {
-    static std::atomic<unsigned> done{0};
-    cudaError_t e = cl_attr(cl_scale_block_kernel<N, IO>, ClusterShape<N>::SMEM_BYTES, &done);
-    if (e != cudaSuccess) return e;
-    cl_scale_block_kernel<N, IO><<<rows * ClusterShape<N>::CL, kClThreads, ClusterShape<N>::SMEM_BYTES, st>>>(a);
-    return cudaGetLastError();
+    return a.sub == 1 ? cl_sb_nk<N, IO, true>(a, rows, st) : cl_sb_nk<N, IO, false>(a, rows, st);
 }
 
 template <int N, int SIGN>
