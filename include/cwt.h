@@ -191,7 +191,7 @@ typedef struct {
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
                                compiled for exactly this N and radix schedule (10000,
                                8000, 5000, 4000, 2500, 2000, 1000, 500),
-                               else 0; the forward FFT stays on inlined_pair's kernel */
+                               else 0; the forward FFTs then run on the same schedule */
     int precision;          /* cwt_precision of the inverse FFTs */
 } cwt_plan_info_t;
 

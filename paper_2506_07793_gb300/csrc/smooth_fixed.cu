@@ -31,7 +31,29 @@ cudaError_t fixed_launch(const MrArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <class FX>
+cudaError_t fixed_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    static std::atomic<unsigned> done{0};
+    constexpr int smem = FX::ROWS * (FX::N + (FX::N >> 4)) * 8;
+    cudaError_t e = ensure_smem_attr(mr_fixed_forward_kernel<FX>, smem, &done);
+    if (e != cudaSuccess) return e;
+    const int grid = (p->C + FX::ROWS - 1) / FX::ROWS;
+    mr_fixed_forward_kernel<FX><<<grid, FX::THREADS, smem, st>>>(signal, p->io == CWT_DTYPE_F64, p->n,
+                                                                 p->spec, p->twN, p->C);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t mr_fixed_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    switch (p->sch.fixed) {
+#define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \
+    case I: return fixed_fwd_launch<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, signal, st);
+        CWT_MR_FIXED(CWT_MR_CASE)
+#undef CWT_MR_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 int mr_fixed_index(const MrSchedule &s) {
 #define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \

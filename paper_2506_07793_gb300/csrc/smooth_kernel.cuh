@@ -217,6 +217,39 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
 // Index of the fixed-length kernel whose schedule equals s, or -1.
 int mr_fixed_index(const MrSchedule &s);
 cudaError_t mr_fixed_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st);
+// The forward FFTs of a plan whose schedule is a fixed-length one (same
+// schedule, SIGN -1, the forward kernel's epilogue).
+cudaError_t mr_fixed_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+
+// Forward FFT of each zero-padded channel on a fixed-length schedule FX.
+template <class FX>
+__global__ void __launch_bounds__(FX::THREADS, FX::MINB)
+mr_fixed_forward_kernel(const void *__restrict__ x, int f64, int n, float2 *__restrict__ spec,
+                        const float2 *__restrict__ twN, int C) {
+    extern __shared__ float2 mrsm[];
+    constexpr int N = FX::N;
+    RowSlot rs;
+    rs.rr = (int)threadIdx.x / FX::T;
+    rs.j = (int)threadIdx.x - rs.rr * FX::T;
+    rs.active = rs.rr < FX::ROWS && (int)blockIdx.x * FX::ROWS + rs.rr < C;
+    const int row = rs.active ? (int)blockIdx.x * FX::ROWS + rs.rr : 0;
+    const int rr = rs.rr < FX::ROWS ? rs.rr : 0;
+    float2 *sm = mrsm + (size_t)rr * (N + (N >> 4));
+    const float *xf = (const float *)x + (size_t)row * n;
+    const double *xd = (const double *)x + (size_t)row * n;
+    float2 *out = spec + (size_t)row * N;
+    auto load = [=](int i) -> float2 {
+        float v = 0.f;
+        if (i < n) v = f64 ? (float)xd[i] : xf[i];
+        return make_float2(v, 0.f);
+    };
+    auto none = [](int, int, unsigned, int &, float2 &) -> bool { return false; };
+    mr_row_fixed<FX, -1>(sm, twN, rs.j, rs.active, false, load, none);
+    if (rs.active) {
+#pragma unroll 4
+        for (int t = rs.j; t < N; t += FX::T) out[t] = *CWT_SMEM(&sm[spad2(t)]);
+    }
+}
 
 // The inlined radix pairs (index = MrSchedule::fast), chosen for 2^a 5^b
 // lengths (whole seconds of EEG at 250 / 500 / 1000 Hz), each instantiated in
