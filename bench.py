@@ -745,23 +745,29 @@ def precision_suite(args):
     """The precision workload (256 ch x 122880 @2048 Hz, N = 131072, 128 scales,
     power + phase) in its three inverse-FFT arithmetics -- FP32 on clusters,
     tensor-core FP16 and BF16 hi/lo -- beside the plain FP32 cuFFT pipeline,
-    each timed like the headline (CUDA events, L2 flushed between steps)."""
+    each timed like the headline (CUDA events, L2 flushed between steps); and
+    FP32 under the paper's smooth padding, where 122880 = 8 x 15360 needs none
+    (mixed-radix clusters)."""
     out = {}
-    for prec in ("fp32", "tc_fp16", "tc_bf16"):
-        a = sub_args(args, workload="precision", precision=prec, pad="pow2", steps=5, warmup=3,
-                     no_e2e=prec != "fp32", no_plain=prec != "fp32", no_other=True,
-                     no_cpu=prec != "fp32", cpu_seconds=5.0, e2e_steps=1, channels=0)
+    for key, prec, pad in (("fp32", "fp32", "pow2"), ("tc_fp16", "tc_fp16", "pow2"),
+                           ("tc_bf16", "tc_bf16", "pow2"), ("fp32_smooth", "fp32", "smooth")):
+        main = key == "fp32"
+        a = sub_args(args, workload="precision", precision=prec, pad=pad, steps=5, warmup=3,
+                     no_e2e=not main, no_plain=not main, no_other=True,
+                     no_cpu=not main, cpu_seconds=5.0, e2e_steps=1, channels=0)
         line = run_plan_workload(a, "precision")
         keep = {k: line[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "clocks",
                                      "gpu_launches", "e2e", "cpu_baseline", "plain_fp32_gpu",
                                      "steps", "warmup") if k in line}
-        out[prec] = keep
-        if prec == "fp32":
+        if not main:
+            keep["fft_length"] = line["config"]["fft_length"]
+        out[key] = keep
+        if main:
             out["config"] = line["config"]
     plain = out["fp32"].pop("plain_fp32_gpu", None)
     if plain is not None:
         out["plain_fp32_gpu"] = plain
-        for prec in ("fp32", "tc_fp16", "tc_bf16"):
+        for prec in ("fp32", "tc_fp16", "tc_bf16", "fp32_smooth"):
             out[prec]["speedup_over_plain_fp32_gpu"] = plain["ms_per_step"] / out[prec]["ms_per_step"]
     for prec in ("tc_fp16", "tc_bf16"):
         out[prec]["speedup_over_fp32_clusters"] = out["fp32"]["ms_per_step"] / out[prec]["ms_per_step"]
@@ -806,7 +812,8 @@ def main(argv=None):
     ap.add_argument("--pad", default=None, choices=["pow2", "smooth"],
                     help="padding policy: the paper's 2,3,5,7-smooth length (default for the fused "
                          "workload) or the next power of two (default for the precision workload, "
-                         "whose 122880 samples exceed the smooth lengths built)")
+                         "whose tensor-core forms need a power of two; its 122880 samples are "
+                         "themselves smooth)")
     ap.add_argument("--channels", type=int, default=0,
                     help="override the workload's channel count (small profiling captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc_fp16", "tc_bf16"],
@@ -1032,7 +1039,11 @@ def run_plan_workload(args, name):
     if N & (N - 1):
         pair = tuple(info.inlined_pair)
         rad = "x".join(str(r) for r in info.radices if r)
-        if info.fixed_kernel:
+        if info.cluster > 1:
+            kname = (f"cl_mr::scale_block_kernel<{info.cluster}, "
+                     f"{'fixed' if info.fixed_kernel else 'generic'}> (cluster of {info.cluster} CTAs; "
+                     f"N = {N} = {info.cluster} x {N // info.cluster}, local passes {rad})")
+        elif info.fixed_kernel:
             kname = f"mr_fixed_scale_block_kernel (compiled for N = {N} = {rad})"
         elif pair[0]:
             kname = f"mr_scale_block_kernel<{pair[0]}, {pair[1]}> (inlined radix pair; N = {N} = {rad})"

@@ -81,11 +81,15 @@ typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
  * power of two (the choice the paper attributes to MNE-python), up to 131072.
  * SMOOTH is the paper's own policy: the smallest length >= max(samples, 32)
  * whose prime factors are 2, 3, 5 and 7.  Smooth lengths that are not powers
- * of two run on the mixed-radix kernels and are limited to 16384 points;
- * the 15 smooth lengths 14175 ... 16200 that no radix schedule of at most 32
- * values per thread and 512 threads per row covers are passed over (SMOOTH
- * then gives the next smooth length, and an explicit fft_length of one of
- * them is CWT_EUNSUPPORTED).
+ * of two run on the mixed-radix kernels: one CTA per row where a radix
+ * schedule of at most 32 values per thread and 512 threads covers N (every
+ * smooth N <= 16384 but 15 in 14175 ... 16200), else a row of N = CL NL
+ * points on a thread-block cluster of CL CTAs, CL the smallest of 2 ... 8
+ * that divides N with NL <= 16384 a scheduled length (up to N = 131072).
+ * The 43 smooth lengths with neither (3^10 = 59049, 5^7 = 78125, and 41
+ * from 84375 up, where every split leaves NL > 16384 or unscheduled) are
+ * passed over: SMOOTH then gives the next one, and an explicit fft_length
+ * of such a length is CWT_EUNSUPPORTED.
  * cwt_execute_batch does not take mixed-radix plans (CWT_EUNSUPPORTED). */
 typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
 
@@ -161,7 +165,7 @@ typedef struct {
     int pad_policy; /* cwt_pad_policy (default CWT_PAD_POW2) */
     int fft_length; /* 0: from pad_policy; else an explicit N >= samples that is a
                        power of two the build supports or a 2,3,5,7-smooth
-                       length <= 16384 (see cwt_pad_policy) */
+                       length the mixed-radix kernels run (see cwt_pad_policy) */
     int io_dtype;   /* cwt_dtype of the signal and of every output (default F32);
                        F64 is converted to FP32 on load and back on store */
     int edge_mode;  /* cwt_edge_mode (default CWT_EDGE_CYCLIC) */
@@ -190,9 +194,14 @@ typedef struct {
                                it, or 0, 0 for the generic mixed-radix kernel */
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
                                compiled for exactly this N and radix schedule (10000,
-                               8000, 5000, 4000, 2500, 2000, 1000, 500),
+                               8000, 5000, 4000, 2500, 2000, 1000, 500; on a cluster,
+                               a local length of 15360, e.g. N = 122880),
                                else 0; the forward FFTs then run on the same schedule */
     int precision;          /* cwt_precision of the inverse FFTs */
+    int cluster;            /* CTAs that share each inverse FFT (a thread-block cluster
+                               over distributed shared memory): 1 up to 16384 points,
+                               else 2, 4 or 8, each CTA holding inverse_length / cluster
+                               points; radices then describe those points' passes */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */
@@ -207,8 +216,8 @@ cwt_status cwt_options_init(cwt_options *opt);
  * smallest 2,3,5,7-smooth length >= max(samples, 32) that the mixed-radix
  * kernels run (see cwt_pad_policy).  Writes *n_fft.  CWT_EINVAL if samples < 1
  * or the policy is unknown; CWT_EUNSUPPORTED if N exceeds the largest
- * supported length (POW2: 2^17, lengths above 2^14 running each row on a
- * thread-block cluster; SMOOTH: 2^14).  Host-only; no CUDA call. */
+ * supported length, 2^17 under both policies (lengths above 2^14 run each row
+ * on a thread-block cluster).  Host-only; no CUDA call. */
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 
 /* The schedule the mixed-radix kernels run for a 2,3,5,7-smooth length n_fft

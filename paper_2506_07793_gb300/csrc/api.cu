@@ -123,6 +123,7 @@ void free_plan_memory(cwt_plan_s *p) {
     cudaFree(p->spec);
     cudaFree(p->tc_chmax);
     cudaFree(p->tc_wl1);
+    if (p->twL != p->twN) cudaFree(p->twL);
     cudaFree(p->twN);
     cudaFree(p->stage_in);
     cudaFree(p->stage_c);
@@ -162,8 +163,8 @@ const char *cwt_status_str(cwt_status s) {
 static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24 &&
                   offsetof(cwt_options, normalization) == 32,
               "cwt_options layout");
-static_assert(sizeof(cwt_plan_info_t) == 112 && offsetof(cwt_plan_info_t, radices) == 64 &&
-                  offsetof(cwt_plan_info_t, fixed_kernel) == 104,
+static_assert(sizeof(cwt_plan_info_t) == 120 && offsetof(cwt_plan_info_t, radices) == 64 &&
+                  offsetof(cwt_plan_info_t, fixed_kernel) == 104 && offsetof(cwt_plan_info_t, cluster) == 112,
               "cwt_plan_info_t layout");
 
 cwt_status cwt_options_init(cwt_options *opt) {
@@ -182,15 +183,18 @@ cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft) {
     if (!n_fft || samples < 1) return CWT_EINVAL;
     if (pad_policy == CWT_PAD_SMOOTH) {
         // smallest 2,3,5,7-smooth length >= max(samples, 32) that the kernels
-        // run: 15 smooth lengths in [14175, 16200] that no radix schedule of
-        // one CTA covers are passed over
-        for (int m = samples < cwtk::kMinFft ? cwtk::kMinFft : samples; m <= cwtk::kMaxFft; ++m) {
+        // run: one CTA per row, else a cluster split N = CL NL (passed over:
+        // the 43 lengths with neither, e.g. 5^7)
+        for (int m = samples < cwtk::kMinFft ? cwtk::kMinFft : samples; m <= cwtk::kMaxClusterFft; ++m) {
             int x = m;
             for (int f : {2, 3, 5, 7})
                 while (x % f == 0) x /= f;
             if (x != 1) continue;
             cwtk::MrSchedule sch;
-            if (!is_pow2(m) && !cwtk::mr_schedule(m, &sch)) continue;
+            int cl = 1;
+            if (!is_pow2(m) && !(m <= cwtk::kMaxFft && cwtk::mr_schedule(m, &sch)) &&
+                !cwtk::mr_cluster_split(m, &cl, &sch))
+                continue;
             *n_fft = m;
             return CWT_OK;
         }
@@ -249,7 +253,10 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             for (int f : {2, 3, 5, 7})
                 while (x % f == 0) x /= f;
             if (x != 1) return CWT_EINVAL;  // not 2,3,5,7-smooth
-            if (!cwtk::mr_schedule(o.fft_length, &sch)) return CWT_EUNSUPPORTED;
+            int cl = 1;
+            if (!(o.fft_length <= cwtk::kMaxFft && cwtk::mr_schedule(o.fft_length, &sch)) &&
+                !cwtk::mr_cluster_split(o.fft_length, &cl, &sch))
+                return CWT_EUNSUPPORTED;
         }
         if (o.fft_length > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
         N = o.fft_length;
@@ -271,7 +278,10 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->N = N;
     p->d = o.decimation;
     p->mr = !is_pow2(N);
-    if (p->mr) cwtk::mr_schedule(N, &p->sch);
+    if (p->mr) {
+        // one CTA per row where a schedule covers N, else a cluster (checked above)
+        if (!(N <= cwtk::kMaxFft && cwtk::mr_schedule(N, &p->sch))) cwtk::mr_cluster_split(N, &p->cl, &p->sch);
+    }
     p->precision = o.precision;
     int f = 1;  // no spectral fold on the cluster and tensor-core paths
     while (!p->mr && !tc && (p->d % (2 * f)) == 0 && N / (2 * f) >= cwtk::kMinFft) f *= 2;
@@ -305,6 +315,13 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         e = cwtk::dmalloc(&p->twN, sizeof(float2) * (size_t)N);
         if (e == cudaSuccess) e = cwtk::make_twiddles_n(N, p->twN, st);
         p->bytes += sizeof(float2) * (size_t)N;
+        p->twL = p->twN;
+        if (e == cudaSuccess && p->cl > 1) {
+            const int NL = N / p->cl;
+            e = cwtk::dmalloc(&p->twL, sizeof(float2) * (size_t)NL);
+            if (e == cudaSuccess) e = cwtk::make_twiddles_n(NL, p->twL, st);
+            p->bytes += sizeof(float2) * (size_t)NL;
+        }
     }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
     if (e == cudaSuccess && tc) {
@@ -340,8 +357,14 @@ namespace {
 
 // radices[8] (0-terminated), the inlined pair (0, 0: generic) and the
 // fixed-kernel flag of a mixed-radix schedule; radices and pair pre-zeroed.
-void describe_schedule(const cwtk::MrSchedule &sch, int *radices, int *pair, int *fixed) {
+// As the local row of a cluster (cl > 1) the schedule runs on the cluster
+// kernels: no inlined pair, fixed when its local length is compiled in.
+void describe_schedule(const cwtk::MrSchedule &sch, int cl, int *radices, int *pair, int *fixed) {
     for (int q = 0; q < sch.np && q < 7; ++q) radices[q] = sch.p[q].R;
+    if (cl > 1) {
+        *fixed = sch.fixed_cl >= 0;
+        return;
+    }
 #define CWT_MR_CASE(I, A, B) \
     if (sch.fast == I) pair[0] = A, pair[1] = B;
     CWT_MR_FAST_PAIRS(CWT_MR_CASE)
@@ -368,7 +391,8 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->workspace_bytes = p->bytes + p->stage_bytes;
     info->bank_ms = p->bank_ms;
     info->precision = p->precision;
-    if (p->mr) describe_schedule(p->sch, info->radices, info->inlined_pair, &info->fixed_kernel);
+    info->cluster = p->mr ? p->cl : (p->M > cwtk::kMaxFft ? p->M / cwtk::kMaxFft : 1);
+    if (p->mr) describe_schedule(p->sch, p->cl, info->radices, info->inlined_pair, &info->fixed_kernel);
     return CWT_OK;
 }
 
@@ -379,7 +403,7 @@ cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlin
     if (is_pow2(n_fft) || !cwtk::mr_schedule(n_fft, &sch)) return CWT_EUNSUPPORTED;
     for (int q = 0; q < 8; ++q) radices[q] = 0;
     inlined_pair[0] = inlined_pair[1] = 0;
-    describe_schedule(sch, radices, inlined_pair, fixed_kernel);
+    describe_schedule(sch, 1, radices, inlined_pair, fixed_kernel);
     *threads = sch.T;
     return CWT_OK;
 }

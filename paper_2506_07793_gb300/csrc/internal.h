@@ -76,8 +76,10 @@ struct cwt_plan_s {
     std::vector<double> freqs, cycles;
 
     bool mr = false;            // smooth (non power-of-two) N: mixed-radix kernels
-    cwtk::MrSchedule sch{};     // their pass schedule
+    cwtk::MrSchedule sch{};     // their pass schedule (of N / cl points)
+    int cl = 1;                 // smooth N above 16384: CTAs per row (a cluster), N = cl * sch.N
     float2 *twN = nullptr;      // exp(2 pi i m / N), m < N (mixed-radix plans only)
+    float2 *twL = nullptr;      // cl > 1: exp(2 pi i m / NL), m < NL = N / cl
     float *bank = nullptr;    // [S][N] W_s[k] / N (real)
     int *band = nullptr;      // [S][2]: start, length
     float2 *spec = nullptr;   // [C][N] forward spectra (workspace)
@@ -207,6 +209,11 @@ cudaError_t launch_fft_cluster(const float2 *in, float2 *out, int log2n, int bat
 bool mr_schedule(int N, MrSchedule *out);
 cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st);
 cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+// Smooth lengths above 16384 on clusters (smooth_cluster.cu).
+bool mr_cluster_split(int N, int *cl, MrSchedule *sch);
+cudaError_t launch_forward_mr_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+cudaError_t launch_scale_block_mr_cluster(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
+                                          cudaStream_t st);
 cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
                                   cudaStream_t st);
 cudaError_t batch_execute(cwt_plan_s *p, const cwt_epoch *epochs, int n_epochs, const float *in,

@@ -57,6 +57,7 @@ struct MrSchedule {
     int np;          // passes
     int fast;        // index of the inlined radix pair that runs it, or -1 (generic)
     int fixed;       // index of the fixed-length kernel that runs it, or -1
+    int fixed_cl;    // as the local row of a cluster: index of its fixed-length kernel, or -1
     unsigned mag0;   // ceil(2^32 / (N / R_0)), for the sparse first pass
     MrPass p[kMrMaxPasses];
 };

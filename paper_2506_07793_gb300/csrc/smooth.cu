@@ -193,6 +193,7 @@ bool mr_schedule(int N, MrSchedule *out) {
     }
     s.mag0 = mr_magic(N / s.p[0].R);
     s.fixed = mr_fixed_index(s);
+    s.fixed_cl = -1;  // set by mr_cluster_split
     *out = s;
     return true;
 }
@@ -204,6 +205,7 @@ cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st) {
 
 cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
                                   cudaStream_t st) {
+    if (p->cl > 1) return launch_scale_block_mr_cluster(p, out_c, out_p, out_ph, st);
     MrArgs a;
     a.spec = p->spec;
     a.bank = p->bank;

@@ -1,0 +1,73 @@
+// smooth_cluster_fixed.cu -- the cluster kernels of smooth_cluster.cuh for the
+// local lengths whose schedule is compiled in (CWT_CL_MR_FIXED), and the host
+// check that the scheduler's schedule for NL is exactly that one.
+#include "smooth_cluster.cuh"
+
+namespace cwtk {
+
+namespace {
+
+template <class FX>
+bool same_schedule(const MrSchedule &s) {
+    if (s.N != FX::N || s.T != FX::T || s.np != FX::NP || s.mag0 != FX::mag0) return false;
+    for (int q = 0; q < FX::NP; ++q) {
+        const MrPass f = FX::pass(q);
+        const MrPass &h = s.p[q];
+        if (h.R != f.R || h.G != f.G || h.Ns != f.Ns || h.mag != f.mag || h.tws != f.tws) return false;
+    }
+    return true;
+}
+
+template <class FX>
+cudaError_t sb_any_cl(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+    switch (p->cl) {
+#define CWT_CL_CASE(CL) \
+    case CL: return cl_mr::sb_launch<CL, FX>(p, a, st);
+        CWT_CL_SIZES(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class FX>
+cudaError_t fwd_any_cl(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    switch (p->cl) {
+#define CWT_CL_CASE(CL) \
+    case CL: return cl_mr::fwd_launch<CL, FX>(p, signal, st);
+        CWT_CL_SIZES(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int cl_mr_fixed_index(const MrSchedule &s) {
+#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
+    if (same_schedule<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(s)) return I;
+    CWT_CL_MR_FIXED(CWT_CL_CASE)
+#undef CWT_CL_CASE
+    return -1;
+}
+
+cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+    switch (p->sch.fixed_cl) {
+#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
+    case I: return sb_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, a, st);
+        CWT_CL_MR_FIXED(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t cl_mr_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    switch (p->sch.fixed_cl) {
+#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
+    case I: return fwd_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, signal, st);
+        CWT_CL_MR_FIXED(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cwtk

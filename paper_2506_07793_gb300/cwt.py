@@ -50,7 +50,8 @@ class cwt_plan_info_t(ctypes.Structure):
                 ("io_dtype", ctypes.c_int), ("output_kinds", ctypes.c_uint),
                 ("workspace_bytes", ctypes.c_size_t), ("bank_ms", ctypes.c_double),
                 ("radices", ctypes.c_int * 8), ("inlined_pair", ctypes.c_int * 2),
-                ("fixed_kernel", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("fixed_kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cluster", ctypes.c_int)]
 
 
 class cwt_epoch(ctypes.Structure):

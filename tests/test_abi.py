@@ -71,15 +71,59 @@ def test_pow2_padding(lib, n, N):
 
 
 @pytest.mark.parametrize("n,N", [(1, 32), (97, 98), (122, 125), (500, 500), (3001, 3024),
-                                 (10000, 10000), (14000, 14000), (14401, 15000), (15000, 15000),
-                                 (15100, 15360), (16001, 16384), (16383, 16384)])
+                                 (10000, 10000), (14000, 14000), (14401, 14406), (15000, 15000),
+                                 (15100, 15120), (16001, 16128), (16383, 16384), (16385, 16464),
+                                 (19683, 19683), (20000, 20000), (50000, 50000), (59000, 59535),
+                                 (59049, 59535), (78125, 78400), (122880, 122880), (128000, 131072),
+                                 (131072, 131072)])
 def test_smooth_padding(lib, n, N):
     """Section "Fast Fourier transform": the smallest 2,3,5,7-smooth length >= n
-    among those the mixed-radix kernels schedule.  14406 = 2 3 7^4 and
-    15120 = 2^4 3^3 5 7 are smooth but have no schedule of at most 32 values
-    per thread and 512 threads per row, so 14401 pads to 15000 and 15100 to
-    15360 (the 15 such lengths in [14175, 16200] are passed over)."""
+    that the kernels run.  14406 = 2 3 7^4 and 15120 = 2^4 3^3 5 7 have no
+    one-CTA schedule (at most 32 values per thread, 512 threads) but split as
+    2 x 7203 and 2 x 7560 over a cluster; 16128 = 2^8 3^2 7 likewise; 16464
+    = 2 x 8232 is the first smooth length past 16384; 19683 = 3 x 6561 runs
+    on a cluster of 3.  3^10 = 59049 has no split with NL <= 16384 (3 is its
+    only factor), so 59000 and 59049 pad to 59535 = 5 x 11907; 5^7 = 78125
+    splits only as 5 x 15625, unscheduled, and pads to 78400 = 2^6 5^2 7^2;
+    122880 = 8 x 15360 needs no padding; 128000 = 8 x 16000 and
+    129024 = 8 x 16128 split only into unscheduled NL, so 128000 pads to 2^17."""
     assert lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) == N
+
+
+def _smooth(m):
+    for f in (2, 3, 5, 7):
+        while m % f == 0:
+            m //= f
+    return m == 1
+
+
+def _one_cta(lib, m):
+    try:
+        lib.cwt_smooth_schedule(m)
+        return True
+    except lib.CWTError as e:
+        assert e.status == lib.CWT_EUNSUPPORTED
+        return False
+
+
+def test_smooth_cluster_split_rule(lib):
+    """Every smooth length in [32, 2^17] that is not a power of two is kept by
+    the SMOOTH policy exactly when the one-CTA scheduler covers it (N <= 16384)
+    or some CL in 2 ... 8 divides it with N / CL <= 16384 a length that
+    scheduler covers."""
+    passed_over = []
+    for m in range(32, 131073):
+        if not _smooth(m) or (m & (m - 1)) == 0:
+            continue
+        ok = m <= 16384 and _one_cta(lib, m)
+        for cl in range(2, 9):
+            if ok:
+                break
+            ok = m % cl == 0 and m // cl <= 16384 and _one_cta(lib, m // cl)
+        assert (lib.cwt_fft_length(m, lib.CWT_PAD_SMOOTH) == m) == ok, m
+        if not ok:
+            passed_over.append(m)
+    assert len(passed_over) == 43 and passed_over[:3] == [59049, 78125, 84375]
 
 
 def test_padding_limits(lib):
@@ -90,7 +134,7 @@ def test_padding_limits(lib):
         lib.cwt_fft_length(131073)
     assert e.value.status == lib.CWT_EUNSUPPORTED
     with pytest.raises(lib.CWTError) as e:
-        lib.cwt_fft_length(16385, lib.CWT_PAD_SMOOTH)  # smooth lengths above 16384 are not built
+        lib.cwt_fft_length(131073, lib.CWT_PAD_SMOOTH)
     assert e.value.status == lib.CWT_EUNSUPPORTED
 
 
@@ -142,8 +186,8 @@ def test_option_struct_layout(lib):
     assert o.gmw_gamma == 3.0 and o.decimation == 1
     assert type(o).edge_mode.offset == 20 and o.edge_mode == lib.CWT_EDGE_CYCLIC
     assert type(o).normalization.offset == 32 and o.normalization == lib.CWT_NORM_UNIT_ENERGY
-    assert ctypes.sizeof(lib.cwt_plan_info_t) == 112 and lib.cwt_plan_info_t.radices.offset == 64
-    assert lib.cwt_plan_info_t.fixed_kernel.offset == 104
+    assert ctypes.sizeof(lib.cwt_plan_info_t) == 120 and lib.cwt_plan_info_t.radices.offset == 64
+    assert lib.cwt_plan_info_t.fixed_kernel.offset == 104 and lib.cwt_plan_info_t.cluster.offset == 112
     so = lib.cwt_server_options_init()
     assert ctypes.sizeof(so) == 56 and type(so).gmw_gamma.offset == 32
     assert so.gmw_gamma == 3.0 and so.max_streams == 32
@@ -161,16 +205,26 @@ def test_linear_edges_unsupported_for_gmw_and_too_long(lib):
     assert e.value.status == lib.CWT_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long"])
+@pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long", "odd_smooth", "unsplit_smooth",
+                                  "tc_smooth"])
 def test_unsupported_requests(lib, what):
     """The tensor-core inverse FFTs cover power-of-two N of 16384 .. 131072
-    only (here N = 128); 140000 samples exceed the longest padding."""
+    only (here N = 128, then the smooth 20000); 140000 samples exceed the
+    longest padding; an explicit smooth fft_length with no cluster split
+    (5^7 = 78125 splits only as 5 x 15625; 128000 = 8 x 16000, both NL
+    unscheduled) is refused."""
     o = lib.cwt_options_init()
     wavelet, samples = 0, 100
     if what == "tc_fp16":
         o.precision = lib.CWT_PREC_TC_FP16
     elif what == "tc_bf16":
         o.precision = lib.CWT_PREC_TC_BF16
+    elif what == "odd_smooth":
+        o.fft_length = 78125
+    elif what == "unsplit_smooth":
+        o.fft_length = 128000
+    elif what == "tc_smooth":
+        o.precision, o.fft_length = lib.CWT_PREC_TC_FP16, 20000
     else:
         samples = 140000
     with pytest.raises(lib.CWTError) as e:

@@ -378,6 +378,53 @@ def test_fused_workload_smooth_padding_sampled_rows(lib):
     check({k: np.stack([v[c, s] for c, s in rows]) for k, v in res.items()}, ref)
 
 
+SMOOTH_CLUSTER = [
+    # (C, n, fs, freqs, cycles, kwargs, N, CL): smooth N above 16384, one
+    # thread-block cluster of CL CTAs per row, NL = N / CL points each.
+    # Narrow bands (a low carrier with many cycles) take the sparse first
+    # pass, wide ones the dense pass.
+    (1, 16400, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], {}, 16464, 2),
+    (2, 20000, 2000.0, [0.5, 50.0, 900.0], [3.0, 7.0, 12.0], dict(dtype="f64"), 20000, 2),
+    (1, 50000, 1000.0, [1.0, 100.0, 450.0], [20.0, 7.0, 4.0], dict(decimation=4), 50000, 4),
+    (1, 100000, 4000.0, [0.3, 60.0, 1900.0], [7.0, 7.0, 10.0], dict(decimation=8), 100000, 8),
+    (1, 122880, 2048.0, [0.5, 13.0, 200.0], [7.0, 7.0, 7.0], dict(decimation=8), 122880, 8),
+    # smooth lengths of at most 16384 that no one-CTA schedule covers, odd
+    # cluster sizes, and the compiled-in local length 15360 on 6 and 7 CTAs
+    (1, 14175, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], {}, 14175, 3),
+    (2, 14406, 500.0, [1.0, 30.0, 200.0], [3.0, 7.0, 12.0], dict(dtype="f64"), 14406, 2),
+    (1, 15625, 1000.0, [0.7, 80.0, 450.0], [7.0, 7.0, 7.0], dict(decimation=2), 15625, 5),
+    (1, 19683, 2000.0, [1.5, 100.0, 800.0], [7.0, 7.0, 7.0], {}, 19683, 3),
+    (1, 92160, 4096.0, [0.5, 50.0, 1800.0], [7.0, 7.0, 7.0], dict(decimation=16), 92160, 6),
+    (1, 107520, 4096.0, [0.4, 120.0, 2000.0], [7.0, 7.0, 12.0], dict(decimation=16), 107520, 7),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SMOOTH_CLUSTER)))
+def test_smooth_cluster_every_row(lib, case):
+    """Smooth lengths one CTA does not run (Section "Fast Fourier transform"):
+    the row of N = CL NL points runs on a cluster, each CTA a residue class
+    through the NL-point mixed-radix passes, then one radix-CL stage across
+    the cluster; parity with the oracle at the same N for every output kind."""
+    import torch
+    C, n, fs, freqs, cycles, kw, N_want, CL = SMOOTH_CLUSTER[case]
+    kw = dict(kw)
+    dtype = kw.pop("dtype", "f32")
+    d = kw.get("decimation", 1)
+    x = eeg(1100 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    t = lib.CWT(C, n, fs, freqs, cycles, outputs=("complex", "power", "phase"), dtype=dtype,
+                pad="smooth", **kw)
+    info = t.info
+    assert info.fft_length == N_want and info.cluster == CL
+    rad = [r for r in info.radices if r]
+    assert int(np.prod(rad)) == N_want // CL
+    out = t(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    t.close()
+    ref = oracle.cwt(x.astype(np.float64), N_want, fs, freqs, cycles, decimation=d)
+    check(res, ref)
+
+
 GMW = [
     # (C, n, fs, freqs, betas, gamma, kwargs)
     (2, 500, 500.0, [4.0, 40.0, 200.0], [20.0, 20.0, 20.0], 3.0, {}),
