@@ -179,11 +179,48 @@ __host__ __device__ constexpr int first_factor(int r) { return (r & 1) == 0 ? lo
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_r(float2 *v);
 
-template <int R, int SIGN>
-__device__ __forceinline__ void dft_composite(float2 *v) {
-    constexpr int R1 = first_factor(R), R2 = R / R1;
-    // n = R2 n1 + n2, k = k1 + R1 k2:
-    //   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 x[R2 n1 + n2] w_R1^(n1 k1)
+__host__ __device__ constexpr int ct_gcd(int a, int b) { return b == 0 ? a : ct_gcd(b, a % b); }
+// x with a x = 1 (mod m), for gcd(a, m) = 1 and m >= 2.
+__host__ __device__ constexpr int ct_inv_mod(int a, int m) {
+    int x = 1;
+    while ((a * x) % m != 1) ++x;
+    return x;
+}
+
+// R = R1 R2 with gcd(R1, R2) = 1: the prime-factor (Good-Thomas) algorithm,
+// no twiddles between the two stages.  Input index n = (R2 n1 + R1 n2) mod R
+// and output index k with k = k1 (mod R1), k = k2 (mod R2), i.e.
+// k = (k1 R2 u2 + k2 R1 u1) mod R, u2 = R2^-1 mod R1, u1 = R1^-1 mod R2:
+//   w_R^(n k) = w_R1^(n1 k1) w_R2^(n2 k2), so
+//   X[k] = sum_n2 w_R2^(n2 k2) sum_n1 x[(R2 n1 + R1 n2) mod R] w_R1^(n1 k1).
+template <int R, int SIGN, int R1, int R2>
+__device__ __forceinline__ void dft_pfa(float2 *v) {
+    constexpr int u2 = ct_inv_mod(R2 % R1, R1), u1 = ct_inv_mod(R1 % R2, R2);
+    float2 t[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+        float2 a[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[(R2 * n1 + R1 * n2) % R];
+        dft_r<R1, SIGN>(a);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) t[n2 * R1 + k1] = a[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 b[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) b[n2] = t[n2 * R1 + k1];
+        dft_r<R2, SIGN>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[(k1 * R2 * u2 + k2 * R1 * u1) % R] = b[k2];
+    }
+}
+
+// R1, R2 sharing a factor (9, 25, 27): Cooley-Tukey, n = R2 n1 + n2, k = k1 + R1 k2:
+//   X[k1 + R1 k2] = sum_n2 w_R2^(n2 k2) w_R^(n2 k1) sum_n1 x[R2 n1 + n2] w_R1^(n1 k1)
+template <int R, int SIGN, int R1, int R2>
+__device__ __forceinline__ void dft_ct(float2 *v) {
     float2 t[R];
     static_for<R2>([&](auto n2c) {
         constexpr int n2 = decltype(n2c)::value;
@@ -205,6 +242,15 @@ __device__ __forceinline__ void dft_composite(float2 *v) {
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
     }
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_composite(float2 *v) {
+    constexpr int R1 = first_factor(R), R2 = R / R1;
+    if constexpr (ct_gcd(R1, R2) == 1)
+        dft_pfa<R, SIGN, R1, R2>(v);
+    else
+        dft_ct<R, SIGN, R1, R2>(v);
 }
 
 template <int R, int SIGN>

@@ -588,6 +588,26 @@ def test_explicit_smooth_fft_length(lib, N):
     check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
 
 
+# For every radix the scheduler uses, the shortest smooth length whose
+# schedule takes it as the first pass and as a later pass (the host schedule
+# is pinned in test_abi.py; here the kernels run it).
+RADIX_LENGTHS = [40, 35, 13125, 36, 49, 80, 48, 81, 45, 100, 144, 72, 196, 70, 225, 75, 320, 112,
+                 324, 108, 400, 180, 441, 147, 576, 192, 625, 125, 729, 189, 784, 280, 900, 300, 640]
+
+
+@pytest.mark.parametrize("N", RADIX_LENGTHS)
+def test_every_radix_in_every_position(lib, N):
+    """Each mixed-radix DFT (prime, prime-power and coprime composite radices
+    4 ... 32, Section "Fast Fourier transform") in the first and in a later
+    pass, forward and inverse: parity with the oracle at an explicit N."""
+    fs, freqs, cycles = 100.0, [8.0, 30.0], [3.0, 5.0]
+    n = N - 3
+    x = eeg(1400 + N, 1, n, fs, np.float32)
+    res, got_N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), fft_length=N)
+    assert got_N == N
+    check(res, oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles))
+
+
 @pytest.mark.parametrize("pad,edge", [("pow2", "cyclic"), ("smooth", "cyclic"), ("pow2", "linear")])
 def test_mne_normalisation(lib, pad, edge):
     """MNE-python's wavelet normalisation (sum |w|^2 = 2) on every row, against

@@ -189,3 +189,83 @@ def test_cluster_decomposition(CL, NL):
                 owner[t1[span] + NL * t2] = cta
         assert (owner >= 0).all()
         np.testing.assert_allclose(X, ref, rtol=0, atol=1e-9 * N)
+
+
+def _factor_split(R):
+    """The kernels' first factor of a composite radix: its power-of-two part,
+    else its smallest prime."""
+    if R % 2 == 0:
+        return R & -R
+    return 3 if R % 3 == 0 else 5 if R % 5 == 0 else 7
+
+
+@pytest.mark.parametrize("R", [6, 10, 12, 14, 15, 18, 20, 21, 24, 28, 30])
+def test_prime_factor_maps(R):
+    """Composite radices whose two factors are coprime run the prime-factor
+    (Good-Thomas) algorithm without inner twiddles: inputs gathered at
+    (R2 n1 + R1 n2) mod R, an R1-point DFT over n1, an R2-point DFT over n2,
+    output (k1, k2) stored at (k1 R2 u2 + k2 R1 u1) mod R with u2 = R2^-1
+    mod R1 and u1 = R1^-1 mod R2 -- the maps must give the R-point DFT."""
+    R1 = _factor_split(R)
+    R2 = R // R1
+    assert np.gcd(R1, R2) == 1
+    u2, u1 = pow(R2, -1, R1), pow(R1, -1, R2)
+    rng = np.random.default_rng(R)
+    x = rng.standard_normal(R) + 1j * rng.standard_normal(R)
+    for sign in (-1, +1):
+        F1 = np.exp(sign * 2j * np.pi * np.outer(np.arange(R1), np.arange(R1)) / R1)
+        F2 = np.exp(sign * 2j * np.pi * np.outer(np.arange(R2), np.arange(R2)) / R2)
+        g = np.array([[x[(R2 * n1 + R1 * n2) % R] for n1 in range(R1)] for n2 in range(R2)])  # [n2][n1]
+        t = g @ F1.T                     # [n2][k1]
+        y = F2 @ t                       # [k2][k1]
+        X = np.empty(R, dtype=np.complex128)
+        for k1 in range(R1):
+            for k2 in range(R2):
+                X[(k1 * R2 * u2 + k2 * R1 * u1) % R] = y[k2, k1]
+        ref = np.exp(sign * 2j * np.pi * np.outer(np.arange(R), np.arange(R)) / R) @ x
+        np.testing.assert_allclose(X, ref, rtol=0, atol=1e-12 * R)
+
+
+@pytest.mark.parametrize("CL,NL", [(3, 4725), (2, 7203), (5, 3125), (6, 2560), (7, 2240), (8, 15360)])
+def test_smooth_cluster_decomposition(lib, CL, NL):
+    """Smooth rows on clusters (any CL in 2 ... 8): the residue classes run the
+    scheduler's NL-point passes, the cross-CTA radix-CL stage finishes the row;
+    the class's in-band bins are the cyclic run of Bm local points from
+    m_first (delta = (c - b0) mod CL, Bm = ceil((B - delta) / CL)), and with
+    Bm <= NL / R_0 each first-pass butterfly meets at most one of them."""
+    N = CL * NL
+    radices = lib.cwt_smooth_schedule(NL)[0]
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for sign, ref in ((-1, np.fft.fft(x)), (+1, np.fft.ifft(x) * N)):
+        A = np.stack([stockham(x[c::CL], radices, sign) for c in range(CL)])
+        t1 = np.arange(NL)
+        X = np.empty(N, dtype=np.complex128)
+        for cta in range(CL):
+            span = slice(cta * NL // CL, (cta + 1) * NL // CL)
+            for t2 in range(CL):
+                X[t1[span] + NL * t2] = sum(np.exp(sign * 2j * np.pi * c * t2 / CL)
+                                            * np.exp(sign * 2j * np.pi * c * t1[span] / N) * A[c, span]
+                                            for c in range(CL))
+        np.testing.assert_allclose(X, ref, rtol=0, atol=1e-9 * N)
+    nb = NL // radices[0]
+    for _ in range(30):
+        b0 = int(rng.integers(0, N))
+        B = int(rng.integers(1, N // 4))
+        band = np.zeros(N, dtype=bool)
+        band[(b0 + np.arange(B)) % N] = True
+        for c in range(CL):
+            delta = (c - b0) % CL
+            Bm = -(-(B - delta) // CL) if delta < B else 0
+            m_first = ((((b0 + delta) % N) - c) // CL) % NL
+            run = (m_first + np.arange(Bm)) % NL
+            assert sorted(run.tolist()) == np.flatnonzero(band[c::CL]).tolist()
+            if Bm <= nb:
+                for b in range(nb):
+                    hits = [r for r in range(radices[0]) if band[c + CL * (b + r * nb)]]
+                    u = (b - m_first) % nb
+                    if u < Bm:
+                        m = (m_first + u) % NL
+                        assert hits == [(m - b) // nb]
+                    else:
+                        assert hits == []
