@@ -193,9 +193,10 @@ typedef struct {
     int inlined_pair[2];    /* smooth N: the radix pair of the inlined kernel that runs
                                it, or 0, 0 for the generic mixed-radix kernel */
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
-                               compiled for exactly this N and radix schedule (10000,
-                               8000, 5000, 4000, 2500, 2000, 1000, 500; on a cluster,
-                               a local length of 15360, e.g. N = 122880),
+                               compiled for exactly this N and radix schedule (15000,
+                               12000, 10000, 9000, 8000, 7500, 6000, 5000, 4000, 3000,
+                               2500, 2000, 1500, 1000, 500; on a cluster, a local
+                               length of 15360, e.g. N = 122880),
                                else 0; the forward FFTs then run on the same schedule */
     int precision;          /* cwt_precision of the inverse FFTs */
     int cluster;            /* CTAs that share each inverse FFT (a thread-block cluster

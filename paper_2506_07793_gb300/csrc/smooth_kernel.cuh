@@ -212,7 +212,14 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
     X(4, 2500, 125, 2, 3, 10, 10, 25)      \
     X(5, 2000, 100, 2, 4, 10, 10, 20)      \
     X(6, 1000, 50, 5, 4, 10, 10, 10)       \
-    X(7, 500, 25, 10, 3, 20, 25)
+    X(7, 500, 25, 10, 3, 20, 25)           \
+    X(8, 12000, 512, 1, 2, 16, 25, 30)     \
+    X(9, 7500, 384, 1, 2, 12, 25, 25)      \
+    X(10, 6000, 256, 1, 4, 10, 24, 25)     \
+    X(11, 15000, 512, 1, 1, 10, 10, 10, 15) \
+    X(12, 3000, 100, 2, 3, 10, 10, 30)     \
+    X(13, 9000, 384, 1, 2, 10, 30, 30)     \
+    X(14, 1500, 50, 4, 4, 10, 10, 15)
 
 // Index of the fixed-length kernel whose schedule equals s, or -1.
 int mr_fixed_index(const MrSchedule &s);

@@ -262,6 +262,13 @@ FIXED_SCHEDULES = {
     2000: ([10, 10, 20], 100, (10, 20)),
     1000: ([10, 10, 10], 50, (10, 16)),
     500: ([20, 25], 25, (20, 25)),
+    15000: ([10, 10, 10, 15], 512, (0, 0)),
+    12000: ([16, 25, 30], 512, (0, 0)),
+    9000: ([10, 30, 30], 384, (0, 0)),
+    7500: ([12, 25, 25], 384, (0, 0)),
+    6000: ([10, 24, 25], 256, (0, 0)),
+    3000: ([10, 10, 30], 100, (0, 0)),
+    1500: ([10, 10, 15], 50, (0, 0)),
 }
 
 

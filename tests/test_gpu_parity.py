@@ -530,15 +530,22 @@ FIXED = [
     (2000, 5, [3.0, 40.0, 300.0], [4.0, 7.0, 10.0], "f64", 2),                     # odd row count
     (1000, 7, np.geomspace(4.0, 450.0, 3), [5.0, 7.0, 12.0], "f32", 1),            # 5 rows per CTA
     (500, 3, [10.0, 100.0, 400.0, 480.0], [6.0, 7.0, 9.0, 12.0], "f32", 4),         # 10 rows per CTA
+    (15000, 2, np.geomspace(0.5, 450.0, 5), np.linspace(3.0, 12.0, 5), "f32", 1),  # four passes
+    (12000, 2, [0.6, 50.0, 420.0], [3.0, 7.0, 12.0], "f64", 1),
+    (9000, 2, np.geomspace(1.0, 450.0, 4), np.linspace(3.0, 12.0, 4), "f32", 3),
+    (7500, 3, [0.8, 25.0, 330.0], [3.0, 7.0, 10.0], "f32", 1),
+    (6000, 2, [1.5, 70.0, 440.0], [4.0, 7.0, 12.0], "f32", 2),
+    (3000, 5, np.geomspace(2.0, 450.0, 3), [5.0, 7.0, 12.0], "f32", 1),             # 2 rows per CTA
+    (1500, 6, [4.0, 90.0, 470.0], [5.0, 7.0, 9.0], "f64", 1),                      # 4 rows per CTA
 ]
 
 
 @pytest.mark.parametrize("case", range(len(FIXED)))
 def test_fixed_length_kernel_every_row(lib, case):
-    """N = 10000, 8000, 5000, 4000, 2500, 2000, 1000 and 500 run on the
-    kernels compiled for that length and schedule (several rows per CTA below
-    4000, row counts that leave a CTA partly idle); parity with the oracle
-    for every output kind."""
+    """N = 15000, 12000, 10000, 9000, 8000, 7500, 6000, 5000, 4000, 3000,
+    2500, 2000, 1500, 1000 and 500 run on the kernels compiled for that length
+    and schedule (several rows per CTA below 4000, row counts that leave a CTA
+    partly idle); parity with the oracle for every output kind."""
     n, C, freqs, cycles, dtype, d = FIXED[case]
     fs = 1000.0
     x = eeg(1200 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
