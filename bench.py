@@ -138,13 +138,44 @@ def padded_length(n, pad):
         m += 1
 
 
+def host_cores():
+    """Host threads this process may use (the oracle runs one per core)."""
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def host_cpu_model():
+    """The host CPU's model name: lscpu's "Model name", else /proc/cpuinfo's
+    "model name", else its Arm implementer and part codes."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip().lower(), v.strip())
+    if "model name" in fields:
+        return fields["model name"]
+    if "cpu implementer" in fields:
+        return f"Arm implementer {fields['cpu implementer']} part {fields.get('cpu part', '?')}"
+    return "unknown"
+
+
 def cpu_baseline(w, x_rows, n_channels, N, n_scales=None, min_seconds=10.0):
     """The FP64 oracle, as it stands, on the host cores: the first n_scales
     (default all) scales of the first channels of the same workload, at the
     padded length N of the timed plan -- n_channels channels, then one more at a
     time until at least min_seconds of work (at most every channel given)."""
     import oracle
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = host_cores()
     ns = w.scales if n_scales is None else n_scales
     scales = list(range(0, w.scales, max(1, w.scales // ns)))[:ns]
     x64 = x_rows.astype(np.float64)
@@ -157,7 +188,8 @@ def cpu_baseline(w, x_rows, n_channels, N, n_scales=None, min_seconds=10.0):
         dt += time.perf_counter() - t0
         done += take
     coeffs = done * len(scales) * w.n_out
-    return {"value": coeffs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": coeffs / dt, "unit": UNIT, "cores": cores, "cpu_model": host_cpu_model(),
+            "kind": "oracle",
             "sample": f"{done} of {w.channels} channels x {len(scales)} of {w.scales} scales x "
                       f"{w.n_out} samples ({coeffs} coefficients), {dt:.2f} s wall"}
 
@@ -171,7 +203,7 @@ def run_reference(args):
     from eeg_synth import workload
     import oracle
     w = workload(WORKLOAD)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = host_cores()
     N = padded_length(w.samples, args.pad)
     x = w.signal(channels=1).astype(np.float64)
     rows = [(0, s) for s in range(w.scales)]
@@ -190,7 +222,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": w.notes, "channels": w.channels, "samples": w.samples,
                    "scales": w.scales, "fft_length": N, "padding": args.pad, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": host_cpu_model(),
+                         "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -407,7 +440,7 @@ def run_batch(args):
             line["plain_fp32_gpu"] = plain
         if world == 1:
             # the oracle over the first epochs, one at a time until at least 10 s of work
-            cores = len(os.sched_getaffinity(0))
+            cores = host_cores()
             t0 = time.perf_counter()
             done = n_ep = 0
             while n_ep < len(lengths) and (n_ep < 2 or time.perf_counter() - t0 < getattr(args, "cpu_seconds", 10.0)):
@@ -419,7 +452,7 @@ def run_batch(args):
                 n_ep += 1
             dt = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": done / dt, "unit": UNIT, "cores": cores,
-                                    "kind": "oracle",
+                                    "cpu_model": host_cpu_model(), "kind": "oracle",
                                     "sample": f"first {n_ep} of {len(lengths)} epochs x all {C} "
                                               f"channels x all {S} scales ({done} coefficients), "
                                               f"{dt:.2f} s wall"}
@@ -653,7 +686,7 @@ def serving_cpu_baseline(w, blocks, min_seconds=5.0):
     which the H = 50 centred outputs are delivered; hops one after another
     until min_seconds of work."""
     import oracle
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = host_cores()
     fs, C, W, H = 1000.0, 8, 2048, 50
     rec = blocks[fs]
     rows = [(c, s) for c in range(C) for s in range(w.scales)]
@@ -666,7 +699,8 @@ def serving_cpu_baseline(w, blocks, min_seconds=5.0):
         hops += 1
     dt = time.perf_counter() - t0
     delivered = hops * C * w.scales * H
-    return {"value": delivered / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": delivered / dt, "unit": UNIT, "cores": cores, "cpu_model": host_cpu_model(),
+            "kind": "oracle",
             "sample": f"{hops} hops of 8 channels at 1000 Hz x all {w.scales} scales: the "
                       f"2048-sample window's CWT, {H} outputs delivered per row, {dt:.2f} s wall"}
 
