@@ -457,6 +457,7 @@ LINEAR = [
     (2, 1000, 1000.0, np.geomspace(2, 300, 5), np.linspace(3, 10, 5), dict(decimation=3)),
     (1, 3000, 1000.0, [5.0, 90.0], [7.0, 7.0], dict(pad="smooth")),
     (2, 300, 200.0, [9.0, 50.0], [5.0, 7.0], dict(wavelet="gabor", dtype="f64")),
+    (1, 20000, 1000.0, [2.0, 60.0], [5.0, 7.0], dict(pad="smooth")),  # N = 22680 on a cluster of 2
 ]
 
 
