@@ -196,7 +196,8 @@ typedef struct {
                                compiled for exactly this N and radix schedule (15000,
                                12000, 10000, 9000, 8000, 7500, 6000, 5000, 4000, 3000,
                                2500, 2000, 1500, 1000, 500; on a cluster, a local
-                               length of 15360, e.g. N = 122880),
+                               length of 15360, 15000 or 10000, e.g. N = 122880,
+                               60000, 20000),
                                else 0; the forward FFTs then run on the same schedule */
     int precision;          /* cwt_precision of the inverse FFTs */
     int cluster;            /* CTAs that share each inverse FFT (a thread-block cluster

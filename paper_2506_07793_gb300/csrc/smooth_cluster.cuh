@@ -45,16 +45,27 @@ struct ClMrArgs {
 #define CWT_CL_SIZES_WIDE(X) X(5) X(6) X(7) X(8)
 #define CWT_CL_SIZES(X) CWT_CL_SIZES_NARROW(X) CWT_CL_SIZES_WIDE(X)
 
-// Local lengths whose schedule is compiled in (index, NL, T, rows = 1,
-// CTAs per SM = 1, radices): 15360 = 16 x 30 x 32, the local row of the
-// minute at 2048 Hz (122880 = 8 x 15360).
-#define CWT_CL_MR_FIXED(X) X(0, 15360, 512, 1, 1, 16, 30, 32)
+// Local lengths whose schedule is compiled in (index, NL, T, rows = 1, CTAs
+// per SM, radices), each in a translation unit of its own
+// (smooth_cluster_fixed_<index>.cu): 15360 = 16 x 30 x 32, the local row of
+// a minute at 512, 1024 or 2048 Hz (30720, 61440, 122880); 15000 =
+// 10 x 10 x 10 x 15 (30000, 60000, 120000: a minute at 500, 1000, 2000 Hz);
+// 10000 = 16 x 25 x 25 (20000, 40000, 80000), whose 85 KB CTAs fit two per SM.
+#define CWT_CL_MR_FIXED_0(X) X(0, 15360, 512, 1, 1, 16, 30, 32)
+#define CWT_CL_MR_FIXED_1(X) X(1, 15000, 512, 1, 1, 10, 10, 10, 15)
+#define CWT_CL_MR_FIXED_2(X) X(2, 10000, 512, 1, 2, 16, 25, 25)
+#define CWT_CL_MR_FIXED(X) CWT_CL_MR_FIXED_0(X) CWT_CL_MR_FIXED_1(X) CWT_CL_MR_FIXED_2(X)
 
 // Index in CWT_CL_MR_FIXED of the local schedule s, or -1 (smooth_cluster_fixed.cu).
 int cl_mr_fixed_index(const MrSchedule &s);
 // The fixed-length launches (smooth_cluster_fixed.cu).
 cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st);
 cudaError_t cl_mr_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+// Entry I of CWT_CL_MR_FIXED on any cluster size (smooth_cluster_fixed_<I>.cu).
+template <int I>
+cudaError_t cl_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st);
+template <int I>
+cudaError_t cl_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 // The runtime-schedule launches for CWT_CL_SIZES_WIDE (smooth_cluster_wide.cu).
 cudaError_t cl_mr_wide_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st);
 cudaError_t cl_mr_wide_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st);
@@ -136,6 +147,13 @@ __device__ __forceinline__ int local_n(const MrSchedule &sch) {
     else return FX::N;
 }
 
+// CTAs per SM the register budget is set for.
+template <class FX>
+constexpr int min_blocks() {
+    if constexpr (std::is_void_v<FX>) return 1;
+    else return FX::MINB;
+}
+
 template <class FX>
 __device__ __forceinline__ int first_radix(const MrSchedule &sch) {
     if constexpr (std::is_void_v<FX>) return sch.p[0].R;
@@ -167,7 +185,7 @@ __device__ __forceinline__ void cross(const float2 *sm, const float2 *__restrict
 }
 
 template <int CL, class FX>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, 1)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, min_blocks<FX>())
 scale_block_kernel(const ClMrArgs a, const MrSchedule sch) {
     extern __shared__ float2 mrsm[];
     float2 *sm = mrsm;
@@ -211,7 +229,7 @@ scale_block_kernel(const ClMrArgs a, const MrSchedule sch) {
 }
 
 template <int CL, class FX>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, 1)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, min_blocks<FX>())
 forward_kernel(const void *__restrict__ x, int f64, int n, float2 *__restrict__ spec,
                const float2 *__restrict__ twL, const float2 *__restrict__ twN, const MrSchedule sch) {
     extern __shared__ float2 mrsm[];
@@ -252,5 +270,40 @@ cudaError_t fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <class FX>
+cudaError_t sb_any_cl(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+    switch (p->cl) {
+#define CWT_CL_CASE(CL) \
+    case CL: return sb_launch<CL, FX>(p, a, st);
+        CWT_CL_SIZES(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class FX>
+cudaError_t fwd_any_cl(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    switch (p->cl) {
+#define CWT_CL_CASE(CL) \
+    case CL: return fwd_launch<CL, FX>(p, signal, st);
+        CWT_CL_SIZES(CWT_CL_CASE)
+#undef CWT_CL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace cl_mr
+
+// The definitions of cl_fixed_sb<I> / cl_fixed_fwd<I> for one entry of
+// CWT_CL_MR_FIXED (expanded in that entry's translation unit).
+#define CWT_CL_FIXED_DEFINE(I, N, T, ROWS, MINB, ...)                                              \
+    template <>                                                                                    \
+    cudaError_t cl_fixed_sb<I>(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {          \
+        return cl_mr::sb_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, a, st);                 \
+    }                                                                                              \
+    template <>                                                                                    \
+    cudaError_t cl_fixed_fwd<I>(const cwt_plan_s *p, const void *signal, cudaStream_t st) {        \
+        return cl_mr::fwd_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, signal, st);           \
+    }
+
 }  // namespace cwtk

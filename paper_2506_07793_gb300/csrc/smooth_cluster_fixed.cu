@@ -1,6 +1,7 @@
-// smooth_cluster_fixed.cu -- the cluster kernels of smooth_cluster.cuh for the
-// local lengths whose schedule is compiled in (CWT_CL_MR_FIXED), and the host
-// check that the scheduler's schedule for NL is exactly that one.
+// smooth_cluster_fixed.cu -- the dispatch to the cluster kernels of
+// smooth_cluster.cuh for the local lengths whose schedule is compiled in
+// (CWT_CL_MR_FIXED; the kernels themselves are in smooth_cluster_fixed_<I>.cu),
+// and the host check that the scheduler's schedule for NL is exactly that one.
 #include "smooth_cluster.cuh"
 
 namespace cwtk {
@@ -18,28 +19,6 @@ bool same_schedule(const MrSchedule &s) {
     return true;
 }
 
-template <class FX>
-cudaError_t sb_any_cl(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
-    switch (p->cl) {
-#define CWT_CL_CASE(CL) \
-    case CL: return cl_mr::sb_launch<CL, FX>(p, a, st);
-        CWT_CL_SIZES(CWT_CL_CASE)
-#undef CWT_CL_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <class FX>
-cudaError_t fwd_any_cl(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
-    switch (p->cl) {
-#define CWT_CL_CASE(CL) \
-    case CL: return cl_mr::fwd_launch<CL, FX>(p, signal, st);
-        CWT_CL_SIZES(CWT_CL_CASE)
-#undef CWT_CL_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 }  // namespace
 
 int cl_mr_fixed_index(const MrSchedule &s) {
@@ -52,8 +31,8 @@ int cl_mr_fixed_index(const MrSchedule &s) {
 
 cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
     switch (p->sch.fixed_cl) {
-#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
-    case I: return sb_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, a, st);
+#define CWT_CL_CASE(I, ...) \
+    case I: return cl_fixed_sb<I>(p, a, st);
         CWT_CL_MR_FIXED(CWT_CL_CASE)
 #undef CWT_CL_CASE
         default: return cudaErrorInvalidValue;
@@ -62,8 +41,8 @@ cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t 
 
 cudaError_t cl_mr_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
     switch (p->sch.fixed_cl) {
-#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
-    case I: return fwd_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, signal, st);
+#define CWT_CL_CASE(I, ...) \
+    case I: return cl_fixed_fwd<I>(p, signal, st);
         CWT_CL_MR_FIXED(CWT_CL_CASE)
 #undef CWT_CL_CASE
         default: return cudaErrorInvalidValue;

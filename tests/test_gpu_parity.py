@@ -396,7 +396,13 @@ SMOOTH_CLUSTER = [
     (1, 19683, 2000.0, [1.5, 100.0, 800.0], [7.0, 7.0, 7.0], {}, 19683, 3),
     (1, 92160, 4096.0, [0.5, 50.0, 1800.0], [7.0, 7.0, 7.0], dict(decimation=16), 92160, 6),
     (1, 107520, 4096.0, [0.4, 120.0, 2000.0], [7.0, 7.0, 12.0], dict(decimation=16), 107520, 7),
+    # compiled-in local rows of 15000 (a minute at 500 and 1000 Hz)
+    (1, 30000, 500.0, [1.0, 40.0, 240.0], [7.0, 7.0, 12.0], dict(decimation=4), 30000, 2),
+    (1, 60000, 1000.0, [0.6, 80.0, 480.0], [5.0, 7.0, 12.0], dict(decimation=8, dtype="f64"), 60000, 4),
 ]
+
+# local lengths whose schedule is compiled into the cluster kernels
+CLUSTER_FIXED_NL = (15360, 15000, 10000)
 
 
 @pytest.mark.parametrize("case", range(len(SMOOTH_CLUSTER)))
@@ -415,6 +421,7 @@ def test_smooth_cluster_every_row(lib, case):
                 pad="smooth", **kw)
     info = t.info
     assert info.fft_length == N_want and info.cluster == CL
+    assert info.fixed_kernel == (N_want // CL in CLUSTER_FIXED_NL)
     rad = [r for r in info.radices if r]
     assert int(np.prod(rad)) == N_want // CL
     out = t(torch.from_numpy(np.ascontiguousarray(x)).cuda())
