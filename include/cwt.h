@@ -193,9 +193,9 @@ typedef struct {
     int inlined_pair[2];    /* smooth N: the radix pair of the inlined kernel that runs
                                it, or 0, 0 for the generic mixed-radix kernel */
     int fixed_kernel;       /* smooth N: 1 when the scale-block kernel runs from a build
-                               compiled for exactly this N and radix schedule (15000,
-                               12000, 10000, 9000, 8000, 7500, 6000, 5000, 4000, 3000,
-                               2500, 2000, 1500, 1000, 500; on a cluster, a local
+                               compiled for exactly this N and radix schedule (27
+                               whole-second EEG lengths from 500 to 15000, e.g. 10000,
+                               12000, 7500, 3000, 1250; on a cluster, a local
                                length of 15360, 15000 or 10000, e.g. N = 122880,
                                60000, 20000),
                                else 0; the forward FFTs then run on the same schedule */

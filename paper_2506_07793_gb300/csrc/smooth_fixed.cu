@@ -1,7 +1,8 @@
-// smooth_fixed.cu -- fixed-length scale-block kernels (smooth_kernel.cuh,
-// CWT_MR_FIXED): the row lengths whose whole schedule is compiled in, and the
+// smooth_fixed.cu -- fixed-length scale-block and forward kernels (smooth_kernel.cuh,
+// CWT_MR_FIXED): the row lengths whose whole schedule is compiled in (list A
+// here, list B in smooth_fixed_b.cu), the dispatch over both lists, and the
 // host check that the scheduler's schedule for N is exactly that one.
-#include "smooth_kernel.cuh"
+#include "smooth_fixed.cuh"
 
 namespace cwtk {
 
@@ -18,37 +19,14 @@ bool same_schedule(const MrSchedule &s) {
     return true;
 }
 
-template <class FX>
-cudaError_t fixed_launch(const MrArgs &a, cudaStream_t st) {
-    static_assert(FX::N <= kMaxFft, "one shared-memory row");
-    static std::atomic<unsigned> done{0};
-    constexpr int smem = FX::ROWS * (FX::N + (FX::N >> 4)) * 8;
-    static_assert(smem <= kMrMaxSmem, "shared memory of one CTA");
-    cudaError_t e = ensure_smem_attr(mr_fixed_scale_block_kernel<FX>, smem, &done);
-    if (e != cudaSuccess) return e;
-    const int grid = (a.total_rows + FX::ROWS - 1) / FX::ROWS;
-    mr_fixed_scale_block_kernel<FX><<<grid, FX::THREADS, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <class FX>
-cudaError_t fixed_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
-    static std::atomic<unsigned> done{0};
-    constexpr int smem = FX::ROWS * (FX::N + (FX::N >> 4)) * 8;
-    cudaError_t e = ensure_smem_attr(mr_fixed_forward_kernel<FX>, smem, &done);
-    if (e != cudaSuccess) return e;
-    const int grid = (p->C + FX::ROWS - 1) / FX::ROWS;
-    mr_fixed_forward_kernel<FX><<<grid, FX::THREADS, smem, st>>>(signal, p->io == CWT_DTYPE_F64, p->n,
-                                                                 p->spec, p->twN, p->C);
-    return cudaGetLastError();
-}
-
 }  // namespace
+
+CWT_MR_FIXED_A(CWT_MR_FIXED_DEFINE)
 
 cudaError_t mr_fixed_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
     switch (p->sch.fixed) {
-#define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \
-    case I: return fixed_fwd_launch<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, signal, st);
+#define CWT_MR_CASE(I, ...) \
+    case I: return mr_fixed_fwd<I>(p, signal, st);
         CWT_MR_FIXED(CWT_MR_CASE)
 #undef CWT_MR_CASE
         default: return cudaErrorInvalidValue;
@@ -65,8 +43,8 @@ int mr_fixed_index(const MrSchedule &s) {
 
 cudaError_t mr_fixed_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
     switch (p->sch.fixed) {
-#define CWT_MR_CASE(I, N, T, ROWS, MINB, ...) \
-    case I: return fixed_launch<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(a, st);
+#define CWT_MR_CASE(I, ...) \
+    case I: return mr_fixed_sb<I>(p, a, st);
         CWT_MR_FIXED(CWT_MR_CASE)
 #undef CWT_MR_CASE
         default: return cudaErrorInvalidValue;

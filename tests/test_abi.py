@@ -269,6 +269,18 @@ FIXED_SCHEDULES = {
     6000: ([10, 24, 25], 256, (0, 0)),
     3000: ([10, 10, 30], 100, (0, 0)),
     1500: ([10, 10, 15], 50, (0, 0)),
+    14000: ([10, 10, 10, 14], 512, (0, 0)),
+    13500: ([15, 30, 30], 512, (0, 0)),
+    12500: ([5, 10, 10, 25], 512, (0, 0)),
+    10500: ([15, 25, 28], 512, (0, 0)),
+    7000: ([10, 25, 28], 384, (0, 0)),
+    4500: ([10, 15, 30], 256, (0, 0)),
+    3750: ([6, 25, 25], 256, (0, 0)),
+    3500: ([5, 25, 28], 256, (0, 0)),
+    2250: ([10, 15, 15], 75, (0, 0)),
+    1750: ([5, 14, 25], 70, (0, 0)),
+    1250: ([5, 10, 25], 50, (0, 0)),
+    750: ([25, 30], 30, (0, 0)),
 }
 
 

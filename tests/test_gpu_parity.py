@@ -545,15 +545,27 @@ FIXED = [
     (6000, 2, [1.5, 70.0, 440.0], [4.0, 7.0, 12.0], "f32", 2),
     (3000, 5, np.geomspace(2.0, 450.0, 3), [5.0, 7.0, 12.0], "f32", 1),             # 2 rows per CTA
     (1500, 6, [4.0, 90.0, 470.0], [5.0, 7.0, 9.0], "f64", 1),                      # 4 rows per CTA
+    (14000, 2, [0.5, 30.0, 400.0], [3.0, 7.0, 12.0], "f32", 1),
+    (13500, 1, [0.9, 60.0, 450.0], [4.0, 7.0, 10.0], "f32", 2),
+    (12500, 2, [0.7, 20.0, 300.0], [3.0, 7.0, 12.0], "f64", 1),
+    (10500, 2, [1.2, 45.0, 380.0], [5.0, 7.0, 9.0], "f32", 3),
+    (7000, 3, [0.8, 35.0, 460.0], [3.0, 7.0, 12.0], "f32", 1),
+    (4500, 3, [1.5, 25.0, 330.0], [4.0, 7.0, 10.0], "f32", 1),
+    (3750, 3, [2.0, 50.0, 410.0], [5.0, 7.0, 12.0], "f64", 2),
+    (3500, 3, [1.8, 70.0, 260.0], [4.0, 7.0, 9.0], "f32", 1),
+    (2250, 5, [3.0, 40.0, 350.0], [5.0, 7.0, 10.0], "f32", 1),                     # 2 rows per CTA
+    (1750, 5, [3.5, 80.0, 420.0], [5.0, 7.0, 11.0], "f32", 1),                     # 2 rows per CTA
+    (1250, 7, [4.0, 60.0, 440.0], [5.0, 7.0, 9.0], "f32", 1),                      # 4 rows per CTA
+    (750, 9, [8.0, 100.0, 470.0], [6.0, 7.0, 12.0], "f32", 1),                     # 8 rows per CTA
 ]
 
 
 @pytest.mark.parametrize("case", range(len(FIXED)))
 def test_fixed_length_kernel_every_row(lib, case):
-    """N = 15000, 12000, 10000, 9000, 8000, 7500, 6000, 5000, 4000, 3000,
-    2500, 2000, 1500, 1000 and 500 run on the kernels compiled for that length
-    and schedule (several rows per CTA below 4000, row counts that leave a CTA
-    partly idle); parity with the oracle for every output kind."""
+    """The 27 whole-second lengths 750 ... 15000 run on the kernels compiled
+    for that length and schedule (several rows per CTA below 3500, row counts
+    that leave a CTA partly idle); parity with the oracle for every output
+    kind."""
     n, C, freqs, cycles, dtype, d = FIXED[case]
     fs = 1000.0
     x = eeg(1200 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
