@@ -201,9 +201,10 @@ typedef struct {
                                else 0; the forward FFTs then run on the same schedule */
     int precision;          /* cwt_precision of the inverse FFTs */
     int cluster;            /* CTAs that share each inverse FFT (a thread-block cluster
-                               over distributed shared memory): 1 up to 16384 points,
-                               else 2, 4 or 8, each CTA holding inverse_length / cluster
-                               points; radices then describe those points' passes */
+                               over distributed shared memory): 1 when one CTA holds the
+                               row (at most 16384 points), else 2 ... 8, each CTA holding
+                               inverse_length / cluster points (powers of two: 2, 4, 8);
+                               radices then describe those points' passes */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */

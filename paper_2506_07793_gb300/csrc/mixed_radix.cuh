@@ -1,4 +1,5 @@
-// mixed_radix.cuh -- Stockham FFT for 2,3,5,7-smooth lengths N <= 16384.
+// mixed_radix.cuh -- Stockham FFT for 2,3,5,7-smooth lengths N <= 16384 in one
+// CTA (longer rows run it per residue class on a cluster, smooth_cluster.cuh).
 //
 // Section "Fast Fourier transform" of arXiv 2506.07793 pads each signal to the
 // smallest length whose prime factors are 2, 3, 5 and 7 (the fftpack radices)
