@@ -906,8 +906,11 @@ def run_sweep(args):
     two and to the paper's 2,3,5,7-smooth length.  `device_us` is one
     cwt_execute on resident buffers (CUDA events, mean of --steps calls after
     --warmup); `e2e_us` is cwt_execute_host from pinned host memory, copies
-    included.  Bank generation: 61 scales, 1 s at 2048 Hz (N = 2048), Morlet
-    and the GMW of Fig. 1 (beta 17.5, gamma 3), FP64 on the GPU."""
+    included.  `smooth_specialized` is the smooth padding with
+    cwt_options.specialize (the fixed-length kernels compiled for the length
+    at plan creation; `plan_ms` includes that compile, cached per process).
+    Bank generation: 61 scales, 1 s at 2048 Hz (N = 2048), Morlet and the GMW
+    of Fig. 1 (beta 17.5, gamma 3), FP64 on the GPU."""
     import torch
     import paper_2506_07793_gb300 as cw
     from eeg_synth import eeg
@@ -928,11 +931,14 @@ def run_sweep(args):
         h_in = torch.from_numpy(x_host).pin_memory()
         h_out = torch.empty((C, S, n), dtype=torch.complex64).pin_memory()
         pt = {"samples": n}
-        for pad in ("pow2", "smooth"):
+        for pad in ("pow2", "smooth", "smooth_specialized"):
             o = cw.cwt_options_init()
-            o.pad_policy = cw.CWT_PAD_SMOOTH if pad == "smooth" else cw.CWT_PAD_POW2
+            o.pad_policy = cw.CWT_PAD_POW2 if pad == "pow2" else cw.CWT_PAD_SMOOTH
+            o.specialize = 1 if pad == "smooth_specialized" else 0
+            t_plan = time.perf_counter()
             plan = cw.cwt_plan_create(C, n, fs, freqs, cycles, cw.CWT_WAVELET_MORLET,
                                       cw.CWT_OUT_COMPLEX, o)
+            plan_ms = (time.perf_counter() - t_plan) * 1e3
             info = cw.cwt_plan_info(plan)
             for _ in range(args.warmup):
                 cw.cwt_execute(plan, x, out, None, None, stream)
@@ -953,7 +959,8 @@ def run_sweep(args):
                 cw.cwt_execute_host(plan, h_in, h_out, None, None, stream)
             e2e_us = (time.perf_counter() - t0) / reps * 1e6
             pt[pad] = {"N": info.fft_length, "device_us": dev_us, "e2e_us": e2e_us,
-                       "bank_ms": info.bank_ms}
+                       "bank_ms": info.bank_ms, "plan_ms": plan_ms, "fixed_kernel": info.fixed_kernel,
+                       "specialized": info.specialized}
             cw.cwt_plan_destroy(plan)
         points.append(pt)
     clk = clocks.stop()
@@ -980,7 +987,7 @@ def run_sweep(args):
                                    "Morlet sigma 7, 30-90 Hz by 1 Hz (61 scales), complex64",
                        "l2": "not flushed (every length's working set is below the 129 MB L2)"},
             "points": points, "bank_generation": bank, "clocks": clk,
-            "gpu_launches": 2 * args.steps * 2 * len(points),
+            "gpu_launches": 2 * args.steps * 3 * len(points),
         }), flush=True)
 
 

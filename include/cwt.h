@@ -173,7 +173,14 @@ typedef struct {
                          default 3; read only for CWT_WAVELET_GMW */
     int normalization; /* cwt_normalization of each scale's wavelet (default
                           CWT_NORM_UNIT_ENERGY) */
-    int reserved[7];
+    int specialize;    /* 1: for a smooth N that one CTA holds and that has no
+                          kernel compiled in, compile the fixed-length kernels for
+                          N's schedule at plan creation (NVRTC, about a second,
+                          cached per process; Section "Fast Fourier transform");
+                          if that fails the plan runs the runtime-schedule kernels
+                          (cwt_plan_info.specialized, cwt_plan_last_error).
+                          0 (default): never compile at plan creation */
+    int reserved[6];
 } cwt_options;
 
 typedef struct {
@@ -205,6 +212,8 @@ typedef struct {
                                row (at most 16384 points), else 2 ... 8, each CTA holding
                                inverse_length / cluster points (powers of two: 2, 4, 8);
                                radices then describe those points' passes */
+    int specialized;        /* 1 when the plan runs kernels compiled at its creation
+                               (cwt_options.specialize) */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */
@@ -236,6 +245,15 @@ cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
  * call. */
 cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlined_pair,
                                int *fixed_kernel);
+
+/* The plan-time compile of cwt_options.specialize for the one-CTA schedule of
+ * a smooth n_fft, for sm_103a, without a device (a check that the embedded
+ * kernel source compiles): CWT_OK, CWT_EUNSUPPORTED when n_fft is not a
+ * length the mixed-radix kernels run in one CTA (see cwt_smooth_schedule), or
+ * CWT_ECUDA when the compiler fails; the compiler's log goes to `log` (host
+ * memory of log_len bytes, may be NULL), NUL-terminated.  Host-only; no CUDA
+ * runtime call. */
+cwt_status cwt_specialize_check(int n_fft, char *log, size_t log_len);
 
 /*
  * cwt_plan_create -- validate, pick N, allocate the plan's device memory on

@@ -161,10 +161,11 @@ const char *cwt_status_str(cwt_status s) {
 
 // the Python binding mirrors this layout
 static_assert(sizeof(cwt_options) == 64 && offsetof(cwt_options, gmw_gamma) == 24 &&
-                  offsetof(cwt_options, normalization) == 32,
+                  offsetof(cwt_options, normalization) == 32 && offsetof(cwt_options, specialize) == 36,
               "cwt_options layout");
 static_assert(sizeof(cwt_plan_info_t) == 120 && offsetof(cwt_plan_info_t, radices) == 64 &&
-                  offsetof(cwt_plan_info_t, fixed_kernel) == 104 && offsetof(cwt_plan_info_t, cluster) == 112,
+                  offsetof(cwt_plan_info_t, fixed_kernel) == 104 && offsetof(cwt_plan_info_t, cluster) == 112 &&
+                  offsetof(cwt_plan_info_t, specialized) == 116,
               "cwt_plan_info_t layout");
 
 cwt_status cwt_options_init(cwt_options *opt) {
@@ -232,6 +233,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     if (o.precision != CWT_PREC_FP32 && !tc) return CWT_EINVAL;
     if (o.edge_mode != CWT_EDGE_CYCLIC && o.edge_mode != CWT_EDGE_LINEAR) return CWT_EINVAL;
     if (o.normalization != CWT_NORM_UNIT_ENERGY && o.normalization != CWT_NORM_MNE) return CWT_EINVAL;
+    if (o.specialize != 0 && o.specialize != 1) return CWT_EINVAL;
     // linear edges: pad by the widest wavelet's support radius R (Gaussian
     // envelope below 1e-9 of its peak beyond R samples) so that nothing wraps
     int pad_extra = 0;
@@ -323,6 +325,12 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             p->bytes += sizeof(float2) * (size_t)NL;
         }
     }
+    if (e == cudaSuccess && o.specialize && p->mr && p->cl == 1 && p->sch.fixed < 0) {
+        // a failed compile or load is not a plan error: the runtime-schedule kernels run
+        std::string log;
+        p->jit = cwtk::jit_kernels(p->sch, cwtk::mr_launch_rows(p->sch, channels * n_freqs), p->device, &log);
+        if (!p->jit) p->last_error = log;
+    }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
     if (e == cudaSuccess && tc) {
         e = cwtk::dmalloc(&p->tc_chmax, sizeof(float) * (size_t)channels);
@@ -393,6 +401,11 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->precision = p->precision;
     info->cluster = p->mr ? p->cl : (p->M > cwtk::kMaxFft ? p->M / cwtk::kMaxFft : 1);
     if (p->mr) describe_schedule(p->sch, p->cl, info->radices, info->inlined_pair, &info->fixed_kernel);
+    info->specialized = p->jit != nullptr;
+    if (p->jit) {  // the compiled-at-creation kernels are fixed-length ones
+        info->fixed_kernel = 1;
+        info->inlined_pair[0] = info->inlined_pair[1] = 0;
+    }
     return CWT_OK;
 }
 

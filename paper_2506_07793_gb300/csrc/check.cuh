@@ -13,7 +13,9 @@
 // both macros are the identity and cost nothing.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 #ifdef CWT_BOUNDS_CHECK
 

@@ -23,8 +23,10 @@
 //    functor (fused epilogue), so neither end touches shared memory.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "check.cuh"
 

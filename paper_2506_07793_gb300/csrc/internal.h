@@ -16,6 +16,9 @@
 
 namespace cwtk {
 
+struct JitKernels;  // jit.cu
+
+
 constexpr int kMinFft = 32;        // smallest padded length (keeps radix passes >= 2)
 constexpr int kMaxFftLog2 = 14;    // largest one-CTA length 16384 (shared-memory row)
 constexpr int kMaxFft = 1 << kMaxFftLog2;
@@ -78,6 +81,7 @@ struct cwt_plan_s {
     bool mr = false;            // smooth (non power-of-two) N: mixed-radix kernels
     cwtk::MrSchedule sch{};     // their pass schedule (of N / cl points)
     int cl = 1;                 // smooth N above 16384: CTAs per row (a cluster), N = cl * sch.N
+    cwtk::JitKernels *jit = nullptr;  // kernels compiled at plan creation for sch (jit.cu; shared, cached)
     float2 *twN = nullptr;      // exp(2 pi i m / N), m < N (mixed-radix plans only)
     float2 *twL = nullptr;      // cl > 1: exp(2 pi i m / NL), m < NL = N / cl
     float *bank = nullptr;    // [S][N] W_s[k] / N (real)
@@ -209,6 +213,14 @@ cudaError_t launch_fft_cluster(const float2 *in, float2 *out, int log2n, int bat
 bool mr_schedule(int N, MrSchedule *out);
 cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st);
 cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+// Plan-time specialization (jit.cu): the fixed-length kernels compiled for
+// schedule s with `rows` rows per CTA on `device` (cached), or nullptr with
+// the reason in *log; the same compile for sm_103a without a device, as a
+// check.
+JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *log);
+bool jit_compile_check(const MrSchedule &s, int rows, std::string *log);
+// Rows per CTA of the runtime-schedule kernels for total_rows rows (smooth.cu).
+int mr_launch_rows(const MrSchedule &sch, int total_rows);
 // Smooth lengths above 16384 on clusters (smooth_cluster.cu).
 bool mr_cluster_split(int N, int *cl, MrSchedule *sch);
 cudaError_t launch_forward_mr_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st);

@@ -1,0 +1,267 @@
+// jit.cu -- plan-time specialization of the smooth-length kernels (Section
+// "Fast Fourier transform": the paper pads to 2,3,5,7-smooth lengths).
+//
+// The fixed-length kernels of smooth_device.cuh run a radix schedule whose
+// every stride, butterfly count and divisor is a compile-time constant; the
+// library ships them for 27 whole-second EEG lengths (CWT_MR_FIXED), and
+// every other smooth length that one CTA holds runs the runtime-schedule
+// kernels.  A plan created with cwt_options.specialize = 1 gets the fixed
+// form for its own length instead: NVRTC compiles smooth_device.cuh (its text
+// is embedded in the library at build time, jit_headers.cpp) for the
+// scheduler's schedule of N into a cubin for the device's architecture, the
+// driver loads it, and the plan launches those kernels.  Modules are cached
+// per (device, schedule) for the life of the process; a failed compile or
+// load leaves the plan on the runtime-schedule kernels
+// (cwt_plan_info.specialized reports which ran).
+//
+// Rows per CTA are the runtime-schedule kernels' choice for the plan's row
+// count (up to 256 threads, at least two CTAs per SM when rows are few);
+// CTAs per SM as many as shared memory, 2048 threads and 64 registers a
+// thread allow, at most 4 (the rules the shipped fixed kernels were measured
+// with).
+#include <cuda.h>
+#include <nvrtc.h>
+
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "smooth_kernel.cuh"
+
+// The headers the plan-time compiler needs, embedded by build.py.
+extern "C" const int cwt_jit_header_count;
+extern "C" const char *const cwt_jit_header_names[];
+extern "C" const char *const cwt_jit_header_texts[];
+
+namespace cwtk {
+
+struct JitKernels {
+    CUmodule mod = nullptr;
+    CUfunction sb = nullptr, fwd = nullptr;
+    int rows = 1, threads = 32, smem = 0;
+};
+
+namespace {
+
+// The driver calls, fetched through the runtime (the library links no driver
+// library, so that it loads on a machine without one).
+struct Driver {
+    CUresult (*module_load_data)(CUmodule *, const void *) = nullptr;
+    CUresult (*module_get_function)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*module_unload)(CUmodule) = nullptr;
+    CUresult (*func_set_attribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*launch_kernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                              CUstream, void **, void **) = nullptr;
+    bool ok = false;
+};
+
+template <typename F>
+bool entry(const char *name, F *fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    *fn = reinterpret_cast<F>(p);
+    return true;
+}
+
+const Driver &driver() {
+    static const Driver d = [] {
+        Driver x;
+        x.ok = entry("cuModuleLoadData", &x.module_load_data) &&
+               entry("cuModuleGetFunction", &x.module_get_function) && entry("cuModuleUnload", &x.module_unload) &&
+               entry("cuFuncSetAttribute", &x.func_set_attribute) && entry("cuLaunchKernel", &x.launch_kernel);
+        return x;
+    }();
+    return d;
+}
+
+struct JitBinary {
+    std::vector<char> cubin;
+    std::string sb_name, fwd_name;  // the kernels' lowered names
+};
+
+std::mutex g_jit_mu;
+std::map<std::string, JitBinary> g_cubins;     // (arch, schedule) -> compiled module
+std::map<std::string, JitKernels *> g_modules;  // (device, schedule) -> loaded kernels
+
+struct JitShape {
+    int rows, minb, threads, smem;
+};
+
+JitShape jit_shape(const MrSchedule &s, int rows) {
+    JitShape j;
+    const int row_smem = (s.N + (s.N >> 4)) * 8;
+    j.rows = rows;
+    j.threads = (j.rows * s.T + 31) / 32 * 32;
+    j.smem = j.rows * row_smem;
+    const int by_smem = (227 * 1024) / (j.smem + 1024);
+    const int by_threads = 2048 / j.threads;
+    const int by_regs = 65536 / (j.threads * 64);
+    j.minb = by_smem < by_threads ? by_smem : by_threads;
+    if (by_regs < j.minb) j.minb = by_regs;
+    if (j.minb > 4) j.minb = 4;
+    if (j.minb < 1) j.minb = 1;
+    return j;
+}
+
+// MrFixed<N, T, ROWS, MINB, R0, R1, ...> for schedule s.
+std::string fixed_type(const MrSchedule &s, const JitShape &j) {
+    std::string t = "cwtk::MrFixed<" + std::to_string(s.N) + ", " + std::to_string(s.T) + ", " +
+                    std::to_string(j.rows) + ", " + std::to_string(j.minb);
+    for (int q = 0; q < s.np; ++q) t += ", " + std::to_string(s.p[q].R);
+    return t + ">";
+}
+
+// Compile the two kernels of schedule s for `arch` (e.g. "sm_103a"); on
+// failure *log holds the compiler's message.
+bool compile(const MrSchedule &s, int rows, const std::string &arch, std::vector<char> *cubin,
+             std::string *sb_name, std::string *fwd_name, std::string *log) {
+    const JitShape j = jit_shape(s, rows);
+    const std::string fx = fixed_type(s, j);
+    const std::string sb_expr = "&cwtk::mr_fixed_scale_block_kernel<" + fx + ">";
+    const std::string fwd_expr = "&cwtk::mr_fixed_forward_kernel<" + fx + ">";
+    const char *src = "#include \"smooth_device.cuh\"\n";
+    nvrtcProgram prog = nullptr;
+    if (nvrtcCreateProgram(&prog, src, "cwt_specialized.cu", cwt_jit_header_count, cwt_jit_header_texts,
+                           cwt_jit_header_names) != NVRTC_SUCCESS) {
+        *log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    nvrtcAddNameExpression(prog, sb_expr.c_str());
+    nvrtcAddNameExpression(prog, fwd_expr.c_str());
+    const std::string arch_opt = "--gpu-architecture=" + arch;
+    // -default-device: the kernels' lambdas (no execution-space annotation) are device code
+    const char *opts[] = {arch_opt.c_str(), "-std=c++17", "-lineinfo", "-default-device"};
+    const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+    size_t log_size = 0;
+    nvrtcGetProgramLogSize(prog, &log_size);
+    std::string lg(log_size, '\0');
+    if (log_size) nvrtcGetProgramLog(prog, &lg[0]);
+    bool ok = r == NVRTC_SUCCESS;
+    if (ok) {
+        const char *lowered = nullptr;
+        ok = nvrtcGetLoweredName(prog, sb_expr.c_str(), &lowered) == NVRTC_SUCCESS && lowered;
+        if (ok) *sb_name = lowered;
+        ok = ok && nvrtcGetLoweredName(prog, fwd_expr.c_str(), &lowered) == NVRTC_SUCCESS && lowered;
+        if (ok) *fwd_name = lowered;
+        size_t n = 0;
+        ok = ok && nvrtcGetCUBINSize(prog, &n) == NVRTC_SUCCESS && n > 0;
+        if (ok) {
+            cubin->resize(n);
+            ok = nvrtcGetCUBIN(prog, cubin->data()) == NVRTC_SUCCESS;
+        }
+    }
+    if (!ok) *log = std::string("plan-time compile of ") + fx + " failed: " + nvrtcGetErrorString(r) + "\n" + lg;
+    nvrtcDestroyProgram(&prog);
+    return ok;
+}
+
+std::string schedule_key(const MrSchedule &s, int rows) {
+    std::string k = std::to_string(s.N) + "/" + std::to_string(s.T) + "/" + std::to_string(rows);
+    for (int q = 0; q < s.np; ++q) k += "x" + std::to_string(s.p[q].R);
+    return k;
+}
+
+}  // namespace
+
+bool jit_compile_check(const MrSchedule &s, int rows, std::string *log) {
+    std::vector<char> cubin;
+    std::string a, b;
+    return compile(s, rows, "sm_103a", &cubin, &a, &b, log);
+}
+
+JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *log) {
+#ifdef CWT_BOUNDS_CHECK
+    // the bounds-checked build runs the runtime-schedule kernels, whose checks it collects
+    (void)s;
+    (void)rows;
+    (void)device;
+    *log = "plan-time specialization is off in the bounds-checked build";
+    return nullptr;
+#else
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device) != cudaSuccess) {
+        *log = "compute capability query failed";
+        return nullptr;
+    }
+    const std::string arch = "sm_" + std::to_string(major * 10 + minor) + "a";
+    const std::string skey = schedule_key(s, rows);
+    const std::string mkey = std::to_string(device) + ":" + skey;
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    auto it = g_modules.find(mkey);
+    if (it != g_modules.end()) return it->second;
+    auto bin = g_cubins.find(arch + ":" + skey);
+    if (bin == g_cubins.end()) {
+        JitBinary b;
+        if (!compile(s, rows, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return nullptr;
+        bin = g_cubins.emplace(arch + ":" + skey, std::move(b)).first;
+    }
+    const JitBinary &b = bin->second;
+    // the runtime API has made the device's primary context current
+    const Driver &drv = driver();
+    if (!drv.ok) {
+        *log = "the driver's module calls are not available";
+        return nullptr;
+    }
+    JitKernels *k = new (std::nothrow) JitKernels();
+    if (!k) return nullptr;
+    const JitShape j = jit_shape(s, rows);
+    k->rows = j.rows;
+    k->threads = j.threads;
+    k->smem = j.smem;
+    CUresult r = drv.module_load_data(&k->mod, b.cubin.data());
+    if (r == CUDA_SUCCESS) r = drv.module_get_function(&k->sb, k->mod, b.sb_name.c_str());
+    if (r == CUDA_SUCCESS) r = drv.module_get_function(&k->fwd, k->mod, b.fwd_name.c_str());
+    if (r == CUDA_SUCCESS) r = drv.func_set_attribute(k->sb, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k->smem);
+    if (r == CUDA_SUCCESS) r = drv.func_set_attribute(k->fwd, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k->smem);
+    if (r != CUDA_SUCCESS) {
+        *log = "loading the specialized kernels failed: driver error " + std::to_string((int)r);
+        if (k->mod) drv.module_unload(k->mod);
+        delete k;
+        return nullptr;
+    }
+    g_modules[mkey] = k;
+    return k;
+#endif
+}
+
+cudaError_t jit_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
+    const JitKernels *k = p->jit;
+    MrArgs args = a;
+    void *params[] = {&args};
+    const unsigned grid = (unsigned)((a.total_rows + k->rows - 1) / k->rows);
+    const CUresult r = driver().launch_kernel(k->sb, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
+                                              (CUstream)st, params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+cudaError_t jit_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    const JitKernels *k = p->jit;
+    const void *x = signal;
+    int f64 = p->io == CWT_DTYPE_F64, n = p->n, C = p->C;
+    float2 *spec = p->spec;
+    const float2 *twN = p->twN;
+    void *params[] = {&x, &f64, &n, &spec, &twN, &C};
+    const unsigned grid = (unsigned)((C + k->rows - 1) / k->rows);
+    const CUresult r = driver().launch_kernel(k->fwd, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
+                                              (CUstream)st, params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace cwtk
+
+extern "C" cwt_status cwt_specialize_check(int n_fft, char *log, size_t log_len) {
+    cwtk::MrSchedule s;
+    if (n_fft > cwtk::kMaxFft || (n_fft & (n_fft - 1)) == 0 || !cwtk::mr_schedule(n_fft, &s))
+        return CWT_EUNSUPPORTED;
+    std::string lg;
+    const bool ok = cwtk::jit_compile_check(s, s.T < 128 ? 256 / s.T : 1, &lg);
+    if (log && log_len) std::snprintf(log, log_len, "%s", lg.c_str());
+    return ok ? CWT_OK : CWT_ECUDA;
+}

@@ -34,7 +34,6 @@
 //    come from a short multiplication chain.
 #pragma once
 
-#include <utility>
 
 #include "fft_core.cuh"
 
@@ -122,14 +121,28 @@ __device__ __forceinline__ float2 rot_c(float2 a) {
     }
 }
 
-// Compile-time loop: f(std::integral_constant<int, I>) for I < N.
+// Compile-time loop: f(int_c<I>{}) for I < N (int_c<I>::value == I).  The
+// sequence types are the header's own, so that it needs no standard library
+// header (the plan-time compiler, jit.cu, builds it without one).
+template <int I>
+struct int_c {
+    static constexpr int value = I;
+};
+template <int... I>
+struct int_seq {};
+template <int N, int... I>
+struct make_int_seq : make_int_seq<N - 1, N - 1, I...> {};
+template <int... I>
+struct make_int_seq<0, I...> {
+    using type = int_seq<I...>;
+};
 template <typename F, int... I>
-__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
-    (f(std::integral_constant<int, I>{}), ...);
+__device__ __forceinline__ void static_for_impl(F &&f, int_seq<I...>) {
+    (f(int_c<I>{}), ...);
 }
 template <int N, typename F>
 __device__ __forceinline__ void static_for(F &&f) {
-    static_for_impl(f, std::make_integer_sequence<int, N>{});
+    static_for_impl(f, typename make_int_seq<N>::type{});
 }
 
 // cos / sin (2 pi m / R) for the odd primes, m = 1..(R-1)/2.

@@ -219,6 +219,7 @@ cudaError_t launch_scale_block_mr(const cwt_plan_s *p, void *out_c, void *out_p,
     a.sub = p->d;
     a.total_rows = p->C * p->S;
     a.f64 = p->io == CWT_DTYPE_F64;
+    if (p->jit) return jit_sb_launch(p, a, st);
     if (p->sch.fixed >= 0) return mr_fixed_sb_launch(p, a, st);
     switch (p->sch.fast) {
 #define CWT_MR_CASE(I, A, B) \

@@ -13,6 +13,7 @@ namespace cwtk {
 
 cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
     if (p->cl > 1) return launch_forward_mr_cluster(p, signal, st);
+    if (p->jit) return jit_fwd_launch(p, signal, st);
     if (p->sch.fixed >= 0) return mr_fixed_fwd_launch(p, signal, st);
     switch (p->sch.fast) {
 #define CWT_MR_CASE(I, A, B) \

@@ -40,7 +40,7 @@ class cwt_options(ctypes.Structure):
                 ("pad_policy", ctypes.c_int), ("fft_length", ctypes.c_int),
                 ("io_dtype", ctypes.c_int), ("edge_mode", ctypes.c_int),
                 ("gmw_gamma", ctypes.c_double), ("normalization", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("specialize", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class cwt_plan_info_t(ctypes.Structure):
@@ -51,7 +51,7 @@ class cwt_plan_info_t(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("bank_ms", ctypes.c_double),
                 ("radices", ctypes.c_int * 8), ("inlined_pair", ctypes.c_int * 2),
                 ("fixed_kernel", ctypes.c_int), ("precision", ctypes.c_int),
-                ("cluster", ctypes.c_int)]
+                ("cluster", ctypes.c_int), ("specialized", ctypes.c_int)]
 
 
 class cwt_epoch(ctypes.Structure):
@@ -100,6 +100,7 @@ _sig("cwt_status_str", ctypes.c_char_p, [ctypes.c_int])
 _sig("cwt_options_init", ctypes.c_int, [ctypes.POINTER(cwt_options)])
 _sig("cwt_fft_length", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip])
 _sig("cwt_smooth_schedule", ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip, _ip])
+_sig("cwt_specialize_check", ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t])
 _sig("cwt_plan_create", ctypes.c_int,
      [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, _dp,
       ctypes.c_int, ctypes.c_uint, ctypes.POINTER(cwt_options)])
@@ -194,6 +195,18 @@ def cwt_smooth_schedule(n_fft):
     _check(_lib.cwt_smooth_schedule(int(n_fft), rad, ctypes.byref(t), pair, ctypes.byref(fixed)),
            "cwt_smooth_schedule")
     return [r for r in rad if r], t.value, (pair[0], pair[1]), fixed.value
+
+
+def cwt_specialize_check(n_fft):
+    """Compile (host only, for sm_103a) the fixed-length kernels of the one-CTA
+    schedule of n_fft that cwt_options.specialize would build; returns the
+    compiler's log.  Raises CWTError (CWT_EUNSUPPORTED: no such schedule;
+    CWT_ECUDA: the compile failed, log in the message)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = _lib.cwt_specialize_check(int(n_fft), buf, ctypes.sizeof(buf))
+    if st != CWT_OK:
+        raise CWTError(st, f"cwt_specialize_check({n_fft}): {buf.value.decode(errors='replace')[:2000]}")
+    return buf.value.decode(errors="replace")
 
 
 def cwt_plan_create(channels, samples, fs, freqs_hz, n_cycles, wavelet=CWT_WAVELET_MORLET,
@@ -330,9 +343,11 @@ class CWT:
 
     def __init__(self, channels, samples, fs, freqs, n_cycles, outputs=("power",),
                  wavelet="morlet", dtype="f32", decimation=1, fft_length=0, pad="pow2",
-                 gmw_gamma=3.0, edge="cyclic", precision="fp32", normalization="unit"):
+                 gmw_gamma=3.0, edge="cyclic", precision="fp32", normalization="unit",
+                 specialize=False):
         opt = cwt_options_init()
         opt.normalization = {"unit": CWT_NORM_UNIT_ENERGY, "mne": CWT_NORM_MNE}[normalization]
+        opt.specialize = 1 if specialize else 0
         opt.precision = {"fp32": CWT_PREC_FP32, "tc_fp16": CWT_PREC_TC_FP16,
                          "tc_bf16": CWT_PREC_TC_BF16}[precision]
         opt.decimation = int(decimation)

@@ -147,7 +147,7 @@ BAD = [
     dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
     dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]), dict(edge=2), dict(edge=-1),
     dict(edge=1, fft_length=128),  # linear edges need N >= n + R + 1 (here 100 + 363 + 1)
-    dict(norm=2), dict(norm=-1),
+    dict(norm=2), dict(norm=-1), dict(specialize=2), dict(specialize=-1),
     # a carrier far below the first DFT bin: 1.5 Hz with sigma 7 in a 32-point
     # window at 500 Hz (first bin 15.6 Hz) has a spectrum below 1e-150 on every
     # bin, so its unit-energy normalisation would underflow
@@ -162,13 +162,14 @@ BAD = [
 def test_invalid_arguments_rejected_before_cuda(lib, bad):
     a = dict(channels=2, samples=100, fs=500.0, freqs=[10.0, 20.0], n_cycles=[7.0, 7.0],
              wavelet=0, kinds=2, decimation=1, io=0, precision=0, fft_length=0, gamma=3.0, edge=0,
-             norm=0)
+             norm=0, specialize=0)
     a.update(bad)
     o = lib.cwt_options_init()
     o.decimation, o.io_dtype, o.precision, o.fft_length = a["decimation"], a["io"], a["precision"], a["fft_length"]
     o.gmw_gamma = a["gamma"]
     o.edge_mode = a["edge"]
     o.normalization = a["norm"]
+    o.specialize = a["specialize"]
     f = np.asarray(a["freqs"], dtype=np.float64)
     c = np.asarray(a["n_cycles"], dtype=np.float64)
     if len(c) != len(f):
@@ -186,8 +187,10 @@ def test_option_struct_layout(lib):
     assert o.gmw_gamma == 3.0 and o.decimation == 1
     assert type(o).edge_mode.offset == 20 and o.edge_mode == lib.CWT_EDGE_CYCLIC
     assert type(o).normalization.offset == 32 and o.normalization == lib.CWT_NORM_UNIT_ENERGY
+    assert type(o).specialize.offset == 36 and o.specialize == 0
     assert ctypes.sizeof(lib.cwt_plan_info_t) == 120 and lib.cwt_plan_info_t.radices.offset == 64
     assert lib.cwt_plan_info_t.fixed_kernel.offset == 104 and lib.cwt_plan_info_t.cluster.offset == 112
+    assert lib.cwt_plan_info_t.specialized.offset == 116
     so = lib.cwt_server_options_init()
     assert ctypes.sizeof(so) == 56 and type(so).gmw_gamma.offset == 32
     assert so.gmw_gamma == 3.0 and so.max_streams == 32
@@ -338,3 +341,19 @@ def test_grid_check_boundary(lib):
         with pytest.raises(lib.CWTError) as e:
             lib.cwt_plan_create(1, 32, 500.0, [6.0], [5.0], 0, lib.CWT_OUT_POWER, o)
         assert e.value.status != lib.CWT_EINVAL
+
+
+@pytest.mark.parametrize("N", [6300, 42])
+def test_specialize_check_compiles_on_the_host(lib, N):
+    """The plan-time compiler builds the fixed-length kernels of a smooth
+    length's one-CTA schedule from the embedded source, without a device."""
+    assert lib.cwt_specialize_check(N) == ""  # no warnings either
+
+
+@pytest.mark.parametrize("N", [4096, 14175, 20000, 31])
+def test_specialize_check_refuses_other_lengths(lib, N):
+    """Powers of two, the one-CTA-unscheduled smooth lengths, cluster lengths
+    and lengths below 32 have no one-CTA schedule to specialize."""
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_specialize_check(N)
+    assert e.value.status == lib.CWT_EUNSUPPORTED

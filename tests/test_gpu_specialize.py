@@ -1,0 +1,72 @@
+"""Plan-time specialization (cwt_options.specialize): a smooth length with no
+fixed-length kernel compiled in gets one compiled at plan creation (NVRTC) for
+its scheduler schedule.  Same schedule, same arithmetic: the outputs must be
+bitwise those of the runtime-schedule kernels, and within the FP32 bar of the
+FP64 oracle (Section "Fast Fourier transform" for the padding)."""
+import numpy as np
+import pytest
+
+import oracle
+from eeg_synth import eeg
+from tests.metrics import FP32_TOL, complex_err, power_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2506_07793_gb300 as p
+    return p
+
+# (n = N, C, fs, freqs, cycles, dtype, decimation): runtime-schedule lengths of
+# several shapes -- many rows per CTA (42, 105), a generic and a pair schedule,
+# four passes, one row per CTA up to 512 threads.
+CASES = [
+    (42, 5, 100.0, [8.0, 30.0], [3.0, 5.0], "f32", 1),
+    (105, 4, 100.0, [6.0, 35.0], [4.0, 7.0], "f32", 1),
+    (250, 3, 500.0, [5.0, 60.0, 200.0], [5.0, 7.0, 9.0], "f32", 2),
+    (1323, 3, 500.0, [3.0, 40.0, 220.0], [5.0, 7.0, 10.0], "f64", 1),
+    (6300, 2, 1000.0, [1.0, 30.0, 400.0], [3.0, 7.0, 12.0], "f32", 1),
+    (11025, 2, 1000.0, [0.8, 50.0, 450.0], [4.0, 7.0, 11.0], "f32", 3),
+]
+
+
+def _run(lib, x, n, fs, freqs, cycles, dtype, d, specialize):
+    import torch
+    t = lib.CWT(x.shape[0], n, fs, freqs, cycles, outputs=("complex", "power", "phase"), dtype=dtype,
+                decimation=d, pad="smooth", specialize=specialize)
+    info = t.info
+    out = t(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    t.close()
+    return res, info
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_specialized_kernels_match_runtime_schedule_and_oracle(lib, case):
+    n, C, fs, freqs, cycles, dtype, d = CASES[case]
+    x = eeg(1500 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    plain, info0 = _run(lib, x, n, fs, freqs, cycles, dtype, d, False)
+    spec, info1 = _run(lib, x, n, fs, freqs, cycles, dtype, d, True)
+    assert info0.fft_length == info1.fft_length == n
+    assert info0.specialized == 0 and info0.fixed_kernel == 0
+    assert info1.specialized == 1 and info1.fixed_kernel == 1
+    for k in plain:
+        assert np.array_equal(plain[k], spec[k]), k
+    ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
+    assert complex_err(spec["complex"], ref).max() <= FP32_TOL
+    assert power_err(spec["power"], ref).max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("n,pad", [(10000, "smooth"), (1000, "pow2"), (20000, "smooth")])
+def test_specialize_leaves_compiled_in_paths(lib, n, pad):
+    """A length with a kernel compiled in (10000), a power of two and a cluster
+    row run their usual kernels: nothing is compiled at plan creation."""
+    t = lib.CWT(1, n, 1000.0, [10.0, 50.0], [7.0, 7.0], outputs=("power",), pad=pad, specialize=True)
+    assert t.info.specialized == 0
+    t.close()
