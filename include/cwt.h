@@ -173,10 +173,12 @@ typedef struct {
                          default 3; read only for CWT_WAVELET_GMW */
     int normalization; /* cwt_normalization of each scale's wavelet (default
                           CWT_NORM_UNIT_ENERGY) */
-    int specialize;    /* 1: for a smooth N that one CTA holds and that has no
-                          kernel compiled in, compile the fixed-length kernels for
-                          N's schedule at plan creation (NVRTC, about a second,
-                          cached per process; Section "Fast Fourier transform");
+    int specialize;    /* 1: for a smooth N (not a power of two) with no
+                          fixed-length kernel compiled in, compile the fixed-length
+                          kernels for N's schedule -- or for the local length of
+                          its cluster split -- at plan creation (NVRTC, about a
+                          second, cached per process; Section "Fast Fourier
+                          transform");
                           if that fails the plan runs the runtime-schedule kernels
                           (cwt_plan_info.specialized, cwt_plan_last_error).
                           0 (default): never compile at plan creation */
@@ -246,13 +248,13 @@ cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
 cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlined_pair,
                                int *fixed_kernel);
 
-/* The plan-time compile of cwt_options.specialize for the one-CTA schedule of
- * a smooth n_fft, for sm_103a, without a device (a check that the embedded
- * kernel source compiles): CWT_OK, CWT_EUNSUPPORTED when n_fft is not a
- * length the mixed-radix kernels run in one CTA (see cwt_smooth_schedule), or
- * CWT_ECUDA when the compiler fails; the compiler's log goes to `log` (host
- * memory of log_len bytes, may be NULL), NUL-terminated.  Host-only; no CUDA
- * runtime call. */
+/* The plan-time compile of cwt_options.specialize for a smooth n_fft that is
+ * not a power of two -- its one-CTA schedule, or its cluster split N = CL NL
+ * (see cwt_pad_policy) -- for sm_103a, without a device (a check that the
+ * embedded kernel source compiles): CWT_OK, CWT_EUNSUPPORTED when n_fft is
+ * not such a length, or CWT_ECUDA when the compiler fails; the compiler's log
+ * goes to `log` (host memory of log_len bytes, may be NULL), NUL-terminated.
+ * Host-only; no CUDA runtime call. */
 cwt_status cwt_specialize_check(int n_fft, char *log, size_t log_len);
 
 /*

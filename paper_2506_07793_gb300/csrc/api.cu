@@ -325,10 +325,12 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             p->bytes += sizeof(float2) * (size_t)NL;
         }
     }
-    if (e == cudaSuccess && o.specialize && p->mr && p->cl == 1 && p->sch.fixed < 0) {
+    if (e == cudaSuccess && o.specialize && p->mr &&
+        (p->cl == 1 ? p->sch.fixed < 0 : p->sch.fixed_cl < 0)) {
         // a failed compile or load is not a plan error: the runtime-schedule kernels run
         std::string log;
-        p->jit = cwtk::jit_kernels(p->sch, cwtk::mr_launch_rows(p->sch, channels * n_freqs), p->device, &log);
+        const int rows = p->cl == 1 ? cwtk::mr_launch_rows(p->sch, channels * n_freqs) : 1;
+        p->jit = cwtk::jit_kernels(p->sch, rows, p->cl, p->device, &log);
         if (!p->jit) p->last_error = log;
     }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);

@@ -19,6 +19,7 @@
 
 #include <cooperative_groups.h>
 
+#include "dsmem.cuh"
 #include "fft_core.cuh"
 
 namespace cwtk {
@@ -37,16 +38,6 @@ struct ClusterShape {
     static constexpr int SMEM_BYTES = SMEM_F2 * 8;
     static_assert(CL >= 2 && CL <= 8 && CL * kClPoints == N, "N = 2, 4 or 8 x 16384");
 };
-
-// Load a float2 from the same shared-memory offset in CTA `rank` of the cluster.
-__device__ __forceinline__ float2 ld_cluster(const float2 *local, unsigned rank) {
-    const unsigned laddr = (unsigned)__cvta_generic_to_shared(local);
-    unsigned raddr;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(raddr) : "r"(laddr), "r"(rank));
-    float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(raddr) : "memory");
-    return v;
-}
 
 // Whole-row FFT on the cluster: `load(k)` gives x[k] (k in [0, N)); `store(t,
 // X[t])` receives outputs t = t1 + NL t2 for this CTA's t1 range.  When

@@ -214,11 +214,11 @@ bool mr_schedule(int N, MrSchedule *out);
 cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st);
 cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 // Plan-time specialization (jit.cu): the fixed-length kernels compiled for
-// schedule s with `rows` rows per CTA on `device` (cached), or nullptr with
-// the reason in *log; the same compile for sm_103a without a device, as a
-// check.
-JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *log);
-bool jit_compile_check(const MrSchedule &s, int rows, std::string *log);
+// schedule s with `rows` rows per CTA (cl = 1), or as the local row of a
+// cluster of cl CTAs, on `device` (cached), or nullptr with the reason in
+// *log; the same compile for sm_103a without a device, as a check.
+JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::string *log);
+bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log);
 // Rows per CTA of the runtime-schedule kernels for total_rows rows (smooth.cu).
 int mr_launch_rows(const MrSchedule &sch, int total_rows);
 // Smooth lengths above 16384 on clusters (smooth_cluster.cu).

@@ -3,13 +3,15 @@
 //
 // The fixed-length kernels of smooth_device.cuh run a radix schedule whose
 // every stride, butterfly count and divisor is a compile-time constant; the
-// library ships them for 27 whole-second EEG lengths (CWT_MR_FIXED), and
-// every other smooth length that one CTA holds runs the runtime-schedule
-// kernels.  A plan created with cwt_options.specialize = 1 gets the fixed
-// form for its own length instead: NVRTC compiles smooth_device.cuh (its text
-// is embedded in the library at build time, jit_headers.cpp) for the
-// scheduler's schedule of N into a cubin for the device's architecture, the
-// driver loads it, and the plan launches those kernels.  Modules are cached
+// library ships them for 27 whole-second EEG lengths (CWT_MR_FIXED) and three
+// cluster local lengths (CWT_CL_MR_FIXED), and every other smooth length runs
+// the runtime-schedule kernels.  A plan created with cwt_options.specialize =
+// 1 gets the fixed form for its own length instead: NVRTC compiles
+// smooth_device.cuh, or smooth_cluster_device.cuh for a row on a cluster of
+// CL CTAs (their text is embedded in the library at build time,
+// jit_headers.cpp), for the scheduler's schedule of N (of N / CL) into a
+// cubin for the device's architecture, the driver loads it, and the plan
+// launches those kernels.  Modules are cached
 // per (device, schedule) for the life of the process; a failed compile or
 // load leaves the plan on the runtime-schedule kernels
 // (cwt_plan_info.specialized reports which ran).
@@ -29,7 +31,7 @@
 #include <string>
 #include <vector>
 
-#include "smooth_kernel.cuh"
+#include "smooth_cluster.cuh"
 
 // The headers the plan-time compiler needs, embedded by build.py.
 extern "C" const int cwt_jit_header_count;
@@ -42,6 +44,7 @@ struct JitKernels {
     CUmodule mod = nullptr;
     CUfunction sb = nullptr, fwd = nullptr;
     int rows = 1, threads = 32, smem = 0;
+    int cl = 1;  // CTAs per row: 1, or the cluster of the cluster kernels
 };
 
 namespace {
@@ -109,7 +112,8 @@ JitShape jit_shape(const MrSchedule &s, int rows) {
     return j;
 }
 
-// MrFixed<N, T, ROWS, MINB, R0, R1, ...> for schedule s.
+// MrFixed<N, T, ROWS, MINB, R0, R1, ...> for schedule s (the local row of a
+// cluster kernel when cl > 1).
 std::string fixed_type(const MrSchedule &s, const JitShape &j) {
     std::string t = "cwtk::MrFixed<" + std::to_string(s.N) + ", " + std::to_string(s.T) + ", " +
                     std::to_string(j.rows) + ", " + std::to_string(j.minb);
@@ -119,13 +123,16 @@ std::string fixed_type(const MrSchedule &s, const JitShape &j) {
 
 // Compile the two kernels of schedule s for `arch` (e.g. "sm_103a"); on
 // failure *log holds the compiler's message.
-bool compile(const MrSchedule &s, int rows, const std::string &arch, std::vector<char> *cubin,
+bool compile(const MrSchedule &s, int rows, int cl, const std::string &arch, std::vector<char> *cubin,
              std::string *sb_name, std::string *fwd_name, std::string *log) {
     const JitShape j = jit_shape(s, rows);
     const std::string fx = fixed_type(s, j);
-    const std::string sb_expr = "&cwtk::mr_fixed_scale_block_kernel<" + fx + ">";
-    const std::string fwd_expr = "&cwtk::mr_fixed_forward_kernel<" + fx + ">";
-    const char *src = "#include \"smooth_device.cuh\"\n";
+    const std::string cls = std::to_string(cl);
+    const std::string sb_expr = cl > 1 ? "&cwtk::cl_mr::scale_block_kernel<" + cls + ", " + fx + ">"
+                                       : "&cwtk::mr_fixed_scale_block_kernel<" + fx + ">";
+    const std::string fwd_expr = cl > 1 ? "&cwtk::cl_mr::forward_kernel<" + cls + ", " + fx + ">"
+                                        : "&cwtk::mr_fixed_forward_kernel<" + fx + ">";
+    const char *src = cl > 1 ? "#include \"smooth_cluster_device.cuh\"\n" : "#include \"smooth_device.cuh\"\n";
     nvrtcProgram prog = nullptr;
     if (nvrtcCreateProgram(&prog, src, "cwt_specialized.cu", cwt_jit_header_count, cwt_jit_header_texts,
                            cwt_jit_header_names) != NVRTC_SUCCESS) {
@@ -161,25 +168,27 @@ bool compile(const MrSchedule &s, int rows, const std::string &arch, std::vector
     return ok;
 }
 
-std::string schedule_key(const MrSchedule &s, int rows) {
-    std::string k = std::to_string(s.N) + "/" + std::to_string(s.T) + "/" + std::to_string(rows);
+std::string schedule_key(const MrSchedule &s, int rows, int cl) {
+    std::string k = std::to_string(s.N) + "/" + std::to_string(s.T) + "/" + std::to_string(rows) + "/" +
+                    std::to_string(cl);
     for (int q = 0; q < s.np; ++q) k += "x" + std::to_string(s.p[q].R);
     return k;
 }
 
 }  // namespace
 
-bool jit_compile_check(const MrSchedule &s, int rows, std::string *log) {
+bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log) {
     std::vector<char> cubin;
     std::string a, b;
-    return compile(s, rows, "sm_103a", &cubin, &a, &b, log);
+    return compile(s, rows, cl, "sm_103a", &cubin, &a, &b, log);
 }
 
-JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *log) {
+JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::string *log) {
 #ifdef CWT_BOUNDS_CHECK
     // the bounds-checked build runs the runtime-schedule kernels, whose checks it collects
     (void)s;
     (void)rows;
+    (void)cl;
     (void)device;
     *log = "plan-time specialization is off in the bounds-checked build";
     return nullptr;
@@ -191,7 +200,7 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *
         return nullptr;
     }
     const std::string arch = "sm_" + std::to_string(major * 10 + minor) + "a";
-    const std::string skey = schedule_key(s, rows);
+    const std::string skey = schedule_key(s, rows, cl);
     const std::string mkey = std::to_string(device) + ":" + skey;
     std::lock_guard<std::mutex> lock(g_jit_mu);
     auto it = g_modules.find(mkey);
@@ -199,7 +208,7 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *
     auto bin = g_cubins.find(arch + ":" + skey);
     if (bin == g_cubins.end()) {
         JitBinary b;
-        if (!compile(s, rows, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return nullptr;
+        if (!compile(s, rows, cl, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return nullptr;
         bin = g_cubins.emplace(arch + ":" + skey, std::move(b)).first;
     }
     const JitBinary &b = bin->second;
@@ -215,6 +224,7 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int device, std::string *
     k->rows = j.rows;
     k->threads = j.threads;
     k->smem = j.smem;
+    k->cl = cl;
     CUresult r = drv.module_load_data(&k->mod, b.cubin.data());
     if (r == CUDA_SUCCESS) r = drv.module_get_function(&k->sb, k->mod, b.sb_name.c_str());
     if (r == CUDA_SUCCESS) r = drv.module_get_function(&k->fwd, k->mod, b.fwd_name.c_str());
@@ -246,10 +256,30 @@ cudaError_t jit_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t
     const void *x = signal;
     int f64 = p->io == CWT_DTYPE_F64, n = p->n, C = p->C;
     float2 *spec = p->spec;
-    const float2 *twN = p->twN;
-    void *params[] = {&x, &f64, &n, &spec, &twN, &C};
-    const unsigned grid = (unsigned)((C + k->rows - 1) / k->rows);
-    const CUresult r = driver().launch_kernel(k->fwd, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
+    const float2 *twN = p->twN, *twL = p->twL;
+    MrSchedule sch = p->sch;
+    CUresult r;
+    if (k->cl > 1) {  // forward_kernel<CL, FX>(x, f64, n, spec, twL, twN, sch), C rows of CL CTAs
+        void *params[] = {&x, &f64, &n, &spec, &twL, &twN, &sch};
+        r = driver().launch_kernel(k->fwd, (unsigned)(C * k->cl), 1, 1, (unsigned)k->threads, 1, 1,
+                                   (unsigned)k->smem, (CUstream)st, params, nullptr);
+    } else {  // mr_fixed_forward_kernel<FX>(x, f64, n, spec, twN, C)
+        void *params[] = {&x, &f64, &n, &spec, &twN, &C};
+        const unsigned grid = (unsigned)((C + k->rows - 1) / k->rows);
+        r = driver().launch_kernel(k->fwd, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
+                                   (CUstream)st, params, nullptr);
+    }
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+// scale_block_kernel<CL, FX>(ClMrArgs, MrSchedule): rows of CL CTAs each.
+cudaError_t jit_cl_sb_launch(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+    const JitKernels *k = p->jit;
+    ClMrArgs args = a;
+    MrSchedule sch = p->sch;
+    void *params[] = {&args, &sch};
+    const unsigned grid = (unsigned)(p->C * p->S * k->cl);
+    const CUresult r = driver().launch_kernel(k->sb, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
                                               (CUstream)st, params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
@@ -258,10 +288,13 @@ cudaError_t jit_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t
 
 extern "C" cwt_status cwt_specialize_check(int n_fft, char *log, size_t log_len) {
     cwtk::MrSchedule s;
-    if (n_fft > cwtk::kMaxFft || (n_fft & (n_fft - 1)) == 0 || !cwtk::mr_schedule(n_fft, &s))
+    int cl = 1;
+    if (n_fft < cwtk::kMinFft || n_fft > cwtk::kMaxClusterFft || (n_fft & (n_fft - 1)) == 0) return CWT_EUNSUPPORTED;
+    if (!(n_fft <= cwtk::kMaxFft && cwtk::mr_schedule(n_fft, &s)) && !cwtk::mr_cluster_split(n_fft, &cl, &s))
         return CWT_EUNSUPPORTED;
     std::string lg;
-    const bool ok = cwtk::jit_compile_check(s, s.T < 128 ? 256 / s.T : 1, &lg);
+    const int rows = cl == 1 && s.T < 128 ? 256 / s.T : 1;
+    const bool ok = cwtk::jit_compile_check(s, rows, cl, &lg);
     if (log && log_len) std::snprintf(log, log_len, "%s", lg.c_str());
     return ok ? CWT_OK : CWT_ECUDA;
 }

@@ -7,6 +7,7 @@
 namespace cwtk {
 
 cudaError_t launch_forward_mr_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
+    if (p->jit) return jit_fwd_launch(p, signal, st);
     if (p->sch.fixed_cl >= 0) return cl_mr_fixed_fwd(p, signal, st);
     switch (p->cl) {
 #define CWT_CL_CASE(CL) \
@@ -32,6 +33,7 @@ cudaError_t launch_scale_block_mr_cluster(const cwt_plan_s *p, void *out_c, void
     a.n_out = p->n_out;
     a.sub = p->d;
     a.f64 = p->io == CWT_DTYPE_F64;
+    if (p->jit) return jit_cl_sb_launch(p, a, st);
     if (p->sch.fixed_cl >= 0) return cl_mr_fixed_sb(p, a, st);
     switch (p->cl) {
 #define CWT_CL_CASE(CL) \

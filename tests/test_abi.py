@@ -343,17 +343,19 @@ def test_grid_check_boundary(lib):
         assert e.value.status != lib.CWT_EINVAL
 
 
-@pytest.mark.parametrize("N", [6300, 42])
+@pytest.mark.parametrize("N", [6300, 42, 50000, 14175])
 def test_specialize_check_compiles_on_the_host(lib, N):
     """The plan-time compiler builds the fixed-length kernels of a smooth
-    length's one-CTA schedule from the embedded source, without a device."""
+    length's one-CTA schedule (6300, 42), or the cluster kernels on its local
+    length (50000 = 4 x 12500, 14175 = 3 x 4725), from the embedded source,
+    without a device."""
     assert lib.cwt_specialize_check(N) == ""  # no warnings either
 
 
-@pytest.mark.parametrize("N", [4096, 14175, 20000, 31])
+@pytest.mark.parametrize("N", [4096, 78125, 31, 131072 * 2])
 def test_specialize_check_refuses_other_lengths(lib, N):
-    """Powers of two, the one-CTA-unscheduled smooth lengths, cluster lengths
-    and lengths below 32 have no one-CTA schedule to specialize."""
+    """Powers of two, smooth lengths with neither a schedule nor a split, and
+    lengths outside [32, 131072] have nothing to specialize."""
     with pytest.raises(lib.CWTError) as e:
         lib.cwt_specialize_check(N)
     assert e.value.status == lib.CWT_EUNSUPPORTED

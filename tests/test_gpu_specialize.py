@@ -63,10 +63,35 @@ def test_specialized_kernels_match_runtime_schedule_and_oracle(lib, case):
     assert power_err(spec["power"], ref).max() <= FP32_TOL
 
 
+# cluster rows whose local length has no kernel compiled in: (n = N, C, fs,
+# freqs, cycles, decimation, CL)
+CLUSTER_CASES = [
+    (50000, 1, 1000.0, [1.0, 100.0, 450.0], [20.0, 7.0, 4.0], 4, 4),
+    (14175, 2, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], 1, 3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CLUSTER_CASES)))
+def test_specialized_cluster_kernels_match_runtime_schedule_and_oracle(lib, case):
+    """The cluster kernels compiled for the local length of the split: bitwise
+    the runtime-schedule cluster kernels, and within the bar of the oracle."""
+    n, C, fs, freqs, cycles, d, CL = CLUSTER_CASES[case]
+    x = eeg(1600 + case, C, n, fs, np.float32)
+    plain, info0 = _run(lib, x, n, fs, freqs, cycles, "f32", d, False)
+    spec, info1 = _run(lib, x, n, fs, freqs, cycles, "f32", d, True)
+    assert info0.cluster == info1.cluster == CL
+    assert info0.specialized == 0 and info1.specialized == 1 and info1.fixed_kernel == 1
+    for k in plain:
+        assert np.array_equal(plain[k], spec[k]), k
+    ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
+    assert power_err(spec["power"], ref).max() <= FP32_TOL
+
+
 @pytest.mark.parametrize("n,pad", [(10000, "smooth"), (1000, "pow2"), (20000, "smooth")])
 def test_specialize_leaves_compiled_in_paths(lib, n, pad):
     """A length with a kernel compiled in (10000), a power of two and a cluster
-    row run their usual kernels: nothing is compiled at plan creation."""
+    row on a compiled-in local length (20000 = 2 x 10000) run their usual
+    kernels: nothing is compiled at plan creation."""
     t = lib.CWT(1, n, 1000.0, [10.0, 50.0], [7.0, 7.0], outputs=("power",), pad=pad, specialize=True)
     assert t.info.specialized == 0
     t.close()
