@@ -793,7 +793,7 @@ def precision_suite(args):
         line = run_plan_workload(a, "precision")
         keep = {k: line[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "clocks",
                                      "gpu_launches", "e2e", "cpu_baseline", "plain_fp32_gpu",
-                                     "steps", "warmup") if k in line}
+                                     "error_vs_fp32_gpu", "steps", "warmup") if k in line}
         if not main:
             keep["fft_length"] = line["config"]["fft_length"]
         out[key] = keep
@@ -1120,11 +1120,37 @@ def run_plan_workload(args, name):
     else:
         plain = None
     cw.cwt_plan_destroy(plan)
+    tc_err = (tc_error_vs_fp32(cw, w, popt, x, out_p, stream)
+              if name == "precision" and args.precision != "fp32" else None)
     other = (other_padding(cw, w, kinds, "pow2" if args.pad == "smooth" else "smooth", x,
                            (out_c, out_p, out_ph), flush, stream, args)
              if name == "fused" and world == 1 and not getattr(args, "no_other", False) else None)
-    return finish_plan_line(args, name, w, info, N, world, rank, value, ms_step, wall, clk, roofline,
+    line = finish_plan_line(args, name, w, info, N, world, rank, value, ms_step, wall, clk, roofline,
                             e2e, plain, other, coeffs_rank, x_host)
+    if line is not None and tc_err is not None:
+        line["error_vs_fp32_gpu"] = tc_err
+    return line
+
+
+def tc_error_vs_fp32(cw, w, popt, x, tc_power, stream, channels=4):
+    """The tensor-core result against the FP32 path on the same rows, per
+    frequency: max over the first `channels` channels of each row's
+    max_t |P_tc - P_fp32| / max_t P_fp32 (the FP32 path is itself within 1e-5
+    of the FP64 oracle, which tests/test_gpu_tc.py checks per frequency)."""
+    import torch
+    o = cw.cwt_options_init()
+    o.pad_policy = popt.pad_policy
+    o.precision = cw.CWT_PREC_FP32
+    plan = cw.cwt_plan_create(channels, w.samples, w.fs, w.freqs, w.n_cycles, cw.CWT_WAVELET_MORLET,
+                              cw.CWT_OUT_POWER, o)
+    ref = torch.empty((channels, w.scales, w.n_out), dtype=torch.float32, device="cuda")
+    cw.cwt_execute(plan, x[:channels].contiguous(), None, ref, None, stream)
+    torch.cuda.synchronize()
+    cw.cwt_plan_destroy(plan)
+    err = ((tc_power[:channels] - ref).abs().amax(dim=-1) / ref.amax(dim=-1)).amax(dim=0)
+    err = [float(e) for e in err.cpu()]
+    return {"channels": channels, "freqs_hz": [round(float(f), 4) for f in w.freqs],
+            "power_err_per_frequency": [float(f"{e:.3g}") for e in err], "max": max(err), "bar": 2e-3}
 
 
 def end_to_end(cw, plan, x_host, shape, out_c, out_ph, stream, w, world, dist, e2e_steps,
