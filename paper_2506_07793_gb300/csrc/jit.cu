@@ -11,10 +11,9 @@
 // CL CTAs (their text is embedded in the library at build time,
 // jit_headers.cpp), for the scheduler's schedule of N (of N / CL) into a
 // cubin for the device's architecture, the driver loads it, and the plan
-// launches those kernels.  Modules are cached
-// per (device, schedule) for the life of the process; a failed compile or
-// load leaves the plan on the runtime-schedule kernels
-// (cwt_plan_info.specialized reports which ran).
+// launches those kernels.  Modules are cached per (device, schedule) for the
+// life of the process; a failed compile or load leaves the plan on the
+// runtime-schedule kernels (cwt_plan_info.specialized reports which ran).
 //
 // Rows per CTA are the runtime-schedule kernels' choice for the plan's row
 // count (up to 256 threads, at least two CTAs per SM when rows are few);

@@ -106,6 +106,13 @@ __device__ __forceinline__ int local_n(const MrSchedule &sch) {
     else return FX::N;
 }
 
+// Threads per CTA the kernel is compiled for.
+template <class FX>
+constexpr int max_threads() {
+    if constexpr (is_void<FX>::value) return kMrThreads;
+    else return FX::THREADS;
+}
+
 // CTAs per SM the register budget is set for.
 template <class FX>
 constexpr int min_blocks() {
@@ -144,7 +151,7 @@ __device__ __forceinline__ void cross(const float2 *sm, const float2 *__restrict
 }
 
 template <int CL, class FX>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, min_blocks<FX>())
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(max_threads<FX>(), min_blocks<FX>())
 scale_block_kernel(const ClMrArgs a, const MrSchedule sch) {
     extern __shared__ float2 mrsm[];
     float2 *sm = mrsm;
@@ -187,7 +194,7 @@ scale_block_kernel(const ClMrArgs a, const MrSchedule sch) {
 }
 
 template <int CL, class FX>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kMrThreads, min_blocks<FX>())
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(max_threads<FX>(), min_blocks<FX>())
 forward_kernel(const void *__restrict__ x, int f64, int n, float2 *__restrict__ spec,
                const float2 *__restrict__ twL, const float2 *__restrict__ twN, const MrSchedule sch) {
     extern __shared__ float2 mrsm[];
