@@ -98,11 +98,10 @@ typedef enum { CWT_PAD_POW2 = 0, CWT_PAD_SMOOTH = 1 } cwt_pad_policy;
  * the edges).  CYCLIC: the cyclic result over N = pad_policy(samples), the
  * paper's own computation.  LINEAR: the "same"-mode linear convolution of
  * the signal with the wavelet, by padding to N = pad_policy(samples + R + 1),
- * R = ceil(6.5 a fs) samples the support radius of the widest wavelet
- * (a = n_cycles / (2 pi F); its Gaussian envelope is below 1e-9 of the peak
- * beyond R), so that no wavelet wraps around; the result then equals the
- * linear convolution on [0, samples) up to that envelope tail.  Morlet and
- * Gabor only (CWT_EUNSUPPORTED for GMW, whose support has no closed form). */
+ * R the largest scale's support radius (cwt_support_radius: the envelope is
+ * below 1e-9 of its peak beyond R samples), so that no wavelet wraps around;
+ * the result then equals the linear convolution on [0, samples) up to that
+ * envelope tail.  CWT_EUNSUPPORTED when samples + R + 1 exceeds 2^17. */
 typedef enum { CWT_EDGE_CYCLIC = 0, CWT_EDGE_LINEAR = 1 } cwt_edge_mode;
 
 /* Per-scale normalisation of the wavelet (Section "Precision" compares the
@@ -233,6 +232,18 @@ cwt_status cwt_options_init(cwt_options *opt);
  * supported length, 2^17 under both policies (lengths above 2^14 run each row
  * on a thread-block cluster).  Host-only; no CUDA call. */
 cwt_status cwt_fft_length(int samples, int pad_policy, int *n_fft);
+
+/* Support radius of one scale's wavelet at sampling rate fs, in samples: the
+ * envelope |psi(t)| stays below 1e-9 of its peak for |t| > radius / fs (the
+ * padding of CWT_EDGE_LINEAR).  Morlet and Gabor (Eq. 3, Eq. 4): their
+ * Gaussian envelope, ceil(6.5 a fs), a = n_cycles / (2 pi freq_hz).  GMW
+ * (Eq. 5; n_cycles holds beta, gmw_gamma its gamma): measured from the
+ * spectrum by an FP64 inverse FFT on the host (it scales as 1 / freq_hz).
+ * Writes *radius.  CWT_EINVAL for arguments cwt_plan_create would refuse;
+ * CWT_EUNSUPPORTED when the radius exceeds 2^17 samples.  Host-only; no CUDA
+ * call. */
+cwt_status cwt_support_radius(int wavelet, double freq_hz, double n_cycles, double gmw_gamma, double fs,
+                              int *radius);
 
 /* The schedule the mixed-radix kernels run for a 2,3,5,7-smooth length n_fft
  * that is not a power of two (Section "Fast Fourier transform"), as

@@ -234,16 +234,18 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     if (o.edge_mode != CWT_EDGE_CYCLIC && o.edge_mode != CWT_EDGE_LINEAR) return CWT_EINVAL;
     if (o.normalization != CWT_NORM_UNIT_ENERGY && o.normalization != CWT_NORM_MNE) return CWT_EINVAL;
     if (o.specialize != 0 && o.specialize != 1) return CWT_EINVAL;
-    // linear edges: pad by the widest wavelet's support radius R (Gaussian
-    // envelope below 1e-9 of its peak beyond R samples) so that nothing wraps
+    // linear edges: pad by the widest wavelet's support radius R (envelope
+    // below 1e-9 of its peak beyond R samples, support.cu) so that nothing wraps
     int pad_extra = 0;
     if (o.edge_mode == CWT_EDGE_LINEAR) {
-        if (wavelet == CWT_WAVELET_GMW) return CWT_EUNSUPPORTED;
-        double amax = 0.0;
-        for (int i = 0; i < n_freqs; ++i) amax = std::max(amax, n_cycles[i] / (2.0 * kPi * freqs_hz[i]));
-        const double R = std::ceil(6.5 * amax * fs);
-        if (!(R + 1.0 + samples <= (double)cwtk::kMaxClusterFft)) return CWT_EUNSUPPORTED;
-        pad_extra = (int)R + 1;
+        int R = 0;
+        for (int i = 0; i < n_freqs; ++i) {
+            const int r = cwtk::support_radius(wavelet, freqs_hz[i], n_cycles[i], o.gmw_gamma, fs);
+            if (r < 0) return CWT_EUNSUPPORTED;
+            R = std::max(R, r);
+        }
+        if (!((double)R + 1.0 + samples <= (double)cwtk::kMaxClusterFft)) return CWT_EUNSUPPORTED;
+        pad_extra = R + 1;
     }
     const int min_len = samples + pad_extra;
     int N = 0;

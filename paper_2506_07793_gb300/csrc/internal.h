@@ -213,6 +213,9 @@ cudaError_t launch_fft_cluster(const float2 *in, float2 *out, int log2n, int bat
 bool mr_schedule(int N, MrSchedule *out);
 cudaError_t make_twiddles_n(int N, float2 *tw, cudaStream_t st);
 cudaError_t launch_forward_mr(const cwt_plan_s *p, const void *signal, cudaStream_t st);
+// Support radius in samples of one scale's wavelet (envelope below 1e-9 of its
+// peak beyond it), or -1 past 2^17 samples (support.cu).
+int support_radius(int wavelet, double F, double sig, double gamma, double fs);
 // Plan-time specialization (jit.cu): the fixed-length kernels compiled for
 // schedule s with `rows` rows per CTA (cl = 1), or as the local row of a
 // cluster of cl CTAs, on `device` (cached), or nullptr with the reason in

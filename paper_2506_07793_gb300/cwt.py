@@ -101,6 +101,8 @@ _sig("cwt_options_init", ctypes.c_int, [ctypes.POINTER(cwt_options)])
 _sig("cwt_fft_length", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip])
 _sig("cwt_smooth_schedule", ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip, _ip])
 _sig("cwt_specialize_check", ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t])
+_sig("cwt_support_radius", ctypes.c_int,
+     [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _ip])
 _sig("cwt_plan_create", ctypes.c_int,
      [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int, _dp,
       ctypes.c_int, ctypes.c_uint, ctypes.POINTER(cwt_options)])
@@ -195,6 +197,14 @@ def cwt_smooth_schedule(n_fft):
     _check(_lib.cwt_smooth_schedule(int(n_fft), rad, ctypes.byref(t), pair, ctypes.byref(fixed)),
            "cwt_smooth_schedule")
     return [r for r in rad if r], t.value, (pair[0], pair[1]), fixed.value
+
+
+def cwt_support_radius(wavelet, freq_hz, n_cycles, fs, gmw_gamma=3.0):
+    """Support radius in samples (envelope below 1e-9 of its peak beyond it)."""
+    r = ctypes.c_int(0)
+    _check(_lib.cwt_support_radius(int(wavelet), float(freq_hz), float(n_cycles), float(gmw_gamma),
+                                   float(fs), ctypes.byref(r)), "cwt_support_radius")
+    return r.value
 
 
 def cwt_specialize_check(n_fft):

@@ -196,16 +196,63 @@ def test_option_struct_layout(lib):
     assert so.gmw_gamma == 3.0 and so.max_streams == 32
 
 
-def test_linear_edges_unsupported_for_gmw_and_too_long(lib):
+def test_linear_edges_too_long(lib):
+    """Linear edges pad by the support radius: refused when n + R + 1 exceeds
+    2^17 (0.01 Hz with 7 cycles at 4 kHz; a GMW with beta = 0.3, whose
+    envelope decays only as |t|^-1.3)."""
     o = lib.cwt_options_init()
     o.edge_mode = lib.CWT_EDGE_LINEAR
     with pytest.raises(lib.CWTError) as e:
-        lib.cwt_plan_create(1, 100, 500.0, [10.0], [20.0], lib.CWT_WAVELET_GMW, lib.CWT_OUT_POWER, o)
-    assert e.value.status == lib.CWT_EUNSUPPORTED
-    # 0.01 Hz with 7 cycles at 4 kHz: the support radius alone exceeds 2^17 samples
-    with pytest.raises(lib.CWTError) as e:
         lib.cwt_plan_create(1, 100, 4000.0, [0.01], [7.0], 0, lib.CWT_OUT_POWER, o)
     assert e.value.status == lib.CWT_EUNSUPPORTED
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_plan_create(1, 100, 500.0, [10.0], [0.3], lib.CWT_WAVELET_GMW, lib.CWT_OUT_POWER, o)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kind,F,sig,fs", [(0, 10.0, 7.0, 1000.0), (1, 3.0, 5.0, 250.0), (0, 0.5, 3.0, 2048.0)])
+def test_support_radius_gaussian(lib, kind, F, sig, fs):
+    """Morlet and Gabor: the Gaussian envelope exp(-t^2 / (2 a^2)) is 1e-9 of
+    its peak at a sqrt(2 ln 1e9) = 6.44 a; the radius is ceil(6.5 a fs)."""
+    a = sig / (2 * np.pi * F)
+    assert lib.cwt_support_radius(kind, F, sig, fs) == int(np.ceil(6.5 * a * fs))
+    assert np.exp(-(6.5 * a) ** 2 / (2 * a * a)) < 1e-9 < np.exp(-(6.4 * a) ** 2 / (2 * a * a))
+
+
+@pytest.mark.parametrize("F,beta,gamma,fs", [(10.0, 20.0, 3.0, 1000.0), (40.0, 3.0, 3.0, 500.0),
+                                             (10.0, 20.0, 1.0, 1000.0), (5.0, 17.5, 3.0, 2048.0)])
+def test_support_radius_gmw_against_fourier_quadrature(lib, F, beta, gamma, fs):
+    """GMW (Eq. 5 with U(nu)): the library measures the radius from the
+    spectrum with an FP64 inverse FFT; here |psi(t)| = |int G(nu) e^(2 pi i nu t)
+    dnu| comes from scipy's Fourier-integral quadrature (QAWF).  At the radius
+    the envelope is below 1e-9 of its peak psi(0) = int G, and at 0.9 of it
+    above."""
+    integrate = pytest.importorskip("scipy.integrate")
+    wp = (beta / gamma) ** (1 / gamma)
+
+    def G(nu):
+        return np.exp(beta * np.log(wp * nu / F) - (wp * nu / F) ** gamma) if nu > 0 else 0.0
+
+    def env(t):
+        w = 2 * np.pi * t
+        c = integrate.quad(G, 0, np.inf, weight="cos", wvar=w, limlst=200)[0]
+        s = integrate.quad(G, 0, np.inf, weight="sin", wvar=w, limlst=200)[0]
+        return np.hypot(c, s)
+
+    R = lib.cwt_support_radius(lib.CWT_WAVELET_GMW, F, beta, fs, gamma)
+    peak = integrate.quad(G, 0, np.inf, limit=500)[0]
+    assert env(R / fs) <= 1.05e-9 * peak
+    assert env(0.9 * R / fs) > 1e-9 * peak
+
+
+def test_support_radius_refusals(lib):
+    with pytest.raises(lib.CWTError) as e:
+        lib.cwt_support_radius(lib.CWT_WAVELET_GMW, 10.0, 0.3, 500.0)
+    assert e.value.status == lib.CWT_EUNSUPPORTED
+    for bad in [(5, 10.0, 7.0, 500.0), (0, 0.0, 7.0, 500.0), (0, 300.0, 7.0, 500.0), (0, 10.0, -1.0, 500.0)]:
+        with pytest.raises(lib.CWTError) as e:
+            lib.cwt_support_radius(*bad)
+        assert e.value.status == lib.CWT_EINVAL
 
 
 @pytest.mark.parametrize("what", ["tc_fp16", "tc_bf16", "too_long", "odd_smooth", "unsplit_smooth",

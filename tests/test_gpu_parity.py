@@ -465,6 +465,9 @@ LINEAR = [
     (1, 3000, 1000.0, [5.0, 90.0], [7.0, 7.0], dict(pad="smooth")),
     (2, 300, 200.0, [9.0, 50.0], [5.0, 7.0], dict(wavelet="gabor", dtype="f64")),
     (1, 20000, 1000.0, [2.0, 60.0], [5.0, 7.0], dict(pad="smooth")),  # N = 22680 on a cluster of 2
+    # GMW (Eq. 5; the cycles column holds beta): support radius measured by the library
+    (2, 800, 500.0, [6.0, 60.0], [20.0, 40.0], dict(wavelet="gmw")),
+    (1, 600, 250.0, [3.0, 40.0], [8.0, 60.0], dict(wavelet="gmw", gmw_gamma=2.0, pad="smooth")),
 ]
 
 
@@ -475,31 +478,44 @@ def _support_radius(fs, freqs, cycles):
 
 @pytest.mark.parametrize("case", range(len(LINEAR)))
 def test_linear_edges_equal_linear_convolution(lib, case):
-    """Linear ("same"-mode) edges: N >= n + R + 1, parity with the oracle at
-    that N, and agreement with a direct linear convolution of the signal with
-    the sampled wavelet (normalised like the oracle's) at every output,
-    edges included."""
+    """Linear ("same"-mode) edges: N >= n + R + 1 with R the largest scale's
+    support radius, parity with the oracle at that N, and agreement with a
+    direct linear convolution of the signal with the sampled wavelet
+    (normalised like the oracle's) at every output, edges included.  Morlet
+    and Gabor take their Gaussian closed form; the GMW, which has none, the
+    oracle's periodised wavelet over a period much longer than its support."""
     C, n, fs, freqs, cycles, kw = LINEAR[case]
     kw = dict(kw)
     dtype = kw.pop("dtype", "f32")
     wavelet = kw.pop("wavelet", "morlet")
+    gamma = kw.get("gmw_gamma", 3.0)
     x = eeg(990 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
     res, N = run_gpu(lib, x, fs, freqs, cycles, ("complex", "power"), dtype=dtype, wavelet=wavelet,
                      edge="linear", **kw)
-    R = _support_radius(fs, freqs, cycles)
-    assert N >= n + R + 1
+    kind = {"morlet": lib.CWT_WAVELET_MORLET, "gabor": lib.CWT_WAVELET_GABOR, "gmw": lib.CWT_WAVELET_GMW}[wavelet]
+    radii = [lib.cwt_support_radius(kind, F, sg, fs, gamma) for F, sg in zip(freqs, cycles)]
+    if wavelet != "gmw":
+        assert max(radii) == _support_radius(fs, freqs, cycles)
+    assert N >= n + max(radii) + 1
     d = kw.get("decimation", 1)
-    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=d, wavelet=wavelet)
+    ref = oracle.cwt(x.astype(np.float64), N, fs, freqs, cycles, decimation=d, wavelet=wavelet, gamma=gamma)
     check(res, ref)
     # direct linear convolution with the unperiodised sampled wavelet
     lin = np.empty_like(ref)
     for s, (F, sg) in enumerate(zip(freqs, cycles)):
-        a = sg / (2 * np.pi * F)
-        Rs = int(np.ceil(40 * a * fs))
-        tau = np.arange(-Rs, Rs + 1) / fs
-        kappa = 0.0 if wavelet == "gabor" else np.exp(-0.5 * sg * sg)
-        psi = np.exp(-tau ** 2 / (2 * a * a)) * (np.exp(2j * np.pi * F * tau) - kappa)
-        psi /= np.sqrt(np.sum(np.abs(oracle.periodised_wavelet(F, sg, fs, N, wavelet=wavelet)) ** 2))
+        if wavelet == "gmw":
+            Rs = int(1.5 * radii[s]) + 1
+            Nbig = 1 << int(np.ceil(np.log2(8 * Rs)))
+            big = oracle.periodised_wavelet(F, sg, fs, Nbig, wavelet="gmw", gamma=gamma)
+            psi = big[np.arange(-Rs, Rs + 1) % Nbig]
+        else:
+            a = sg / (2 * np.pi * F)
+            Rs = int(np.ceil(40 * a * fs))
+            tau = np.arange(-Rs, Rs + 1) / fs
+            kappa = 0.0 if wavelet == "gabor" else np.exp(-0.5 * sg * sg)
+            psi = np.exp(-tau ** 2 / (2 * a * a)) * (np.exp(2j * np.pi * F * tau) - kappa)
+        psi = psi / np.sqrt(np.sum(np.abs(oracle.periodised_wavelet(F, sg, fs, N, wavelet=wavelet,
+                                                                     gamma=gamma)) ** 2))
         for c in range(C):
             lin[c, s] = np.convolve(x[c].astype(np.float64), psi)[Rs:Rs + n][::d]
     check({"complex": res["complex"]}, lin)
