@@ -906,9 +906,10 @@ def run_sweep(args):
     two and to the paper's 2,3,5,7-smooth length.  `device_us` is one
     cwt_execute on resident buffers (CUDA events, mean of --steps calls after
     --warmup); `e2e_us` is cwt_execute_host from pinned host memory, copies
-    included.  `smooth_specialized` is the smooth padding with
-    cwt_options.specialize (the fixed-length kernels compiled for the length
-    at plan creation; `plan_ms` includes that compile, cached per process).
+    included.  `smooth_tuned` is the smooth padding with
+    cwt_options.specialize = 2 (fixed-length kernels compiled at plan creation
+    for candidate schedules of the length, the fastest on the plan's rows
+    kept; `plan_ms` includes the compiles, cached per process).
     Bank generation: 61 scales, 1 s at 2048 Hz (N = 2048), Morlet and the GMW
     of Fig. 1 (beta 17.5, gamma 3), FP64 on the GPU."""
     import torch
@@ -931,10 +932,10 @@ def run_sweep(args):
         h_in = torch.from_numpy(x_host).pin_memory()
         h_out = torch.empty((C, S, n), dtype=torch.complex64).pin_memory()
         pt = {"samples": n}
-        for pad in ("pow2", "smooth", "smooth_specialized"):
+        for pad in ("pow2", "smooth", "smooth_tuned"):
             o = cw.cwt_options_init()
             o.pad_policy = cw.CWT_PAD_POW2 if pad == "pow2" else cw.CWT_PAD_SMOOTH
-            o.specialize = 1 if pad == "smooth_specialized" else 0
+            o.specialize = 2 if pad == "smooth_tuned" else 0
             t_plan = time.perf_counter()
             plan = cw.cwt_plan_create(C, n, fs, freqs, cycles, cw.CWT_WAVELET_MORLET,
                                       cw.CWT_OUT_COMPLEX, o)

@@ -180,6 +180,11 @@ typedef struct {
                           transform");
                           if that fails the plan runs the runtime-schedule kernels
                           (cwt_plan_info.specialized, cwt_plan_last_error).
+                          2: for such an N that one CTA holds, compile up to six
+                          candidate schedules (the scheduler's, then the cost
+                          model's two cheapest radix sets in each pass order)
+                          and keep the fastest on the plan's own rows (a few
+                          seconds; cwt_plan_info.radices reports the winner).
                           0 (default): never compile at plan creation */
     int reserved[6];
 } cwt_options;
@@ -214,7 +219,8 @@ typedef struct {
                                inverse_length / cluster points (powers of two: 2, 4, 8);
                                radices then describe those points' passes */
     int specialized;        /* 1 when the plan runs kernels compiled at its creation
-                               (cwt_options.specialize) */
+                               (cwt_options.specialize), 2 when they were chosen among
+                               candidate schedules by timing (specialize = 2) */
 } cwt_plan_info_t;
 
 /* Human-readable name of a status.  Never NULL. */

@@ -233,7 +233,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     if (o.precision != CWT_PREC_FP32 && !tc) return CWT_EINVAL;
     if (o.edge_mode != CWT_EDGE_CYCLIC && o.edge_mode != CWT_EDGE_LINEAR) return CWT_EINVAL;
     if (o.normalization != CWT_NORM_UNIT_ENERGY && o.normalization != CWT_NORM_MNE) return CWT_EINVAL;
-    if (o.specialize != 0 && o.specialize != 1) return CWT_EINVAL;
+    if (o.specialize < 0 || o.specialize > 2) return CWT_EINVAL;
     // linear edges: pad by the widest wavelet's support radius R (envelope
     // below 1e-9 of its peak beyond R samples, support.cu) so that nothing wraps
     int pad_extra = 0;
@@ -327,7 +327,8 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             p->bytes += sizeof(float2) * (size_t)NL;
         }
     }
-    if (e == cudaSuccess && o.specialize && p->mr &&
+    const bool tune = o.specialize == 2 && p->mr && p->cl == 1 && p->sch.fixed < 0;
+    if (e == cudaSuccess && o.specialize && !tune && p->mr &&
         (p->cl == 1 ? p->sch.fixed < 0 : p->sch.fixed_cl < 0)) {
         // a failed compile or load is not a plan error: the runtime-schedule kernels run
         std::string log;
@@ -342,6 +343,15 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         p->bytes += sizeof(float) * ((size_t)channels + n_freqs);
         if (e == cudaSuccess) e = cwtk::launch_tc_wl1(p, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess && tune) {
+        // candidates timed on the plan's rows once the bank is in place; a
+        // failure leaves the plan on the runtime-schedule kernels
+        e = cudaStreamSynchronize(st);
+        std::string log;
+        if (e == cudaSuccess) p->jit = cwtk::jit_tune(p, st, &log);
+        p->tuned = p->jit != nullptr;
+        if (!p->jit) p->last_error = log;
     }
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) {
@@ -405,7 +415,7 @@ cwt_status cwt_plan_info(cwt_plan p, cwt_plan_info_t *info) {
     info->precision = p->precision;
     info->cluster = p->mr ? p->cl : (p->M > cwtk::kMaxFft ? p->M / cwtk::kMaxFft : 1);
     if (p->mr) describe_schedule(p->sch, p->cl, info->radices, info->inlined_pair, &info->fixed_kernel);
-    info->specialized = p->jit != nullptr;
+    info->specialized = p->jit == nullptr ? 0 : p->tuned ? 2 : 1;
     if (p->jit) {  // the compiled-at-creation kernels are fixed-length ones
         info->fixed_kernel = 1;
         info->inlined_pair[0] = info->inlined_pair[1] = 0;

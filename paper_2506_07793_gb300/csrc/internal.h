@@ -82,6 +82,7 @@ struct cwt_plan_s {
     cwtk::MrSchedule sch{};     // their pass schedule (of N / cl points)
     int cl = 1;                 // smooth N above 16384: CTAs per row (a cluster), N = cl * sch.N
     cwtk::JitKernels *jit = nullptr;  // kernels compiled at plan creation for sch (jit.cu; shared, cached)
+    bool tuned = false;               // jit chosen by timing candidate schedules (specialize = 2)
     float2 *twN = nullptr;      // exp(2 pi i m / N), m < N (mixed-radix plans only)
     float2 *twL = nullptr;      // cl > 1: exp(2 pi i m / NL), m < NL = N / cl
     float *bank = nullptr;    // [S][N] W_s[k] / N (real)
@@ -222,6 +223,13 @@ int support_radius(int wavelet, double F, double sig, double gamma, double fs);
 // *log; the same compile for sm_103a without a device, as a check.
 JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::string *log);
 bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log);
+// cwt_options.specialize = 2: the fixed-length kernels of up to six candidate
+// schedules (mr_schedule_candidates), each timed on the plan's rows; the
+// fastest, with p->sch set to its schedule (jit.cu).
+JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log);
+// The scheduler's schedule of N first, then the cost model's two cheapest
+// radix sets in each of their pass orders; returns how many (smooth.cu).
+int mr_schedule_candidates(int N, MrSchedule *out, int max_out);
 // Rows per CTA of the runtime-schedule kernels for total_rows rows (smooth.cu).
 int mr_launch_rows(const MrSchedule &sch, int total_rows);
 // Smooth lengths above 16384 on clusters (smooth_cluster.cu).

@@ -28,6 +28,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "smooth_cluster.cuh"
@@ -176,6 +177,25 @@ std::string schedule_key(const MrSchedule &s, int rows, int cl) {
 
 }  // namespace
 
+namespace {
+
+// The compiled module of (s, rows, cl) for arch in g_cubins, compiling it
+// (without holding the lock, so that several compile at once) when absent.
+bool jit_binary(const MrSchedule &s, int rows, int cl, const std::string &arch, std::string *log) {
+    const std::string key = arch + ":" + schedule_key(s, rows, cl);
+    {
+        std::lock_guard<std::mutex> lock(g_jit_mu);
+        if (g_cubins.count(key)) return true;
+    }
+    JitBinary b;
+    if (!compile(s, rows, cl, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return false;
+    std::lock_guard<std::mutex> lock(g_jit_mu);
+    g_cubins.emplace(key, std::move(b));
+    return true;
+}
+
+}  // namespace
+
 bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log) {
     std::vector<char> cubin;
     std::string a, b;
@@ -201,16 +221,16 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::
     const std::string arch = "sm_" + std::to_string(major * 10 + minor) + "a";
     const std::string skey = schedule_key(s, rows, cl);
     const std::string mkey = std::to_string(device) + ":" + skey;
+    {
+        std::lock_guard<std::mutex> lock(g_jit_mu);
+        auto it = g_modules.find(mkey);
+        if (it != g_modules.end()) return it->second;
+    }
+    if (!jit_binary(s, rows, cl, arch, log)) return nullptr;
     std::lock_guard<std::mutex> lock(g_jit_mu);
     auto it = g_modules.find(mkey);
     if (it != g_modules.end()) return it->second;
-    auto bin = g_cubins.find(arch + ":" + skey);
-    if (bin == g_cubins.end()) {
-        JitBinary b;
-        if (!compile(s, rows, cl, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return nullptr;
-        bin = g_cubins.emplace(arch + ":" + skey, std::move(b)).first;
-    }
-    const JitBinary &b = bin->second;
+    const JitBinary &b = g_cubins.find(arch + ":" + skey)->second;
     // the runtime API has made the device's primary context current
     const Driver &drv = driver();
     if (!drv.ok) {
@@ -240,14 +260,21 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::
 #endif
 }
 
-cudaError_t jit_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
-    const JitKernels *k = p->jit;
+namespace {
+
+cudaError_t sb_launch_k(const JitKernels *k, const MrArgs &a, cudaStream_t st) {
     MrArgs args = a;
     void *params[] = {&args};
     const unsigned grid = (unsigned)((a.total_rows + k->rows - 1) / k->rows);
     const CUresult r = driver().launch_kernel(k->sb, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
                                               (CUstream)st, params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace
+
+cudaError_t jit_sb_launch(const cwt_plan_s *p, const MrArgs &a, cudaStream_t st) {
+    return sb_launch_k(p->jit, a, st);
 }
 
 cudaError_t jit_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st) {
@@ -281,6 +308,103 @@ cudaError_t jit_cl_sb_launch(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_
     const CUresult r = driver().launch_kernel(k->sb, grid, 1, 1, (unsigned)k->threads, 1, 1, (unsigned)k->smem,
                                               (CUstream)st, params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
+#ifdef CWT_BOUNDS_CHECK
+    (void)p;
+    (void)st;
+    *log = "plan-time specialization is off in the bounds-checked build";
+    return nullptr;
+#else
+    constexpr int kMaxCandidates = 6;
+    MrSchedule cand[kMaxCandidates];
+    const int n = mr_schedule_candidates(p->N, cand, kMaxCandidates);
+    if (n < 1) {
+        *log = "no schedule to tune";
+        return nullptr;
+    }
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p->device) != cudaSuccess) {
+        *log = "compute capability query failed";
+        return nullptr;
+    }
+    const std::string arch = "sm_" + std::to_string(major * 10 + minor) + "a";
+    const int total = p->C * p->S;
+    int rows[kMaxCandidates];
+    for (int i = 0; i < n; ++i) rows[i] = mr_launch_rows(cand[i], total);
+    // compile the candidates at once (NVRTC is thread-safe), then load them
+    {
+        std::vector<std::thread> pool;
+        std::vector<std::string> logs((size_t)n);
+        for (int i = 0; i < n; ++i)
+            pool.emplace_back([&, i] { jit_binary(cand[i], rows[i], 1, arch, &logs[(size_t)i]); });
+        for (auto &t : pool) t.join();
+    }
+    JitKernels *k[kMaxCandidates] = {};
+    for (int i = 0; i < n; ++i) {
+        std::string lg;
+        k[i] = jit_kernels(cand[i], rows[i], 1, p->device, &lg);
+        if (!k[i] && log->empty()) *log = lg;
+    }
+    // time each on the plan's own rows (a bounded slice) into scratch outputs
+    const int trows = total < 2048 ? total : 2048;
+    const size_t cells = (size_t)trows * (size_t)p->n_out;
+    const size_t esz = p->io == CWT_DTYPE_F64 ? 8 : 4;
+    void *oc = nullptr, *op = nullptr, *oph = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (p->outputs & CWT_OUT_COMPLEX) e = dmalloc(&oc, cells * 2 * esz);
+    if (e == cudaSuccess && (p->outputs & CWT_OUT_POWER)) e = dmalloc(&op, cells * esz);
+    if (e == cudaSuccess && (p->outputs & CWT_OUT_PHASE)) e = dmalloc(&oph, cells * esz);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->spec, 0, sizeof(float2) * (size_t)p->C * p->N, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    MrArgs a;
+    a.spec = p->spec;
+    a.bank = p->bank;
+    a.band = p->band;
+    a.twN = p->twN;
+    a.out_c = oc;
+    a.out_p = op;
+    a.out_ph = oph;
+    a.S = p->S;
+    a.n_out = p->n_out;
+    a.sub = p->d;
+    a.total_rows = trows;
+    a.f64 = p->io == CWT_DTYPE_F64;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        if (!k[i]) continue;
+        float ms = 0.f, lo = -1.f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // rep 0 warms up
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = sb_launch_k(k[i], a, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && (lo < 0.f || ms < lo)) lo = ms;
+        }
+        if (e == cudaSuccess && (best < 0 || lo < best_ms)) {
+            best = i;
+            best_ms = lo;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(oc);
+    cudaFree(op);
+    cudaFree(oph);
+    if (e != cudaSuccess) {
+        *log = std::string("timing the tuning candidates failed: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    if (best < 0) return nullptr;
+    p->sch = cand[best];
+    return k[best];
+#endif
 }
 
 }  // namespace cwtk

@@ -149,6 +149,89 @@ constexpr double kFastPairGain = 1.3;
 
 }  // namespace
 
+namespace {
+
+// The schedule of N with passes `radices` (in order) and T threads per row.
+MrSchedule build_schedule(int N, const std::vector<int> &radices, int T, int fast) {
+    MrSchedule s{};
+    s.N = N;
+    s.T = T;
+    s.fast = fast;
+    s.np = (int)radices.size();
+    int Ns = 1;
+    for (int q = 0; q < s.np; ++q) {
+        const int R = radices[q];
+        s.p[q].R = R;
+        s.p[q].G = (N / R + T - 1) / T;
+        s.p[q].Ns = Ns;
+        s.p[q].mag = mr_magic(Ns);
+        s.p[q].tws = N / (Ns * R);
+        Ns *= R;
+    }
+    s.mag0 = mr_magic(N / s.p[0].R);
+    s.fixed = -1;
+    s.fixed_cl = -1;
+    return s;
+}
+
+// Whole warps of 128 for rows of more than 128 threads (see mr_schedule).
+int round_threads(int T) { return T > 128 ? std::min(kMrThreads, (T + 127) / 128 * 128) : T; }
+
+}  // namespace
+
+int mr_schedule_candidates(int N, MrSchedule *out, int max_out) {
+    MrSchedule first;
+    if (max_out < 1 || !mr_schedule(N, &first)) return 0;
+    out[0] = first;
+    out[0].fast = -1;
+    int n = 1;
+    // the cheapest radix multisets under the cost model, each in its distinct pass orders
+    std::vector<std::vector<int>> sets;
+    std::vector<int> cur;
+    const std::vector<int> all(std::begin(kRadixSet), std::end(kRadixSet));
+    enumerate(N, 2, cur, sets, all);
+    std::vector<std::pair<double, std::vector<int>>> ranked;
+    for (const std::vector<int> &rs : sets) {
+        int Tmin = 1;
+        for (int R : rs) {
+            const int gm = std::max(1, kMrPoints / R);
+            Tmin = std::max(Tmin, (N / R + gm - 1) / gm);
+        }
+        if (Tmin > kMrThreads) continue;
+        double best = -1.0;
+        for (int T = Tmin; T <= kMrThreads; ++T) {
+            double c = kPassOverhead * (double)rs.size();
+            for (int R : rs) c += (double)((N / R + T - 1) / T) * butterfly_cost(R);
+            c *= T;
+            if (best < 0 || c < best) best = c;
+        }
+        ranked.push_back({best, rs});
+    }
+    std::sort(ranked.begin(), ranked.end(),
+              [](const std::pair<double, std::vector<int>> &a, const std::pair<double, std::vector<int>> &b) {
+                  return a.first < b.first;
+              });
+    for (size_t m = 0; m < ranked.size() && m < 2 && n < max_out; ++m) {
+        std::vector<int> order = ranked[m].second;
+        std::sort(order.begin(), order.end());
+        do {
+            int Tmin = 1;
+            for (int R : order) {
+                const int gm = std::max(1, kMrPoints / R);
+                Tmin = std::max(Tmin, (N / R + gm - 1) / gm);
+            }
+            const MrSchedule c = build_schedule(N, order, round_threads(Tmin), -1);
+            bool seen = false;
+            for (int i = 0; i < n && !seen; ++i) {
+                seen = out[i].np == c.np && out[i].T == c.T;
+                for (int q = 0; seen && q < c.np; ++q) seen = out[i].p[q].R == c.p[q].R;
+            }
+            if (!seen) out[n++] = c;
+        } while (n < max_out && std::next_permutation(order.begin(), order.end()));
+    }
+    return n;
+}
+
 bool mr_schedule(int N, MrSchedule *out) {
     if (N < kMinFft || N > kMaxFft) return false;
     int x = N;
@@ -176,24 +259,8 @@ bool mr_schedule(int N, MrSchedule *out) {
     // N = 10000 at T = 400 -> 512, 354 -> 342 us; N = 5000 at 209 -> 256,
     // 111 -> 106 us).  A larger T never raises a pass's butterflies per thread.
     if (best.T > 128) best.T = std::min(kMrThreads, (best.T + 127) / 128 * 128);
-    MrSchedule s{};
-    s.N = N;
-    s.T = best.T;
-    s.fast = fast;
-    s.np = (int)best.radices.size();
-    int Ns = 1;
-    for (int q = 0; q < s.np; ++q) {
-        const int R = best.radices[q];
-        s.p[q].R = R;
-        s.p[q].G = (N / R + best.T - 1) / best.T;
-        s.p[q].Ns = Ns;
-        s.p[q].mag = mr_magic(Ns);
-        s.p[q].tws = N / (Ns * R);
-        Ns *= R;
-    }
-    s.mag0 = mr_magic(N / s.p[0].R);
+    MrSchedule s = build_schedule(N, best.radices, best.T, fast);
     s.fixed = mr_fixed_index(s);
-    s.fixed_cl = -1;  // set by mr_cluster_split
     *out = s;
     return true;
 }

@@ -357,7 +357,7 @@ class CWT:
                  specialize=False):
         opt = cwt_options_init()
         opt.normalization = {"unit": CWT_NORM_UNIT_ENERGY, "mne": CWT_NORM_MNE}[normalization]
-        opt.specialize = 1 if specialize else 0
+        opt.specialize = int(specialize)  # False / True / 2 (tune)
         opt.precision = {"fp32": CWT_PREC_FP32, "tc_fp16": CWT_PREC_TC_FP16,
                          "tc_bf16": CWT_PREC_TC_BF16}[precision]
         opt.decimation = int(decimation)

@@ -95,3 +95,17 @@ def test_specialize_leaves_compiled_in_paths(lib, n, pad):
     t = lib.CWT(1, n, 1000.0, [10.0, 50.0], [7.0, 7.0], outputs=("power",), pad=pad, specialize=True)
     assert t.info.specialized == 0
     t.close()
+
+
+@pytest.mark.parametrize("case", [1, 3, 4])
+def test_tuned_specialization_parity(lib, case):
+    """specialize = 2: candidate schedules compiled and timed at plan creation,
+    the fastest kept (its radices reported); parity with the oracle."""
+    n, C, fs, freqs, cycles, dtype, d = CASES[case]
+    x = eeg(1700 + case, C, n, fs, np.float64 if dtype == "f64" else np.float32)
+    res, info = _run(lib, x, n, fs, freqs, cycles, dtype, d, 2)
+    assert info.specialized == 2 and info.fixed_kernel == 1
+    assert int(np.prod([r for r in info.radices if r])) == n
+    ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
+    assert complex_err(res["complex"], ref).max() <= FP32_TOL
+    assert power_err(res["power"], ref).max() <= FP32_TOL
