@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -348,10 +349,15 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
         k[i] = jit_kernels(cand[i], rows[i], 1, p->device, &lg);
         if (!k[i] && log->empty()) *log = lg;
     }
-    // time each on the plan's own rows (a bounded slice) into scratch outputs
-    const int trows = total < 2048 ? total : 2048;
-    const size_t cells = (size_t)trows * (size_t)p->n_out;
+    // time each on the plan's own rows (all of them, or as many as 256 MB of
+    // scratch outputs hold)
     const size_t esz = p->io == CWT_DTYPE_F64 ? 8 : 4;
+    const size_t row_bytes = (size_t)p->n_out * esz *
+                             (((p->outputs & CWT_OUT_COMPLEX) ? 2 : 0) + ((p->outputs & CWT_OUT_POWER) ? 1 : 0) +
+                              ((p->outputs & CWT_OUT_PHASE) ? 1 : 0));
+    const size_t cap = row_bytes ? ((size_t)256 << 20) / row_bytes : (size_t)total;
+    const int trows = (int)std::max<size_t>(1, std::min<size_t>((size_t)total, cap));
+    const size_t cells = (size_t)trows * (size_t)p->n_out;
     void *oc = nullptr, *op = nullptr, *oph = nullptr;
     cudaError_t e = cudaSuccess;
     if (p->outputs & CWT_OUT_COMPLEX) e = dmalloc(&oc, cells * 2 * esz);
@@ -374,20 +380,23 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     a.sub = p->d;
     a.total_rows = trows;
     a.f64 = p->io == CWT_DTYPE_F64;
-    int best = -1;
+    // candidate -1: the length's compiled-in fixed-length kernel, when it has one
+    int best = -2;
     float best_ms = 0.f;
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        if (!k[i]) continue;
+    for (int i = p->sch.fixed >= 0 ? -1 : 0; i < n && e == cudaSuccess; ++i) {
+        if (i >= 0 && !k[i]) continue;
         float ms = 0.f, lo = -1.f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // rep 0 warms up
             e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = sb_launch_k(k[i], a, st);
+            if (e == cudaSuccess) e = i >= 0 ? sb_launch_k(k[i], a, st) : mr_fixed_sb_launch(p, a, st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0 && (lo < 0.f || ms < lo)) lo = ms;
         }
-        if (e == cudaSuccess && (best < 0 || lo < best_ms)) {
+        // a candidate displaces the compiled-in kernel only when 2% faster
+        const float margin = best == -1 ? 0.98f : 1.0f;
+        if (e == cudaSuccess && (best == -2 || lo < margin * best_ms)) {
             best = i;
             best_ms = lo;
         }
@@ -399,6 +408,10 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     cudaFree(oph);
     if (e != cudaSuccess) {
         *log = std::string("timing the tuning candidates failed: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    if (best == -1) {  // the compiled-in kernel is the fastest: the plan keeps it
+        log->clear();
         return nullptr;
     }
     if (best < 0) return nullptr;

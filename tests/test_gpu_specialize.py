@@ -109,3 +109,15 @@ def test_tuned_specialization_parity(lib, case):
     ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
     assert complex_err(res["complex"], ref).max() <= FP32_TOL
     assert power_err(res["power"], ref).max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("n", [1000, 10000])
+def test_tuning_competes_with_compiled_in_kernels(lib, n):
+    """specialize = 2 on a length with a compiled-in kernel: the compiled-in
+    kernel competes with the candidates; whichever runs, parity holds."""
+    fs, freqs, cycles = 1000.0, [3.0, 40.0, 300.0], [5.0, 7.0, 10.0]
+    x = eeg(1800 + n, 2, n, fs, np.float32)
+    res, info = _run(lib, x, n, fs, freqs, cycles, "f32", 1, 2)
+    assert info.specialized in (0, 2) and info.fixed_kernel == 1
+    ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles)
+    assert power_err(res["power"], ref).max() <= FP32_TOL
