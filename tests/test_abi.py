@@ -147,7 +147,7 @@ BAD = [
     dict(wavelet=2, gamma=0.0), dict(wavelet=2, gamma=-3.0), dict(wavelet=2, gamma=float("nan")),
     dict(wavelet=2, gamma=65.0), dict(wavelet=2, n_cycles=[20.0, 1001.0]), dict(edge=2), dict(edge=-1),
     dict(edge=1, fft_length=128),  # linear edges need N >= n + R + 1 (here 100 + 363 + 1)
-    dict(norm=2), dict(norm=-1), dict(specialize=2), dict(specialize=-1),
+    dict(norm=2), dict(norm=-1), dict(specialize=3), dict(specialize=-1),
     # a carrier far below the first DFT bin: 1.5 Hz with sigma 7 in a 32-point
     # window at 500 Hz (first bin 15.6 Hz) has a spectrum below 1e-150 on every
     # bin, so its unit-energy normalisation would underflow
