@@ -91,39 +91,42 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
 }
 
 // Fixed-length kernels (index = MrSchedule::fixed): index, N, T, rows per CTA,
-// CTAs per SM for the register budget, the radices in the scheduler's order.
-// Whole seconds of EEG at 250 / 500 / 1000 Hz; the CTAs per SM were measured
-// per length (several CTAs per SM hide one row's pass barriers behind the
-// others' work, fewer leave more registers per thread).  The kernels of list A are in smooth_fixed.cu, of list B in
-// smooth_fixed_b.cu (two translation units that compile in parallel).
+// CTAs per SM for the register budget, the radices in the scheduler's order
+// (for most of them the pass order the plan-time tuner measured fastest,
+// smooth.cu's kMeasuredOrders).  Whole seconds of EEG at 250 / 500 / 1000 Hz;
+// rows and CTAs per SM measured per length, or those the tuner ran with
+// (several CTAs per SM hide one row's pass barriers behind the others' work,
+// fewer leave more registers per thread).  The kernels of list A are in
+// smooth_fixed.cu, of list B in smooth_fixed_b.cu (two translation units that
+// compile in parallel).
 #define CWT_MR_FIXED_A(X)                     \
     X(0, 10000, 512, 1, 2, 16, 25, 25)        \
-    X(1, 8000, 512, 1, 2, 20, 20, 20)         \
-    X(2, 5000, 256, 1, 4, 8, 25, 25)          \
-    X(3, 4000, 256, 1, 4, 10, 20, 20)         \
-    X(4, 2500, 125, 2, 3, 10, 10, 25)         \
-    X(5, 2000, 100, 2, 4, 10, 10, 20)         \
+    X(1, 8000, 512, 1, 2, 16, 25, 20)         \
+    X(2, 5000, 256, 1, 4, 20, 10, 25)         \
+    X(3, 4000, 256, 1, 4, 16, 10, 25)         \
+    X(4, 2500, 100, 2, 4, 25, 10, 10)         \
+    X(5, 2000, 100, 2, 4, 20, 10, 10)         \
     X(6, 1000, 50, 5, 4, 10, 10, 10)          \
     X(7, 500, 25, 10, 3, 20, 25)              \
     X(8, 12000, 512, 1, 2, 16, 25, 30)        \
-    X(9, 7500, 384, 1, 2, 12, 25, 25)         \
-    X(10, 6000, 256, 1, 4, 10, 24, 25)        \
+    X(9, 7500, 384, 1, 2, 25, 10, 30)         \
+    X(10, 6000, 256, 1, 4, 24, 10, 25)        \
     X(11, 15000, 512, 1, 1, 10, 10, 10, 15)   \
-    X(12, 3000, 100, 2, 3, 10, 10, 30)        \
-    X(13, 9000, 384, 1, 2, 10, 30, 30)        \
+    X(12, 3000, 125, 2, 4, 24, 5, 25)         \
+    X(13, 9000, 384, 1, 2, 24, 15, 25)        \
     X(14, 1500, 50, 4, 4, 10, 10, 15)
 #define CWT_MR_FIXED_B(X)                     \
-    X(15, 14000, 512, 1, 1, 10, 10, 10, 14)   \
-    X(16, 13500, 512, 1, 1, 15, 30, 30)       \
-    X(17, 12500, 512, 1, 2, 5, 10, 10, 25)    \
-    X(18, 10500, 512, 1, 2, 15, 25, 28)       \
-    X(19, 7000, 384, 1, 2, 10, 25, 28)        \
+    X(15, 14000, 512, 1, 1, 14, 10, 10, 10)   \
+    X(16, 13500, 512, 1, 1, 6, 10, 15, 15)    \
+    X(17, 12500, 512, 1, 2, 10, 10, 5, 25)    \
+    X(18, 10500, 512, 1, 2, 28, 15, 25)       \
+    X(19, 7000, 384, 1, 2, 28, 10, 25)        \
     X(20, 4500, 256, 1, 3, 10, 15, 30)        \
-    X(21, 3750, 256, 1, 4, 6, 25, 25)         \
-    X(22, 3500, 256, 1, 3, 5, 25, 28)         \
+    X(21, 3750, 256, 1, 4, 25, 6, 25)         \
+    X(22, 3500, 256, 1, 4, 28, 5, 25)         \
     X(23, 2250, 75, 2, 3, 10, 15, 15)         \
-    X(24, 1750, 70, 2, 4, 5, 14, 25)          \
-    X(25, 1250, 50, 4, 4, 5, 10, 25)          \
+    X(24, 1750, 70, 3, 4, 14, 5, 25)          \
+    X(25, 1250, 50, 5, 4, 25, 10, 5)          \
     X(26, 750, 30, 8, 3, 25, 30)
 #define CWT_MR_FIXED(X) CWT_MR_FIXED_A(X) CWT_MR_FIXED_B(X)
 

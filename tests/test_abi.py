@@ -305,31 +305,31 @@ def test_null_plan_calls(lib):
 # the forward FFT) for each of them, on the host.
 FIXED_SCHEDULES = {
     10000: ([16, 25, 25], 512, (16, 25)),
-    8000: ([20, 20, 20], 512, (20, 25)),
-    5000: ([8, 25, 25], 256, (8, 25)),
-    4000: ([10, 20, 20], 256, (10, 20)),
-    2500: ([10, 10, 25], 125, (10, 25)),
-    2000: ([10, 10, 20], 100, (10, 20)),
+    8000: ([16, 25, 20], 512, (0, 0)),
+    5000: ([20, 10, 25], 256, (0, 0)),
+    4000: ([16, 10, 25], 256, (0, 0)),
+    2500: ([25, 10, 10], 100, (0, 0)),
+    2000: ([20, 10, 10], 100, (0, 0)),
     1000: ([10, 10, 10], 50, (10, 16)),
     500: ([20, 25], 25, (20, 25)),
     15000: ([10, 10, 10, 15], 512, (0, 0)),
     12000: ([16, 25, 30], 512, (0, 0)),
-    9000: ([10, 30, 30], 384, (0, 0)),
-    7500: ([12, 25, 25], 384, (0, 0)),
-    6000: ([10, 24, 25], 256, (0, 0)),
-    3000: ([10, 10, 30], 100, (0, 0)),
+    9000: ([24, 15, 25], 384, (0, 0)),
+    7500: ([25, 10, 30], 384, (0, 0)),
+    6000: ([24, 10, 25], 256, (0, 0)),
+    3000: ([24, 5, 25], 125, (0, 0)),
     1500: ([10, 10, 15], 50, (0, 0)),
-    14000: ([10, 10, 10, 14], 512, (0, 0)),
-    13500: ([15, 30, 30], 512, (0, 0)),
-    12500: ([5, 10, 10, 25], 512, (0, 0)),
-    10500: ([15, 25, 28], 512, (0, 0)),
-    7000: ([10, 25, 28], 384, (0, 0)),
+    14000: ([14, 10, 10, 10], 512, (0, 0)),
+    13500: ([6, 10, 15, 15], 512, (0, 0)),
+    12500: ([10, 10, 5, 25], 512, (0, 0)),
+    10500: ([28, 15, 25], 512, (0, 0)),
+    7000: ([28, 10, 25], 384, (0, 0)),
     4500: ([10, 15, 30], 256, (0, 0)),
-    3750: ([6, 25, 25], 256, (0, 0)),
-    3500: ([5, 25, 28], 256, (0, 0)),
+    3750: ([25, 6, 25], 256, (0, 0)),
+    3500: ([28, 5, 25], 256, (0, 0)),
     2250: ([10, 15, 15], 75, (0, 0)),
-    1750: ([5, 14, 25], 70, (0, 0)),
-    1250: ([5, 10, 25], 50, (0, 0)),
+    1750: ([14, 5, 25], 70, (0, 0)),
+    1250: ([25, 10, 5], 50, (0, 0)),
     750: ([25, 30], 30, (0, 0)),
 }
 
