@@ -327,7 +327,7 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             p->bytes += sizeof(float2) * (size_t)NL;
         }
     }
-    const bool tune = o.specialize == 2 && p->mr && p->cl == 1;
+    const bool tune = o.specialize == 2 && p->mr;
     if (e == cudaSuccess && o.specialize && !tune && p->mr &&
         (p->cl == 1 ? p->sch.fixed < 0 : p->sch.fixed_cl < 0)) {
         // a failed compile or load is not a plan error: the runtime-schedule kernels run

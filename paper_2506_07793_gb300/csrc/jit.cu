@@ -318,9 +318,12 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     *log = "plan-time specialization is off in the bounds-checked build";
     return nullptr;
 #else
+    // one-CTA rows: candidates of N; cluster rows: candidates of the local length NL
+    const int cl = p->cl;
+    const int NL = p->N / cl;
     constexpr int kMaxCandidates = 6;
     MrSchedule cand[kMaxCandidates];
-    const int n = mr_schedule_candidates(p->N, cand, kMaxCandidates);
+    const int n = mr_schedule_candidates(NL, cand, kMaxCandidates);
     if (n < 1) {
         *log = "no schedule to tune";
         return nullptr;
@@ -334,19 +337,19 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     const std::string arch = "sm_" + std::to_string(major * 10 + minor) + "a";
     const int total = p->C * p->S;
     int rows[kMaxCandidates];
-    for (int i = 0; i < n; ++i) rows[i] = mr_launch_rows(cand[i], total);
+    for (int i = 0; i < n; ++i) rows[i] = cl == 1 ? mr_launch_rows(cand[i], total) : 1;
     // compile the candidates at once (NVRTC is thread-safe), then load them
     {
         std::vector<std::thread> pool;
         std::vector<std::string> logs((size_t)n);
         for (int i = 0; i < n; ++i)
-            pool.emplace_back([&, i] { jit_binary(cand[i], rows[i], 1, arch, &logs[(size_t)i]); });
+            pool.emplace_back([&, i] { jit_binary(cand[i], rows[i], cl, arch, &logs[(size_t)i]); });
         for (auto &t : pool) t.join();
     }
     JitKernels *k[kMaxCandidates] = {};
     for (int i = 0; i < n; ++i) {
         std::string lg;
-        k[i] = jit_kernels(cand[i], rows[i], 1, p->device, &lg);
+        k[i] = jit_kernels(cand[i], rows[i], cl, p->device, &lg);
         if (!k[i] && log->empty()) *log = lg;
     }
     // time each on the plan's own rows (all of them, or as many as 256 MB of
@@ -367,7 +370,7 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    MrArgs a;
+    MrArgs a;  // one-CTA rows
     a.spec = p->spec;
     a.bank = p->bank;
     a.band = p->band;
@@ -380,15 +383,40 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     a.sub = p->d;
     a.total_rows = trows;
     a.f64 = p->io == CWT_DTYPE_F64;
-    // candidate -1: the length's compiled-in fixed-length kernel, when it has one
+    ClMrArgs ca;  // cluster rows: the first trows rows (the grid is trows clusters)
+    ca.spec = p->spec;
+    ca.bank = p->bank;
+    ca.band = p->band;
+    ca.twL = p->twL;
+    ca.twN = p->twN;
+    ca.out_c = oc;
+    ca.out_p = op;
+    ca.out_ph = oph;
+    ca.S = p->S;
+    ca.n_out = p->n_out;
+    ca.sub = p->d;
+    ca.f64 = p->io == CWT_DTYPE_F64;
+    const bool compiled_in = cl == 1 ? p->sch.fixed >= 0 : p->sch.fixed_cl >= 0;
+    auto launch = [&](int i) -> cudaError_t {
+        if (cl == 1) return i >= 0 ? sb_launch_k(k[i], a, st) : mr_fixed_sb_launch(p, a, st);
+        const JitKernels *kk = i >= 0 ? k[i] : nullptr;
+        if (!kk) return cl_mr_fixed_sb(p, ca, st, trows);
+        ClMrArgs args = ca;
+        MrSchedule sch = cand[i];
+        void *params[] = {&args, &sch};
+        const CUresult r = driver().launch_kernel(kk->sb, (unsigned)(trows * cl), 1, 1, (unsigned)kk->threads, 1,
+                                                  1, (unsigned)kk->smem, (CUstream)st, params, nullptr);
+        return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+    };
+    // candidate -1: the length's compiled-in kernel, when it has one
     int best = -2;
     float best_ms = 0.f;
-    for (int i = p->sch.fixed >= 0 ? -1 : 0; i < n && e == cudaSuccess; ++i) {
+    for (int i = compiled_in ? -1 : 0; i < n && e == cudaSuccess; ++i) {
         if (i >= 0 && !k[i]) continue;
         float ms = 0.f, lo = -1.f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // rep 0 warms up
             e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) e = i >= 0 ? sb_launch_k(k[i], a, st) : mr_fixed_sb_launch(p, a, st);
+            if (e == cudaSuccess) e = launch(i);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -415,7 +443,7 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
         return nullptr;
     }
     if (best < 0) return nullptr;
-    p->sch = cand[best];
+    p->sch = cand[best];  // fixed / fixed_cl -1: the plan runs k[best]
     return k[best];
 #endif
 }

@@ -46,12 +46,12 @@ namespace cwtk {
 
 // Index in CWT_CL_MR_FIXED of the local schedule s, or -1 (smooth_cluster_fixed.cu).
 int cl_mr_fixed_index(const MrSchedule &s);
-// The fixed-length launches (smooth_cluster_fixed.cu).
-cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st);
+// The fixed-length launches (smooth_cluster_fixed.cu); rows as sb_launch's.
+cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows = -1);
 cudaError_t cl_mr_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 // Entry I of CWT_CL_MR_FIXED on any cluster size (smooth_cluster_fixed_<I>.cu).
 template <int I>
-cudaError_t cl_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st);
+cudaError_t cl_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows);
 template <int I>
 cudaError_t cl_fixed_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 // The cluster scale block compiled at plan creation (p->jit, jit.cu).
@@ -62,14 +62,15 @@ cudaError_t cl_mr_wide_fwd(const cwt_plan_s *p, const void *signal, cudaStream_t
 
 namespace cl_mr {
 
+// rows < 0: every row of the plan; else the first `rows` (the tuner's timing).
 template <int CL, class FX>
-cudaError_t sb_launch(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+cudaError_t sb_launch(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows = -1) {
     static std::atomic<unsigned> done{0};
     const int smem = (p->sch.N + (p->sch.N >> 4)) * 8;
     cudaError_t e = ensure_smem_attr(scale_block_kernel<CL, FX>, kMrMaxSmem, &done);
     if (e != cudaSuccess) return e;
     const int threads = (p->sch.T + 31) & ~31;
-    scale_block_kernel<CL, FX><<<p->C * p->S * CL, threads, smem, st>>>(a, p->sch);
+    scale_block_kernel<CL, FX><<<(rows < 0 ? p->C * p->S : rows) * CL, threads, smem, st>>>(a, p->sch);
     return cudaGetLastError();
 }
 
@@ -86,10 +87,10 @@ cudaError_t fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t st)
 }
 
 template <class FX>
-cudaError_t sb_any_cl(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+cudaError_t sb_any_cl(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows) {
     switch (p->cl) {
 #define CWT_CL_CASE(CL) \
-    case CL: return sb_launch<CL, FX>(p, a, st);
+    case CL: return sb_launch<CL, FX>(p, a, st, rows);
         CWT_CL_SIZES(CWT_CL_CASE)
 #undef CWT_CL_CASE
         default: return cudaErrorInvalidValue;
@@ -113,8 +114,8 @@ cudaError_t fwd_any_cl(const cwt_plan_s *p, const void *signal, cudaStream_t st)
 // CWT_CL_MR_FIXED (expanded in that entry's translation unit).
 #define CWT_CL_FIXED_DEFINE(I, N, T, ROWS, MINB, ...)                                              \
     template <>                                                                                    \
-    cudaError_t cl_fixed_sb<I>(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {          \
-        return cl_mr::sb_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, a, st);                 \
+    cudaError_t cl_fixed_sb<I>(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows) { \
+        return cl_mr::sb_any_cl<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(p, a, st, rows);           \
     }                                                                                              \
     template <>                                                                                    \
     cudaError_t cl_fixed_fwd<I>(const cwt_plan_s *p, const void *signal, cudaStream_t st) {        \

@@ -29,10 +29,10 @@ int cl_mr_fixed_index(const MrSchedule &s) {
     return -1;
 }
 
-cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st) {
+cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows) {
     switch (p->sch.fixed_cl) {
 #define CWT_CL_CASE(I, ...) \
-    case I: return cl_fixed_sb<I>(p, a, st);
+    case I: return cl_fixed_sb<I>(p, a, st, rows);
         CWT_CL_MR_FIXED(CWT_CL_CASE)
 #undef CWT_CL_CASE
         default: return cudaErrorInvalidValue;

@@ -121,3 +121,21 @@ def test_tuning_competes_with_compiled_in_kernels(lib, n):
     assert info.specialized in (0, 2) and info.fixed_kernel == 1
     ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles)
     assert power_err(res["power"], ref).max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("case,n", [(0, None), (1, None), (1, 30720)])
+def test_tuned_cluster_rows_parity(lib, case, n):
+    """specialize = 2 on cluster rows: the candidates are schedules of the local
+    length NL = N / CL (the compiled-in cluster kernel of NL competing where
+    there is one, 30720 = 2 x 15360); the split is kept and parity holds."""
+    n0, C, fs, freqs, cycles, d, CL = CLUSTER_CASES[case]
+    if n is not None:
+        n0, CL = n, 2
+    x = eeg(1900 + case, C, n0, fs, np.float32)
+    res, info = _run(lib, x, n0, fs, freqs, cycles, "f32", d, 2)
+    assert info.cluster == CL and info.fixed_kernel == 1
+    assert info.specialized == (2 if n is None else info.specialized) and info.specialized in (0, 2)
+    assert int(np.prod([r for r in info.radices if r])) == n0 // CL
+    ref = oracle.cwt(x.astype(np.float64), n0, fs, freqs, cycles, decimation=d)
+    assert complex_err(res["complex"], ref).max() <= FP32_TOL
+    assert power_err(res["power"], ref).max() <= FP32_TOL
