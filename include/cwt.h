@@ -267,6 +267,21 @@ cwt_status cwt_support_radius(int wavelet, double freq_hz, double n_cycles, doub
 cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlined_pair,
                                int *fixed_kernel);
 
+/* The row layout a plan of the 2,3,5,7-smooth length n_fft (not a power of
+ * two, 32 ... 131072) runs with cwt_options.specialize = specialize (Section
+ * "Fast Fourier transform"), as cwt_plan_info reports it before any
+ * plan-time tuning: *cluster 1 for one CTA per row, else the CTAs of the
+ * cluster split N = cluster x NL; radices[8] the passes of N's (of NL's)
+ * schedule, 0-terminated; *fixed_kernel 1 when that schedule is compiled in
+ * for this cluster size.  The split prefers local rows two CTAs per SM hold
+ * on kernels built for that: fewest passes, then the smallest cluster; sizes
+ * above 8 CTAs (non-portable clusters) only on compiled-in local rows or,
+ * with specialize != 0, on kernels compiled at plan creation.  Outputs are
+ * host memory owned by the caller.  CWT_EINVAL for a NULL output or
+ * specialize outside 0 ... 2; CWT_EUNSUPPORTED for a length no kernel runs.
+ * Host-only; no CUDA call. */
+cwt_status cwt_smooth_cluster(int n_fft, int specialize, int *cluster, int *radices, int *fixed_kernel);
+
 /* The plan-time compile of cwt_options.specialize for a smooth n_fft that is
  * not a power of two -- its one-CTA schedule, or its cluster split N = CL NL
  * (see cwt_pad_policy) -- for sm_103a, without a device (a check that the

@@ -284,7 +284,8 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
     p->mr = !is_pow2(N);
     if (p->mr) {
         // one CTA per row where a schedule covers N, else a cluster (checked above)
-        if (!(N <= cwtk::kMaxFft && cwtk::mr_schedule(N, &p->sch))) cwtk::mr_cluster_split(N, &p->cl, &p->sch);
+        if (!(N <= cwtk::kMaxFft && cwtk::mr_schedule(N, &p->sch)))
+            cwtk::mr_cluster_split(N, &p->cl, &p->sch, o.specialize != 0);
     }
     p->precision = o.precision;
     int f = 1;  // no spectral fold on the cluster and tensor-core paths
@@ -328,13 +329,27 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         }
     }
     const bool tune = o.specialize == 2 && p->mr;
-    if (e == cudaSuccess && o.specialize && !tune && p->mr &&
+    // a split above 8 CTAs with no kernel compiled in compiles the scheduler's
+    // schedule now, also before tuning (which then has a kernel to fall back on)
+    const bool wide = p->cl > 8 && p->sch.fixed_cl < 0;
+    if (e == cudaSuccess && o.specialize && (!tune || wide) && p->mr &&
         (p->cl == 1 ? p->sch.fixed < 0 : p->sch.fixed_cl < 0)) {
         // a failed compile or load is not a plan error: the runtime-schedule kernels run
         std::string log;
         const int rows = p->cl == 1 ? cwtk::mr_launch_rows(p->sch, channels * n_freqs) : 1;
         p->jit = cwtk::jit_kernels(p->sch, rows, p->cl, p->device, &log);
         if (!p->jit) p->last_error = log;
+        if (!p->jit && wide) {
+            // no kernel for that cluster size: the portable split and its table
+            p->bytes -= sizeof(float2) * (size_t)(N / p->cl);
+            cwtk::mr_cluster_split(N, &p->cl, &p->sch, false);
+            cudaFree(p->twL);
+            p->twL = nullptr;
+            const int NL = N / p->cl;
+            e = cwtk::dmalloc(&p->twL, sizeof(float2) * (size_t)NL);
+            if (e == cudaSuccess) e = cwtk::make_twiddles_n(NL, p->twL, st);
+            p->bytes += sizeof(float2) * (size_t)NL;
+        }
     }
     if (e == cudaSuccess) e = cwtk::launch_bank(p, st);
     if (e == cudaSuccess && tc) {
@@ -349,9 +364,10 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
         // failure leaves the plan on the runtime-schedule kernels
         e = cudaStreamSynchronize(st);
         std::string log;
-        if (e == cudaSuccess) p->jit = cwtk::jit_tune(p, st, &log);
-        p->tuned = p->jit != nullptr;
-        if (!p->jit) p->last_error = log;
+        cwtk::JitKernels *k = e == cudaSuccess ? cwtk::jit_tune(p, st, &log) : nullptr;
+        p->tuned = k != nullptr;
+        if (k) p->jit = k;
+        else if (!p->jit) p->last_error = log;
     }
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) {
@@ -432,6 +448,21 @@ cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlin
     inlined_pair[0] = inlined_pair[1] = 0;
     describe_schedule(sch, 1, radices, inlined_pair, fixed_kernel);
     *threads = sch.T;
+    return CWT_OK;
+}
+
+cwt_status cwt_smooth_cluster(int n_fft, int specialize, int *cluster, int *radices, int *fixed_kernel) {
+    if (!cluster || !radices || !fixed_kernel || specialize < 0 || specialize > 2) return CWT_EINVAL;
+    cwtk::MrSchedule sch;
+    int cl = 1;
+    if (is_pow2(n_fft) || n_fft < cwtk::kMinFft || n_fft > cwtk::kMaxClusterFft) return CWT_EUNSUPPORTED;
+    if (!(n_fft <= cwtk::kMaxFft && cwtk::mr_schedule(n_fft, &sch)) &&
+        !cwtk::mr_cluster_split(n_fft, &cl, &sch, specialize != 0))
+        return CWT_EUNSUPPORTED;
+    int pair[2] = {0, 0};
+    for (int q = 0; q < 8; ++q) radices[q] = 0;
+    describe_schedule(sch, cl, radices, pair, fixed_kernel);
+    *cluster = cl;
     return CWT_OK;
 }
 

@@ -232,8 +232,11 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log);
 int mr_schedule_candidates(int N, MrSchedule *out, int max_out);
 // Rows per CTA of the runtime-schedule kernels for total_rows rows (smooth.cu).
 int mr_launch_rows(const MrSchedule &sch, int total_rows);
-// Smooth lengths above 16384 on clusters (smooth_cluster.cu).
-bool mr_cluster_split(int N, int *cl, MrSchedule *sch);
+// Smooth lengths above 16384 on clusters: the split N = CL NL, preferring
+// local rows two CTAs per SM hold; jit: the plan compiles its kernels at
+// creation, so every local schedule and cluster sizes up to 16 are open
+// (smooth_cluster.cu).
+bool mr_cluster_split(int N, int *cl, MrSchedule *sch, bool jit = false);
 cudaError_t launch_forward_mr_cluster(const cwt_plan_s *p, const void *signal, cudaStream_t st);
 cudaError_t launch_scale_block_mr_cluster(const cwt_plan_s *p, void *out_c, void *out_p, void *out_ph,
                                           cudaStream_t st);

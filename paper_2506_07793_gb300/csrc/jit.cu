@@ -250,6 +250,10 @@ JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::
     if (r == CUDA_SUCCESS) r = drv.module_get_function(&k->fwd, k->mod, b.fwd_name.c_str());
     if (r == CUDA_SUCCESS) r = drv.func_set_attribute(k->sb, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k->smem);
     if (r == CUDA_SUCCESS) r = drv.func_set_attribute(k->fwd, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, k->smem);
+    if (r == CUDA_SUCCESS && cl > 8)  // clusters above the portable 8 CTAs
+        r = drv.func_set_attribute(k->sb, CU_FUNC_ATTRIBUTE_NON_PORTABLE_CLUSTER_SIZE_ALLOWED, 1);
+    if (r == CUDA_SUCCESS && cl > 8)
+        r = drv.func_set_attribute(k->fwd, CU_FUNC_ATTRIBUTE_NON_PORTABLE_CLUSTER_SIZE_ALLOWED, 1);
     if (r != CUDA_SUCCESS) {
         *log = "loading the specialized kernels failed: driver error " + std::to_string((int)r);
         if (k->mod) drv.module_unload(k->mod);
@@ -454,7 +458,7 @@ extern "C" cwt_status cwt_specialize_check(int n_fft, char *log, size_t log_len)
     cwtk::MrSchedule s;
     int cl = 1;
     if (n_fft < cwtk::kMinFft || n_fft > cwtk::kMaxClusterFft || (n_fft & (n_fft - 1)) == 0) return CWT_EUNSUPPORTED;
-    if (!(n_fft <= cwtk::kMaxFft && cwtk::mr_schedule(n_fft, &s)) && !cwtk::mr_cluster_split(n_fft, &cl, &s))
+    if (!(n_fft <= cwtk::kMaxFft && cwtk::mr_schedule(n_fft, &s)) && !cwtk::mr_cluster_split(n_fft, &cl, &s, true))
         return CWT_EUNSUPPORTED;
     std::string lg;
     const int rows = cl == 1 && s.T < 128 ? 256 / s.T : 1;

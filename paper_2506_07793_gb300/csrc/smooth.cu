@@ -236,7 +236,9 @@ int mr_schedule_candidates(int N, MrSchedule *out, int max_out) {
 // kernels: the plan-time tuner (cwt_options.specialize = 2) on 64 channels x
 // 100 scales found them 3-39% faster than the cost model's order (which
 // ranks radix sets, not orders), and the fixed-length kernels are compiled
-// for them (CWT_MR_FIXED).  T is the least thread count that fits.
+// for them (CWT_MR_FIXED); 12288 is the cluster local row of CWT_CL_MR_FIXED,
+// timed on 32 channels of the 128-scale, 122880-point rows of a minute at
+// 2048 Hz.  T is the least thread count that fits.
 struct MeasuredOrder {
     int N;
     int radices[4];
@@ -247,6 +249,7 @@ constexpr MeasuredOrder kMeasuredOrders[] = {
     {3000, {24, 5, 25}},      {9000, {24, 15, 25}},    {14000, {14, 10, 10, 10}}, {13500, {6, 10, 15, 15}},
     {12500, {10, 10, 5, 25}}, {10500, {28, 15, 25}},   {7000, {28, 10, 25}},  {3750, {25, 6, 25}},
     {3500, {28, 5, 25}},      {1750, {14, 5, 25}},     {1250, {25, 10, 5}},
+    {12288, {32, 16, 24}},  // 122880 = 10 x 12288: 3.90 against 4.04 ms (16, 24, 32)
 };
 
 bool mr_schedule(int N, MrSchedule *out) {

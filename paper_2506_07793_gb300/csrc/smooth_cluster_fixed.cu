@@ -21,12 +21,21 @@ bool same_schedule(const MrSchedule &s) {
 
 }  // namespace
 
-int cl_mr_fixed_index(const MrSchedule &s) {
-#define CWT_CL_CASE(I, N, T, ROWS, MINB, ...) \
-    if (same_schedule<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(s)) return I;
+int cl_mr_fixed_index(const MrSchedule &s, int cl) {
+    if (cl < 2 || cl > kMaxClusterCtas) return -1;
+#define CWT_CL_CASE(I, MASK, N, T, ROWS, MINB, ...) \
+    if ((((MASK) >> cl) & 1u) && same_schedule<MrFixed<N, T, ROWS, MINB, __VA_ARGS__>>(s)) return I;
     CWT_CL_MR_FIXED(CWT_CL_CASE)
 #undef CWT_CL_CASE
     return -1;
+}
+
+int cl_mr_fixed_minb(int I) {
+#define CWT_CL_CASE(J, MASK, N, T, ROWS, MINB, ...) \
+    if (I == J) return MINB;
+    CWT_CL_MR_FIXED(CWT_CL_CASE)
+#undef CWT_CL_CASE
+    return 0;
 }
 
 cudaError_t cl_mr_fixed_sb(const cwt_plan_s *p, const ClMrArgs &a, cudaStream_t st, int rows) {

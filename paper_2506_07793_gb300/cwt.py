@@ -100,6 +100,7 @@ _sig("cwt_status_str", ctypes.c_char_p, [ctypes.c_int])
 _sig("cwt_options_init", ctypes.c_int, [ctypes.POINTER(cwt_options)])
 _sig("cwt_fft_length", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip])
 _sig("cwt_smooth_schedule", ctypes.c_int, [ctypes.c_int, _ip, _ip, _ip, _ip])
+_sig("cwt_smooth_cluster", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip])
 _sig("cwt_specialize_check", ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t])
 _sig("cwt_support_radius", ctypes.c_int,
      [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _ip])
@@ -197,6 +198,15 @@ def cwt_smooth_schedule(n_fft):
     _check(_lib.cwt_smooth_schedule(int(n_fft), rad, ctypes.byref(t), pair, ctypes.byref(fixed)),
            "cwt_smooth_schedule")
     return [r for r in rad if r], t.value, (pair[0], pair[1]), fixed.value
+
+
+def cwt_smooth_cluster(n_fft, specialize=0):
+    """(cluster, radices, fixed_kernel) of a smooth length's row layout."""
+    rad = (ctypes.c_int * 8)()
+    cl, fixed = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.cwt_smooth_cluster(int(n_fft), int(specialize), ctypes.byref(cl), rad, ctypes.byref(fixed)),
+           "cwt_smooth_cluster")
+    return cl.value, [r for r in rad if r], fixed.value
 
 
 def cwt_support_radius(wavelet, freq_hz, n_cycles, fs, gmw_gamma=3.0):

@@ -50,8 +50,10 @@ plan_case("smooth pair / generic 6000", 2, 6000, 1000.0, F5, S5, pad="smooth")
 plan_case("smooth generic 1323", 2, 1323, 500.0, F5, S5, pad="smooth", fft_length=1323)
 plan_case("smooth cluster of 2 (16464 = 2 x 8232)", 1, 16400, 1000.0, F5, S5, pad="smooth")
 plan_case("smooth cluster of 3 (14175 = 3 x 4725)", 1, 14175, 1000.0, F5, S5, pad="smooth")
-plan_case("smooth cluster of 8 (122880 = 8 x 15360)", 1, 122880, 2048.0, F5, S5, pad="smooth",
+plan_case("smooth cluster of 8 (115200 = 8 x 14400)", 1, 115200, 1920.0, F5, S5, pad="smooth",
           decimation=16)
+plan_case("smooth cluster of 10 (122880 = 10 x 12288, compiled in)", 1, 122880, 2048.0, F5, S5,
+          pad="smooth", decimation=16)
 plan_case("tensor cores FP16, 16384", 2, 12000, 500.0, F5, S5, tol=TC_TOL, precision="tc_fp16")
 plan_case("tensor cores BF16, cluster of 2", 1, 20000, 1000.0, F5, S5, tol=TC_TOL,
           precision="tc_bf16")

@@ -85,7 +85,7 @@ def test_smooth_padding(lib, n, N):
     on a cluster of 3.  3^10 = 59049 has no split with NL <= 16384 (3 is its
     only factor), so 59000 and 59049 pad to 59535 = 5 x 11907; 5^7 = 78125
     splits only as 5 x 15625, unscheduled, and pads to 78400 = 2^6 5^2 7^2;
-    122880 = 8 x 15360 needs no padding; 128000 = 8 x 16000 and
+    122880 = 8 x 15360 (run as 10 x 12288) needs no padding; 128000 = 8 x 16000 and
     129024 = 8 x 16128 split only into unscheduled NL, so 128000 pads to 2^17."""
     assert lib.cwt_fft_length(n, lib.CWT_PAD_SMOOTH) == N
 
@@ -124,6 +124,62 @@ def test_smooth_cluster_split_rule(lib):
         if not ok:
             passed_over.append(m)
     assert len(passed_over) == 43 and passed_over[:3] == [59049, 78125, 84375]
+
+
+# (N, specialize, CTAs per row, local length, compiled in)
+CLUSTER_LAYOUTS = [
+    (10000, 0, 1, 10000, 1),     # one CTA per row
+    (20000, 0, 2, 10000, 1),     # 2 x 10000: two CTAs per SM already
+    (30000, 0, 3, 10000, 1),     # not 2 x 15000 (one CTA per SM)
+    (45000, 0, 3, 15000, 1),     # no local row two CTAs per SM hold is compiled in
+    (60000, 0, 5, 12000, 1),     # not 4 x 15000
+    (92160, 0, 6, 15360, 1),
+    (100000, 0, 10, 10000, 1),   # a non-portable cluster, compiled in; not 8 x 12500
+    (122880, 0, 10, 12288, 1),   # not 8 x 15360
+    (115200, 0, 8, 14400, 0),    # 10 x 11520 is not compiled in
+    (14406, 0, 2, 7203, 0),
+    (45000, 1, 4, 11250, 0),     # plan-time kernels: any local row two CTAs per SM hold
+    (105000, 1, 10, 10500, 0),
+    (115200, 1, 9, 12800, 0),
+    (14406, 1, 7, 2058, 0),
+    (30720, 1, 3, 10240, 0),
+    (100000, 1, 10, 10000, 1),   # fewest passes first: 3 (10 x 10000) before 4 (8 x 12500)
+    (120000, 2, 10, 12000, 1),
+]
+
+
+@pytest.mark.parametrize("N,spec,CL,NL,fixed", CLUSTER_LAYOUTS)
+def test_smooth_cluster_layout(lib, N, spec, CL, NL, fixed):
+    """The cluster split of a smooth length (host-only): local rows that two
+    CTAs per SM hold are preferred where a kernel is built for them -- fewest
+    passes, then the smallest cluster; sizes above 8 CTAs only on compiled-in
+    local rows or with plan-time compilation -- else the smallest cluster."""
+    cl, rad, fx = lib.cwt_smooth_cluster(N, spec)
+    assert (cl, int(np.prod(rad)), fx) == (CL, NL, fixed)
+
+
+def test_smooth_cluster_layout_invariants(lib):
+    """Every smooth length the SMOOTH policy keeps has a layout: CL local rows
+    whose radices multiply to N / CL; above 8 CTAs only on a compiled-in row
+    unless specialized; the same padding either way."""
+    for m in list(range(16385, 131073, 97)) + [122880, 61440, 98304]:
+        if not _smooth(m) or (m & (m - 1)) == 0 or lib.cwt_fft_length(m, lib.CWT_PAD_SMOOTH) != m:
+            continue
+        for spec in (0, 1):
+            cl, rad, fx = lib.cwt_smooth_cluster(m, spec)
+            assert 2 <= cl <= 16 and cl * int(np.prod(rad)) == m, (m, spec)
+            assert spec or cl <= 8 or fx, m
+
+
+def test_smooth_cluster_layout_refusals(lib):
+    for N in (4096, 78125, 31, 131073):
+        with pytest.raises(lib.CWTError) as e:
+            lib.cwt_smooth_cluster(N)
+        assert e.value.status == lib.CWT_EUNSUPPORTED
+    for spec in (-1, 3):
+        with pytest.raises(lib.CWTError) as e:
+            lib.cwt_smooth_cluster(30000, spec)
+        assert e.value.status == lib.CWT_EINVAL
 
 
 def test_padding_limits(lib):
@@ -390,12 +446,12 @@ def test_grid_check_boundary(lib):
         assert e.value.status != lib.CWT_EINVAL
 
 
-@pytest.mark.parametrize("N", [6300, 42, 50000, 14175])
+@pytest.mark.parametrize("N", [6300, 42, 105000, 14175])
 def test_specialize_check_compiles_on_the_host(lib, N):
     """The plan-time compiler builds the fixed-length kernels of a smooth
     length's one-CTA schedule (6300, 42), or the cluster kernels on its local
-    length (50000 = 4 x 12500, 14175 = 3 x 4725), from the embedded source,
-    without a device."""
+    length (105000 = 10 x 10500 on a non-portable cluster of 10 CTAs,
+    14175 = 3 x 4725), from the embedded source, without a device."""
     assert lib.cwt_specialize_check(N) == ""  # no warnings either
 
 

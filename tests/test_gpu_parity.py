@@ -385,9 +385,16 @@ SMOOTH_CLUSTER = [
     # pass, wide ones the dense pass.
     (1, 16400, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], {}, 16464, 2),
     (2, 20000, 2000.0, [0.5, 50.0, 900.0], [3.0, 7.0, 12.0], dict(dtype="f64"), 20000, 2),
-    (1, 50000, 1000.0, [1.0, 100.0, 450.0], [20.0, 7.0, 4.0], dict(decimation=4), 50000, 4),
-    (1, 100000, 4000.0, [0.3, 60.0, 1900.0], [7.0, 7.0, 10.0], dict(decimation=8), 100000, 8),
-    (1, 122880, 2048.0, [0.5, 13.0, 200.0], [7.0, 7.0, 7.0], dict(decimation=8), 122880, 8),
+    # local rows two CTAs per SM hold, compiled in: 10000, 12000, 12288, on
+    # clusters of up to 10 CTAs (above 8: a non-portable cluster size)
+    (1, 50000, 1000.0, [1.0, 100.0, 450.0], [20.0, 7.0, 4.0], dict(decimation=4), 50000, 5),
+    (1, 100000, 4000.0, [0.3, 60.0, 1900.0], [7.0, 7.0, 10.0], dict(decimation=8), 100000, 10),
+    (1, 122880, 2048.0, [0.5, 13.0, 200.0], [7.0, 7.0, 7.0], dict(decimation=8), 122880, 10),
+    (1, 30000, 500.0, [1.0, 40.0, 240.0], [7.0, 7.0, 12.0], dict(decimation=4), 30000, 3),
+    (1, 60000, 1000.0, [0.6, 80.0, 480.0], [5.0, 7.0, 12.0], dict(decimation=8, dtype="f64"), 60000, 5),
+    (1, 48000, 800.0, [0.8, 50.0, 380.0], [7.0, 7.0, 10.0], dict(decimation=4), 48000, 4),
+    # the runtime schedule of 14400 on 8 CTAs
+    (1, 115200, 1920.0, [0.5, 40.0, 900.0], [7.0, 7.0, 10.0], dict(decimation=8), 115200, 8),
     # smooth lengths of at most 16384 that no one-CTA schedule covers, odd
     # cluster sizes, and the compiled-in local length 15360 on 6 and 7 CTAs
     (1, 14175, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], {}, 14175, 3),
@@ -396,13 +403,13 @@ SMOOTH_CLUSTER = [
     (1, 19683, 2000.0, [1.5, 100.0, 800.0], [7.0, 7.0, 7.0], {}, 19683, 3),
     (1, 92160, 4096.0, [0.5, 50.0, 1800.0], [7.0, 7.0, 7.0], dict(decimation=16), 92160, 6),
     (1, 107520, 4096.0, [0.4, 120.0, 2000.0], [7.0, 7.0, 12.0], dict(decimation=16), 107520, 7),
-    # compiled-in local rows of 15000 (a minute at 500 and 1000 Hz)
-    (1, 30000, 500.0, [1.0, 40.0, 240.0], [7.0, 7.0, 12.0], dict(decimation=4), 30000, 2),
-    (1, 60000, 1000.0, [0.6, 80.0, 480.0], [5.0, 7.0, 12.0], dict(decimation=8, dtype="f64"), 60000, 4),
+    # the compiled-in local row 15000 (a minute and a half at 500 Hz)
+    (1, 45000, 500.0, [1.0, 30.0, 230.0], [5.0, 7.0, 12.0], dict(decimation=4), 45000, 3),
 ]
 
-# local lengths whose schedule is compiled into the cluster kernels
-CLUSTER_FIXED_NL = (15360, 15000, 10000)
+# local lengths whose schedule is compiled into the cluster kernels (for
+# every cluster size these cases use)
+CLUSTER_FIXED_NL = (15360, 15000, 10000, 12000, 12288)
 
 
 @pytest.mark.parametrize("case", range(len(SMOOTH_CLUSTER)))

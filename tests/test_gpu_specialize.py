@@ -63,10 +63,11 @@ def test_specialized_kernels_match_runtime_schedule_and_oracle(lib, case):
     assert power_err(spec["power"], ref).max() <= FP32_TOL
 
 
-# cluster rows whose local length has no kernel compiled in: (n = N, C, fs,
-# freqs, cycles, decimation, CL)
+# cluster rows whose local length has no kernel compiled in, split the same
+# way with and without specialization: (n = N, C, fs, freqs, cycles,
+# decimation, CL)
 CLUSTER_CASES = [
-    (50000, 1, 1000.0, [1.0, 100.0, 450.0], [20.0, 7.0, 4.0], 4, 4),
+    (19683, 1, 2000.0, [1.5, 100.0, 800.0], [20.0, 7.0, 4.0], 4, 3),
     (14175, 2, 1000.0, [2.0, 40.0, 300.0], [5.0, 7.0, 10.0], 1, 3),
 ]
 
@@ -85,6 +86,36 @@ def test_specialized_cluster_kernels_match_runtime_schedule_and_oracle(lib, case
         assert np.array_equal(plain[k], spec[k]), k
     ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
     assert power_err(spec["power"], ref).max() <= FP32_TOL
+
+
+# splits that only plan-time compilation opens (local rows two CTAs per SM
+# hold, clusters above 8 CTAs): (n = N, fs, freqs, cycles, decimation, CL
+# with specialize, CL without)
+WIDE_CASES = [
+    (105000, 1000.0, [0.8, 60.0, 450.0], [7.0, 7.0, 12.0], 8, 10, 7),
+    (115200, 1920.0, [0.5, 40.0, 900.0], [7.0, 7.0, 10.0], 8, 9, 8),
+    (14406, 500.0, [1.0, 30.0, 200.0], [3.0, 7.0, 12.0], 1, 7, 2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(WIDE_CASES)))
+def test_specialized_wide_splits_match_oracle(lib, case):
+    """With specialize the cluster split may take local rows that only a
+    kernel compiled at plan creation runs two CTAs per SM, on up to 16 CTAs
+    (non-portable cluster sizes): parity with the oracle, and with the
+    portable split of the same length."""
+    n, fs, freqs, cycles, d, CL1, CL0 = WIDE_CASES[case]
+    x = eeg(1650 + case, 1, n, fs, np.float32)
+    plain, info0 = _run(lib, x, n, fs, freqs, cycles, "f32", d, False)
+    spec, info1 = _run(lib, x, n, fs, freqs, cycles, "f32", d, True)
+    assert info0.cluster == CL0 and info1.cluster == CL1
+    assert info1.specialized == 1 and info1.fixed_kernel == 1
+    assert int(np.prod([r for r in info1.radices if r])) == n // CL1
+    ref = oracle.cwt(x.astype(np.float64), n, fs, freqs, cycles, decimation=d)
+    assert complex_err(spec["complex"], ref).max() <= FP32_TOL
+    assert power_err(spec["power"], ref).max() <= FP32_TOL
+    peak = plain["power"].max(axis=-1, keepdims=True)
+    assert (np.abs(spec["power"] - plain["power"]) / peak).max() <= 2 * FP32_TOL
 
 
 @pytest.mark.parametrize("n,pad", [(10000, "smooth"), (1000, "pow2"), (20000, "smooth")])
@@ -123,18 +154,18 @@ def test_tuning_competes_with_compiled_in_kernels(lib, n):
     assert power_err(res["power"], ref).max() <= FP32_TOL
 
 
-@pytest.mark.parametrize("case,n", [(0, None), (1, None), (1, 30720)])
+@pytest.mark.parametrize("case,n", [(0, None), (1, None), (1, 30720), (1, 60000)])
 def test_tuned_cluster_rows_parity(lib, case, n):
     """specialize = 2 on cluster rows: the candidates are schedules of the local
-    length NL = N / CL (the compiled-in cluster kernel of NL competing where
-    there is one, 30720 = 2 x 15360); the split is kept and parity holds."""
+    length NL = N / CL (30720 = 3 x 10240; the compiled-in cluster kernel of NL
+    competing where there is one, 60000 = 5 x 12000); parity holds."""
     n0, C, fs, freqs, cycles, d, CL = CLUSTER_CASES[case]
     if n is not None:
-        n0, CL = n, 2
+        n0, CL = n, {30720: 3, 60000: 5}[n]
     x = eeg(1900 + case, C, n0, fs, np.float32)
     res, info = _run(lib, x, n0, fs, freqs, cycles, "f32", d, 2)
     assert info.cluster == CL and info.fixed_kernel == 1
-    assert info.specialized == (2 if n is None else info.specialized) and info.specialized in (0, 2)
+    assert info.specialized in ((0, 2) if n == 60000 else (2,))
     assert int(np.prod([r for r in info.radices if r])) == n0 // CL
     ref = oracle.cwt(x.astype(np.float64), n0, fs, freqs, cycles, decimation=d)
     assert complex_err(res["complex"], ref).max() <= FP32_TOL
