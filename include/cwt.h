@@ -180,10 +180,11 @@ typedef struct {
                           transform");
                           if that fails the plan runs the runtime-schedule kernels
                           (cwt_plan_info.specialized, cwt_plan_last_error).
-                          2: for a smooth N, compile up to six candidate
+                          2: for a smooth N, compile up to eight candidate
                           schedules of N -- or of its cluster split's local
-                          length -- (the scheduler's, then the cost model's two
-                          cheapest radix sets in each pass order) and keep the
+                          length -- (the scheduler's, its passes on two other
+                          thread counts, then the cost model's two cheapest
+                          radix sets in each pass order) and keep the
                           fastest on the plan's own rows, the compiled-in
                           kernel competing where there is one (a few seconds;
                           cwt_plan_info.radices reports the winner).

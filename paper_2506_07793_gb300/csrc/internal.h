@@ -223,12 +223,13 @@ int support_radius(int wavelet, double F, double sig, double gamma, double fs);
 // *log; the same compile for sm_103a without a device, as a check.
 JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::string *log);
 bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log);
-// cwt_options.specialize = 2: the fixed-length kernels of up to six candidate
+// cwt_options.specialize = 2: the fixed-length kernels of up to eight candidate
 // schedules (mr_schedule_candidates), each timed on the plan's rows; the
 // fastest, with p->sch set to its schedule (jit.cu).
 JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log);
-// The scheduler's schedule of N first, then the cost model's two cheapest
-// radix sets in each of their pass orders; returns how many (smooth.cu).
+// The scheduler's schedule of N first, its passes on up to two other thread
+// counts, then the cost model's two cheapest radix sets in each of their pass
+// orders; returns how many (smooth.cu).
 int mr_schedule_candidates(int N, MrSchedule *out, int max_out);
 // Rows per CTA of the runtime-schedule kernels for total_rows rows (smooth.cu).
 int mr_launch_rows(const MrSchedule &sch, int total_rows);

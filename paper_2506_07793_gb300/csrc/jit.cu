@@ -325,7 +325,7 @@ JitKernels *jit_tune(cwt_plan_s *p, cudaStream_t st, std::string *log) {
     // one-CTA rows: candidates of N; cluster rows: candidates of the local length NL
     const int cl = p->cl;
     const int NL = p->N / cl;
-    constexpr int kMaxCandidates = 6;
+    constexpr int kMaxCandidates = 8;
     MrSchedule cand[kMaxCandidates];
     const int n = mr_schedule_candidates(NL, cand, kMaxCandidates);
     if (n < 1) {

@@ -185,6 +185,28 @@ int mr_schedule_candidates(int N, MrSchedule *out, int max_out) {
     out[0] = first;
     out[0].fast = -1;
     int n = 1;
+    // the same passes on fewer or more threads: the least whole-warp count that
+    // fits, one warp more, and the count rounded up to 128 (10000 = 16 x 25 x 25
+    // ran 8% faster on 416 threads than on 512)
+    {
+        std::vector<int> rs;
+        for (int q = 0; q < first.np; ++q) rs.push_back(first.p[q].R);
+        int Tmin = 1;
+        for (int R : rs) {
+            const int gm = std::max(1, kMrPoints / R);
+            Tmin = std::max(Tmin, (N / R + gm - 1) / gm);
+        }
+        const int w = (Tmin + 31) / 32 * 32;
+        int added = 0;
+        for (int T : {w, w + 32, round_threads(Tmin)}) {
+            if (T == first.T || T > kMrThreads || T < 128 || added == 2 || n >= max_out) continue;
+            bool dup = false;
+            for (int i = 0; i < n; ++i) dup = dup || out[i].T == T;
+            if (dup) continue;
+            out[n++] = build_schedule(N, rs, T, -1);
+            ++added;
+        }
+    }
     // the cheapest radix multisets under the cost model, each in its distinct pass orders
     std::vector<std::vector<int>> sets;
     std::vector<int> cur;
@@ -242,6 +264,7 @@ int mr_schedule_candidates(int N, MrSchedule *out, int max_out) {
 struct MeasuredOrder {
     int N;
     int radices[4];
+    int T;  // threads per row; 0: the least that fits, rounded up to 128
 };
 constexpr MeasuredOrder kMeasuredOrders[] = {
     {8000, {16, 25, 20}},     {5000, {20, 10, 25}},    {4000, {16, 10, 25}},  {2500, {25, 10, 10}},
@@ -250,6 +273,10 @@ constexpr MeasuredOrder kMeasuredOrders[] = {
     {12500, {10, 10, 5, 25}}, {10500, {28, 15, 25}},   {7000, {28, 10, 25}},  {3750, {25, 6, 25}},
     {3500, {28, 5, 25}},      {1750, {14, 5, 25}},     {1250, {25, 10, 5}},
     {12288, {32, 16, 24}},  // 122880 = 10 x 12288: 3.90 against 4.04 ms (16, 24, 32)
+    // 13 warps: the radix-25 passes' 400 butterflies leave 16 threads idle instead of 112, and
+    // two 416-thread CTAs per SM allow 78 registers a thread (fewer spills): 0.236 against
+    // 0.256 ms per step of the 64-channel, 100-scale rows at 512 threads
+    {10000, {16, 25, 25}, 416},
 };
 
 bool mr_schedule(int N, MrSchedule *out) {
@@ -268,7 +295,7 @@ bool mr_schedule(int N, MrSchedule *out) {
             const int gm = std::max(1, kMrPoints / R);
             Tmin = std::max(Tmin, (N / R + gm - 1) / gm);
         }
-        MrSchedule s = build_schedule(N, rs, round_threads(Tmin), -1);
+        MrSchedule s = build_schedule(N, rs, m.T ? m.T : round_threads(Tmin), -1);
         s.fixed = mr_fixed_index(s);
         *out = s;
         return true;

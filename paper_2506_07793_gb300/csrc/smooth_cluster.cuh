@@ -47,7 +47,7 @@ namespace cwtk {
 #define CWT_CL_PORTABLE 0x1FCu  // cluster sizes 2 ... 8
 #define CWT_CL_MR_FIXED_0(X) X(0, CWT_CL_PORTABLE, 15360, 512, 1, 1, 16, 30, 32)
 #define CWT_CL_MR_FIXED_1(X) X(1, CWT_CL_PORTABLE, 15000, 512, 1, 1, 10, 10, 10, 15)
-#define CWT_CL_MR_FIXED_2(X) X(2, CWT_CL_PORTABLE | (1u << 10), 10000, 512, 1, 2, 16, 25, 25)
+#define CWT_CL_MR_FIXED_2(X) X(2, CWT_CL_PORTABLE | (1u << 10), 10000, 416, 1, 2, 16, 25, 25)
 #define CWT_CL_MR_FIXED_3(X) X(3, CWT_CL_PORTABLE | (1u << 10), 12000, 512, 1, 2, 16, 25, 30)
 #define CWT_CL_MR_FIXED_4(X) X(4, CWT_CL_PORTABLE | (1u << 10), 12288, 512, 1, 2, 32, 16, 24)
 #define CWT_CL_MR_FIXED(X) \

@@ -100,7 +100,7 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
 // smooth_fixed.cu, of list B in smooth_fixed_b.cu (two translation units that
 // compile in parallel).
 #define CWT_MR_FIXED_A(X)                     \
-    X(0, 10000, 512, 1, 2, 16, 25, 25)        \
+    X(0, 10000, 416, 1, 2, 16, 25, 25)        \
     X(1, 8000, 512, 1, 2, 16, 25, 20)         \
     X(2, 5000, 256, 1, 4, 20, 10, 25)         \
     X(3, 4000, 256, 1, 4, 16, 10, 25)         \

@@ -360,7 +360,7 @@ def test_null_plan_calls(lib):
 # schedule they were compiled for: pin that choice (and the inlined pair of
 # the forward FFT) for each of them, on the host.
 FIXED_SCHEDULES = {
-    10000: ([16, 25, 25], 512, (16, 25)),
+    10000: ([16, 25, 25], 416, (0, 0)),
     8000: ([16, 25, 20], 512, (0, 0)),
     5000: ([20, 10, 25], 256, (0, 0)),
     4000: ([16, 10, 25], 256, (0, 0)),
