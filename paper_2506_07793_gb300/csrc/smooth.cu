@@ -267,16 +267,19 @@ struct MeasuredOrder {
     int T;  // threads per row; 0: the least that fits, rounded up to 128
 };
 constexpr MeasuredOrder kMeasuredOrders[] = {
-    {8000, {16, 25, 20}},     {5000, {20, 10, 25}},    {4000, {16, 10, 25}},  {2500, {25, 10, 10}},
-    {2000, {20, 10, 10}},     {7500, {25, 10, 30}},    {6000, {24, 10, 25}},
-    {3000, {24, 5, 25}},      {9000, {24, 15, 25}},    {14000, {14, 10, 10, 10}}, {13500, {6, 10, 15, 15}},
-    {12500, {10, 10, 5, 25}}, {10500, {28, 15, 25}},   {7000, {28, 10, 25}},  {3750, {25, 6, 25}},
-    {3500, {28, 5, 25}},      {1750, {14, 5, 25}},     {1250, {25, 10, 5}},
+    {5000, {20, 10, 25}},       {4000, {16, 10, 25}},      {2500, {25, 10, 10}},     {2000, {20, 10, 10}},
+    {7500, {25, 10, 30}},       {6000, {24, 10, 25}},      {3000, {24, 5, 25}},      {9000, {24, 15, 25}},
+    {14000, {14, 10, 10, 10}},  {13500, {6, 10, 15, 15}},  {12500, {10, 10, 5, 25}}, {3750, {25, 6, 25}},
+    {1750, {14, 5, 25}},        {1250, {25, 10, 5}},
     {12288, {32, 16, 24}},  // 122880 = 10 x 12288: 3.90 against 4.04 ms (16, 24, 32)
-    // 13 warps: the radix-25 passes' 400 butterflies leave 16 threads idle instead of 112, and
-    // two 416-thread CTAs per SM allow 78 registers a thread (fewer spills): 0.236 against
-    // 0.256 ms per step of the 64-channel, 100-scale rows at 512 threads
-    {10000, {16, 25, 25}, 416},
+    // Thread counts below the 128-rounded one: fewer threads idle in the passes with the fewest
+    // butterflies, and more registers a thread.  Tuner timings per launch (64 channels x 100
+    // scales) against the same passes on the rounded count: 10000 on 416 threads 0.0840 against
+    // 0.0901 ms (0.236 against 0.256 ms per step), 10500 on 448 0.0997 against 0.1061, 8000 on
+    // 416 0.0795 against 0.0813, 7000 on 288 0.0902 against 0.0941, 4500 on 160 0.0900 against
+    // 0.0964, 3500 on 192 0.0853 against 0.0883.
+    {10000, {16, 25, 25}, 416}, {10500, {28, 15, 25}, 448}, {8000, {16, 25, 20}, 416},
+    {7000, {28, 10, 25}, 288},  {4500, {10, 15, 30}, 160},  {3500, {28, 5, 25}, 192},
 };
 
 bool mr_schedule(int N, MrSchedule *out) {

@@ -101,7 +101,7 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
 // compile in parallel).
 #define CWT_MR_FIXED_A(X)                     \
     X(0, 10000, 416, 1, 2, 16, 25, 25)        \
-    X(1, 8000, 512, 1, 2, 16, 25, 20)         \
+    X(1, 8000, 416, 1, 2, 16, 25, 20)         \
     X(2, 5000, 256, 1, 4, 20, 10, 25)         \
     X(3, 4000, 256, 1, 4, 16, 10, 25)         \
     X(4, 2500, 100, 2, 4, 25, 10, 10)         \
@@ -119,11 +119,11 @@ cudaError_t mr_fwd_launch(const cwt_plan_s *p, const void *signal, cudaStream_t 
     X(15, 14000, 512, 1, 1, 14, 10, 10, 10)   \
     X(16, 13500, 512, 1, 1, 6, 10, 15, 15)    \
     X(17, 12500, 512, 1, 2, 10, 10, 5, 25)    \
-    X(18, 10500, 512, 1, 2, 28, 15, 25)       \
-    X(19, 7000, 384, 1, 2, 28, 10, 25)        \
-    X(20, 4500, 256, 1, 3, 10, 15, 30)        \
+    X(18, 10500, 448, 1, 2, 28, 15, 25)       \
+    X(19, 7000, 288, 1, 3, 28, 10, 25)        \
+    X(20, 4500, 160, 1, 4, 10, 15, 30)        \
     X(21, 3750, 256, 1, 4, 25, 6, 25)         \
-    X(22, 3500, 256, 1, 4, 28, 5, 25)         \
+    X(22, 3500, 192, 1, 4, 28, 5, 25)         \
     X(23, 2250, 75, 2, 3, 10, 15, 15)         \
     X(24, 1750, 70, 3, 4, 14, 5, 25)          \
     X(25, 1250, 50, 5, 4, 25, 10, 5)          \

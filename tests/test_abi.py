@@ -361,7 +361,7 @@ def test_null_plan_calls(lib):
 # the forward FFT) for each of them, on the host.
 FIXED_SCHEDULES = {
     10000: ([16, 25, 25], 416, (0, 0)),
-    8000: ([16, 25, 20], 512, (0, 0)),
+    8000: ([16, 25, 20], 416, (0, 0)),
     5000: ([20, 10, 25], 256, (0, 0)),
     4000: ([16, 10, 25], 256, (0, 0)),
     2500: ([25, 10, 10], 100, (0, 0)),
@@ -378,11 +378,11 @@ FIXED_SCHEDULES = {
     14000: ([14, 10, 10, 10], 512, (0, 0)),
     13500: ([6, 10, 15, 15], 512, (0, 0)),
     12500: ([10, 10, 5, 25], 512, (0, 0)),
-    10500: ([28, 15, 25], 512, (0, 0)),
-    7000: ([28, 10, 25], 384, (0, 0)),
-    4500: ([10, 15, 30], 256, (0, 0)),
+    10500: ([28, 15, 25], 448, (0, 0)),
+    7000: ([28, 10, 25], 288, (0, 0)),
+    4500: ([10, 15, 30], 160, (0, 0)),
     3750: ([25, 6, 25], 256, (0, 0)),
-    3500: ([28, 5, 25], 256, (0, 0)),
+    3500: ([28, 5, 25], 192, (0, 0)),
     2250: ([10, 15, 15], 75, (0, 0)),
     1750: ([14, 5, 25], 70, (0, 0)),
     1250: ([25, 10, 5], 50, (0, 0)),
