@@ -84,8 +84,9 @@ typedef enum { CWT_DTYPE_F32 = 0, CWT_DTYPE_F64 = 1 } cwt_dtype;
  * of two run on the mixed-radix kernels: one CTA per row where a radix
  * schedule of at most 32 values per thread and 512 threads covers N (every
  * smooth N <= 16384 but 15 in 14175 ... 16200), else a row of N = CL NL
- * points on a thread-block cluster of CL CTAs, CL the smallest of 2 ... 8
- * that divides N with NL <= 16384 a scheduled length (up to N = 131072).
+ * points on a thread-block cluster of CL CTAs, with NL <= 16384 a scheduled
+ * length and some such CL among 2 ... 8 (up to N = 131072; the split a plan
+ * runs is cwt_smooth_cluster's, which may take up to 16 CTAs).
  * The 43 smooth lengths with neither (3^10 = 59049, 5^7 = 78125, and 41
  * from 84375 up, where every split leaves NL > 16384 or unscheduled) are
  * passed over: SMOOTH then gives the next one, and an explicit fft_length
@@ -218,9 +219,10 @@ typedef struct {
     int precision;          /* cwt_precision of the inverse FFTs */
     int cluster;            /* CTAs that share each inverse FFT (a thread-block cluster
                                over distributed shared memory): 1 when one CTA holds the
-                               row (at most 16384 points), else 2 ... 8, each CTA holding
-                               inverse_length / cluster points (powers of two: 2, 4, 8);
-                               radices then describe those points' passes */
+                               row (at most 16384 points), else 2 ... 16, each CTA holding
+                               inverse_length / cluster points (powers of two: 2, 4, 8;
+                               smooth lengths: cwt_smooth_cluster's split); radices then
+                               describe those points' passes */
     int specialized;        /* 1 when the plan runs kernels compiled at its creation
                                (cwt_options.specialize), 2 when they were chosen among
                                candidate schedules by timing (specialize = 2) */
