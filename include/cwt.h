@@ -279,7 +279,9 @@ cwt_status cwt_smooth_schedule(int n_fft, int *radices, int *threads, int *inlin
  * for this cluster size.  The split prefers local rows two CTAs per SM hold
  * on kernels built for that: fewest passes, then the smallest cluster; sizes
  * above 8 CTAs (non-portable clusters) only on compiled-in local rows or,
- * with specialize != 0, on kernels compiled at plan creation.  Outputs are
+ * with specialize != 0, on kernels compiled at plan creation (such a
+ * cluster needs a GPU partition whose GPCs hold it -- a whole GB300 does;
+ * elsewhere its launch fails with CWT_ECUDA).  Outputs are
  * host memory owned by the caller.  CWT_EINVAL for a NULL output or
  * specialize outside 0 ... 2; CWT_EUNSUPPORTED for a length no kernel runs.
  * Host-only; no CUDA call. */

@@ -54,6 +54,16 @@ plan_case("smooth cluster of 8 (115200 = 8 x 14400)", 1, 115200, 1920.0, F5, S5,
           decimation=16)
 plan_case("smooth cluster of 10 (122880 = 10 x 12288, compiled in)", 1, 122880, 2048.0, F5, S5,
           pad="smooth", decimation=16)
+# plan-time compilation is off in this build: a split that only compiled
+# kernels run (105000 = 10 x 10500) falls back to the portable one (7 x 15000)
+t = lib.CWT(1, 105000, 1000.0, F5, S5, outputs=("power",), pad="smooth", specialize=True)
+try:
+    assert (t.info.cluster, t.info.specialized) == (7, 0), (t.info.cluster, t.info.specialized)
+    print("specialize without plan-time compilation: cluster", t.info.cluster)
+finally:
+    t.close()
+plan_case("portable split after the fallback (105000 = 7 x 15000)", 1, 105000, 1000.0, F5, S5,
+          pad="smooth", decimation=16, specialize=True)
 plan_case("tensor cores FP16, 16384", 2, 12000, 500.0, F5, S5, tol=TC_TOL, precision="tc_fp16")
 plan_case("tensor cores BF16, cluster of 2", 1, 20000, 1000.0, F5, S5, tol=TC_TOL,
           precision="tc_bf16")
