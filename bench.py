@@ -40,8 +40,8 @@ L2_FLUSH_BYTES = 256 << 20
 PROFILES = {
     "pow2": ("scale_block_fp32_fused_64x100x10000.txt", ["fft_core.cuh", "scale_block.cu"]),
     "smooth": ("mr_fixed_scale_block_fp32_fused_smooth_64x100x10000.txt",
-               ["fft_core.cuh", "mixed_radix.cuh", "smooth_kernel.cuh", "smooth.cu", "smooth_fixed.cuh",
-                "smooth_fixed.cu"]),
+               ["fft_core.cuh", "mixed_radix.cuh", "smooth_device.cuh", "smooth_kernel.cuh", "smooth.cu",
+                "smooth_fixed.cuh", "smooth_fixed.cu"]),
 }
 
 

