@@ -343,10 +343,11 @@ cwt_status cwt_plan_create(cwt_plan *out, int channels, int samples, double fs,
             // no kernel for that cluster size: the portable split and its table
             p->bytes -= sizeof(float2) * (size_t)(N / p->cl);
             cwtk::mr_cluster_split(N, &p->cl, &p->sch, false);
+            e = cudaStreamSynchronize(st);  // the old table's fill has finished
             cudaFree(p->twL);
             p->twL = nullptr;
             const int NL = N / p->cl;
-            e = cwtk::dmalloc(&p->twL, sizeof(float2) * (size_t)NL);
+            if (e == cudaSuccess) e = cwtk::dmalloc(&p->twL, sizeof(float2) * (size_t)NL);
             if (e == cudaSuccess) e = cwtk::make_twiddles_n(NL, p->twL, st);
             p->bytes += sizeof(float2) * (size_t)NL;
         }
