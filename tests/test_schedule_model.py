@@ -226,9 +226,10 @@ def test_prime_factor_maps(R):
         np.testing.assert_allclose(X, ref, rtol=0, atol=1e-12 * R)
 
 
-@pytest.mark.parametrize("CL,NL", [(3, 4725), (2, 7203), (5, 3125), (6, 2560), (7, 2240), (8, 15360)])
+@pytest.mark.parametrize("CL,NL", [(3, 4725), (2, 7203), (5, 3125), (6, 2560), (7, 2240), (8, 15360),
+                                   (9, 1000), (10, 12288), (12, 2500), (16, 7680)])
 def test_smooth_cluster_decomposition(lib, CL, NL):
-    """Smooth rows on clusters (any CL in 2 ... 8): the residue classes run the
+    """Smooth rows on clusters (any CL in 2 ... 16): the residue classes run the
     scheduler's NL-point passes, the cross-CTA radix-CL stage finishes the row;
     the class's in-band bins are the cyclic run of Bm local points from
     m_first (delta = (c - b0) mod CL, Bm = ceil((B - delta) / CL)), and with
