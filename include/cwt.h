@@ -189,7 +189,11 @@ typedef struct {
                           fastest on the plan's own rows, the compiled-in
                           kernel competing where there is one (a few seconds;
                           cwt_plan_info.radices reports the winner).
-                          0 (default): never compile at plan creation */
+                          0 (default): never compile at plan creation.
+                          Compiled modules are kept per process; with the
+                          environment variable CWT_JIT_CACHE_DIR naming a
+                          writable directory, also on disk, and later processes
+                          load them instead of compiling */
     int reserved[6];
 } cwt_options;
 

@@ -22,9 +22,14 @@
 // with).
 #include <cuda.h>
 #include <nvrtc.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -182,6 +187,102 @@ namespace {
 
 // The compiled module of (s, rows, cl) for arch in g_cubins, compiling it
 // (without holding the lock, so that several compile at once) when absent.
+// ---- the on-disk cache (CWT_JIT_CACHE_DIR) ------------------------------------
+// With CWT_JIT_CACHE_DIR naming a writable directory, every compiled module is
+// also kept there, one file per (architecture, schedule, rows, cluster,
+// embedded source, NVRTC version), and a later process loads it instead of
+// compiling.  A file holds a magic line, the full key (checked on load, so a
+// hash collision or a truncated file reads as a miss), the two lowered kernel
+// names, the cubin's size and the cubin; it is written to a temporary name and
+// renamed into place, so readers never see half a file.
+
+uint64_t fnv1a(const char *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) h = (h ^ (unsigned char)p[i]) * 1099511628211ull;
+    return h;
+}
+
+// The embedded headers' digest and the compiler's version: a rebuilt library
+// or another toolkit never reads an older file.
+const std::string &source_tag() {
+    static const std::string tag = [] {
+        uint64_t h = fnv1a("", 0);
+        for (int i = 0; i < cwt_jit_header_count; ++i) {
+            h = fnv1a(cwt_jit_header_names[i], std::strlen(cwt_jit_header_names[i]), h);
+            h = fnv1a(cwt_jit_header_texts[i], std::strlen(cwt_jit_header_texts[i]), h);
+        }
+        int major = 0, minor = 0;
+        nvrtcVersion(&major, &minor);
+        char b[64];
+        std::snprintf(b, sizeof b, "%016llx/nvrtc%d.%d", (unsigned long long)h, major, minor);
+        return std::string(b);
+    }();
+    return tag;
+}
+
+std::string cache_path(const std::string &key) {
+    const char *dir = std::getenv("CWT_JIT_CACHE_DIR");
+    if (!dir || !*dir) return std::string();
+    char name[40];
+    std::snprintf(name, sizeof name, "/cwt_jit_%016llx.bin", (unsigned long long)fnv1a(key.data(), key.size()));
+    return std::string(dir) + name;
+}
+
+constexpr const char *kCacheMagic = "cwt-jit-module 1";
+
+bool cache_load(const std::string &key, JitBinary *b) {
+    const std::string path = cache_path(key);
+    if (path.empty()) return false;
+    std::FILE *f = std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    std::string data;
+    char buf[1 << 16];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) data.append(buf, n);
+    std::fclose(f);
+    // magic \n key \n sb_name \n fwd_name \n size \n cubin
+    size_t pos = 0;
+    std::string fields[5];
+    for (std::string &fl : fields) {
+        const size_t e = data.find('\n', pos);
+        if (e == std::string::npos) return false;
+        fl = data.substr(pos, e - pos);
+        pos = e + 1;
+    }
+    if (fields[0] != kCacheMagic || fields[1] != key || fields[2].empty() || fields[3].empty()) return false;
+    char *end = nullptr;
+    const unsigned long long size = std::strtoull(fields[4].c_str(), &end, 10);
+    if (!end || *end || size == 0 || size != data.size() - pos) return false;
+    b->sb_name = fields[2];
+    b->fwd_name = fields[3];
+    b->cubin.assign(data.begin() + (std::ptrdiff_t)pos, data.end());
+    return true;
+}
+
+void cache_store(const std::string &key, const JitBinary &b) {
+    const std::string path = cache_path(key);
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid()) + "." +
+                            std::to_string((unsigned long long)std::hash<std::thread::id>()(std::this_thread::get_id()));
+    std::FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;  // an unwritable cache is no error: the module stays in memory
+    const std::string head = std::string(kCacheMagic) + "\n" + key + "\n" + b.sb_name + "\n" + b.fwd_name + "\n" +
+                             std::to_string(b.cubin.size()) + "\n";
+    const bool ok = std::fwrite(head.data(), 1, head.size(), f) == head.size() &&
+                    std::fwrite(b.cubin.data(), 1, b.cubin.size(), f) == b.cubin.size();
+    if (std::fclose(f) != 0 || !ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
+// The module of (s, rows, cl) for arch: from the cache on disk, else compiled
+// (and stored there).
+bool load_or_compile(const MrSchedule &s, int rows, int cl, const std::string &arch, JitBinary *b,
+                     std::string *log) {
+    const std::string disk_key = arch + ":" + schedule_key(s, rows, cl) + ":" + source_tag();
+    if (cache_load(disk_key, b)) return true;
+    if (!compile(s, rows, cl, arch, &b->cubin, &b->sb_name, &b->fwd_name, log)) return false;
+    cache_store(disk_key, *b);
+    return true;
+}
+
 bool jit_binary(const MrSchedule &s, int rows, int cl, const std::string &arch, std::string *log) {
     const std::string key = arch + ":" + schedule_key(s, rows, cl);
     {
@@ -189,7 +290,7 @@ bool jit_binary(const MrSchedule &s, int rows, int cl, const std::string &arch, 
         if (g_cubins.count(key)) return true;
     }
     JitBinary b;
-    if (!compile(s, rows, cl, arch, &b.cubin, &b.sb_name, &b.fwd_name, log)) return false;
+    if (!load_or_compile(s, rows, cl, arch, &b, log)) return false;
     std::lock_guard<std::mutex> lock(g_jit_mu);
     g_cubins.emplace(key, std::move(b));
     return true;
@@ -198,9 +299,8 @@ bool jit_binary(const MrSchedule &s, int rows, int cl, const std::string &arch, 
 }  // namespace
 
 bool jit_compile_check(const MrSchedule &s, int rows, int cl, std::string *log) {
-    std::vector<char> cubin;
-    std::string a, b;
-    return compile(s, rows, cl, "sm_103a", &cubin, &a, &b, log);
+    JitBinary b;
+    return load_or_compile(s, rows, cl, "sm_103a", &b, log);
 }
 
 JitKernels *jit_kernels(const MrSchedule &s, int rows, int cl, int device, std::string *log) {

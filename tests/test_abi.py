@@ -462,3 +462,42 @@ def test_specialize_check_refuses_other_lengths(lib, N):
     with pytest.raises(lib.CWTError) as e:
         lib.cwt_specialize_check(N)
     assert e.value.status == lib.CWT_EUNSUPPORTED
+
+
+def _specialize_check_in_child(cache_dir, N):
+    """cwt_specialize_check(N) in a fresh process with CWT_JIT_CACHE_DIR set;
+    returns its wall time in seconds."""
+    import subprocess
+    import sys
+    code = ("import time, paper_2506_07793_gb300 as p; t = time.perf_counter(); "
+            f"assert p.cwt_specialize_check({N}) == ''; print(time.perf_counter() - t)")
+    env = dict(os.environ, CWT_JIT_CACHE_DIR=str(cache_dir))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    return float(r.stdout.strip().splitlines()[-1])
+
+
+def test_plan_time_module_cache_on_disk(lib, tmp_path):
+    """CWT_JIT_CACHE_DIR keeps each plan-time compiled module on disk: a second
+    process loads it instead of compiling (one file per schedule, no
+    temporaries left), and a damaged file reads as a miss and is rewritten."""
+    N = 6300
+    t_compile = _specialize_check_in_child(tmp_path, N)
+    files = sorted(tmp_path.iterdir())
+    assert len(files) == 1 and files[0].name.startswith("cwt_jit_") and files[0].suffix == ".bin"
+    good = files[0].read_bytes()
+    assert good.startswith(b"cwt-jit-module 1\n") and b":6300/" in good.split(b"\n")[1]
+    t_load = _specialize_check_in_child(tmp_path, N)
+    assert t_load < 0.5 * t_compile, (t_load, t_compile)
+    assert sorted(tmp_path.iterdir()) == files
+    # a truncated file: a miss, compiled again and rewritten whole (the same
+    # header; the compiler's output need not be byte-identical run to run)
+    files[0].write_bytes(good[: len(good) // 2])
+    _specialize_check_in_child(tmp_path, N)
+    again = files[0].read_bytes()
+    head = again.split(b"\n", 5)
+    assert head[:4] == good.split(b"\n", 5)[:4] and int(head[4]) == len(head[5]) > 0
+    # another schedule: a second file
+    _specialize_check_in_child(tmp_path, 14175)
+    assert len(list(tmp_path.iterdir())) == 2
