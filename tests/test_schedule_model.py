@@ -270,3 +270,72 @@ def test_smooth_cluster_decomposition(lib, CL, NL):
                         assert hits == [(m - b) // nb]
                     else:
                         assert hits == []
+
+
+def _half_warp_degree(addrs):
+    """Most distinct float2 addresses one of 16 eight-byte bank pairs serves in
+    one half-warp of 64-bit shared-memory accesses (1: no bank conflict)."""
+    worst = 1
+    for h in range(0, len(addrs), 16):
+        banks = {}
+        for a in addrs[h:h + 16]:
+            if a is not None:
+                banks.setdefault(a & 15, set()).add(a)
+        if banks:
+            worst = max(worst, max(len(s) for s in banks.values()))
+    return worst
+
+
+@pytest.mark.parametrize("N,T,radices", [(10000, 416, (16, 25, 25)), (8000, 416, (16, 25, 20)),
+                                          (12000, 512, (16, 25, 30)), (15360, 512, (16, 30, 32)),
+                                          (14400, 512, (16, 30, 30))])
+def test_fixed_pass_addressing_is_bank_conflict_free(N, T, radices):
+    """The staging addresses of every pass of a fixed-length row (Stockham,
+    one pad float2 per 16): pass 0 writes butterfly b's outputs at
+    spad2(b R + r); a later pass reads spad2(b + r N/R) and writes
+    spad2(q Ns R + k + r Ns) (k = b mod Ns, q = b / Ns); the epilogue reads
+    spad2(o), o = j + i T.  With consecutive threads on consecutive b, no
+    half-warp's 64-bit accesses meet a bank twice when the first radix is 16
+    and every later N/R and Ns is a multiple of 16 (the fused workload's
+    10000 = 16 x 25 x 25 among them).  Other schedules are not: a first
+    radix R places consecutive threads' outputs about 17 R / 16 slots apart
+    (10000 is conflict-free, 12288 = 32 x 16 x 24 two-way, 15000 =
+    10 x 10 x 10 x 15 five-way in its first pass)."""
+    lanes = np.arange(T)
+    warps = [lanes[w:w + 32] for w in range(0, T, 32)]
+    Ns = 1
+    for p, R in enumerate(radices):
+        nb = N // R
+        gm = max(1, 32 // R)
+        for g in range(gm):
+            for warp in warps:
+                b = warp + g * T
+                live = b < nb
+                for r in range(R):
+                    if p == 0:
+                        wr = [spad2(int(x) * R + r) if ok else None for x, ok in zip(b, live)]
+                        assert _half_warp_degree(wr) == 1, (p, g, r)
+                        continue
+                    rd = [spad2(int(x) + r * nb) if ok else None for x, ok in zip(b, live)]
+                    q, k = b // Ns, b % Ns
+                    wr = [spad2(int(qq) * Ns * R + int(kk) + r * Ns) if ok else None
+                          for qq, kk, ok in zip(q, k, live)]
+                    assert _half_warp_degree(rd) == 1, ("read", p, g, r)
+                    assert _half_warp_degree(wr) == 1, ("write", p, g, r)
+        Ns *= R
+    for i in range(-(-N // T)):
+        for warp in warps:
+            o = warp + i * T
+            assert _half_warp_degree([spad2(int(x)) if x < N else None for x in o]) == 1
+
+
+@pytest.mark.parametrize("N,T,radices,first", [(12288, 512, (32, 16, 24), 2), (15000, 512, (10, 10, 10, 15), 5),
+                                                (7000, 288, (28, 10, 25), 3)])
+def test_first_pass_write_conflicts(N, T, radices, first):
+    """The first-pass writes of a radix that is not 16 meet a bank `first`
+    times in some half-warp (the model of the test above)."""
+    R = radices[0]
+    b = np.arange(T)
+    worst = max(_half_warp_degree([spad2(int(x) * R + r) if x < N // R else None for x in b[w:w + 32]])
+                for w in range(0, T, 32) for r in range(R))
+    assert worst == first
