@@ -555,8 +555,11 @@ cwt_status cwt_measure_peak(int what, double *tflops);
  * x 10000 samples x 100 scales fits; larger requests return CWT_EINVAL
  * before any device work.
  * The first call on a device (the current device) resolves the array's device
- * address and writes its twiddle table, then waits for that on `stream`; make
- * that first call before any stream capture.  The address is kept for the
+ * address and writes its twiddle table, then waits for that on `stream`.  No
+ * call may be made inside a stream capture: each one copies freqs_hz and
+ * n_cycles from pageable host memory (cudaMemcpyAsync), which a captured
+ * stream refuses or would replay from host memory the caller may have freed.
+ * The address is kept for the
  * life of the process: do not call this entry point again on a device after
  * cudaDeviceReset.  Every call copies freqs_hz and n_cycles into the array
  * (so the caller may reuse them as soon as the call returns), reuses the same
